@@ -1,0 +1,90 @@
+"""Oracle: block Davidson diagonalisation of one k (TEST INFRASTRUCTURE ONLY).
+
+Follows the steps of paper Sec. 2.1 in order, with S = I (norm-conserving projectors, no
+q_mn), in FP64, for one k at a time.  The reduced generalized problem (H~ - eps S~) v = 0
+is solved with LAPACK (scipy.linalg.eigh), which the paper also uses for this step
+(Sec. 6, ZHEGV/ZHEGVX).  ``lowest_eigenpairs`` is the exact result the iteration reaches.
+
+Readings of points the paper leaves open (listed with the design notes):
+  * the preconditioner denominator x = H_GG - eps_i is clamped to sign(x) max(|x|, 1e-2 Ry);
+  * a band is converged when |eps_i^(n+1) - eps_i^(n)| < eps_th; an optional residual
+    bound ||H phi - eps phi|| < res_tol may be required as well;
+  * a restart keeps the current Ritz vectors (the "restart with {phi^(n+1), eps^(n+1)}" step).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg
+
+
+def lowest_eigenpairs(H: np.ndarray, nb: int):
+    """Exact lowest nb eigenpairs of the dense Hermitian H(k) (Eq. ks with S = I)."""
+    w, v = np.linalg.eigh(H)
+    return w[:nb], v[:, :nb].T
+
+
+def _reduced(basis, hbasis):
+    # H~_ij = <phi_i|H|phi_j>, S~_ij = <phi_i|S|phi_j> with S = I (Sec. 2.1)
+    Hr = basis.conj() @ hbasis.T
+    Sr = basis.conj() @ basis.T
+    return 0.5 * (Hr + Hr.conj().T), 0.5 * (Sr + Sr.conj().T)
+
+
+def _precondition_denominator(x: np.ndarray, floor: float = 1e-2) -> np.ndarray:
+    s = np.where(x >= 0, 1.0, -1.0)
+    return s * np.maximum(np.abs(x), floor)
+
+
+def davidson(apply_h, h_diag: np.ndarray, psi0: np.ndarray, eth: float = 1e-10,
+             max_iter: int = 100, max_basis: int = None, res_tol: float = None):
+    """Block Davidson (Sec. 2.1) for one k.
+
+    apply_h(X) -> H X for rows X (n, npw); h_diag (npw,) the diagonal of H in the plane-wave
+    basis; psi0 (nb, npw) trial vectors.  Returns (eps (nb,), psi (nb, npw), iterations,
+    number of H applications, converged flags)."""
+    nb = psi0.shape[0]
+    if max_basis is None:
+        max_basis = 4 * nb
+    basis = psi0.astype(np.complex128).copy()
+    hbasis = apply_h(basis)
+    napply = nb
+    # 1. reduced problem on the trial vectors, eigenpairs {phi^(n), eps^(n)}
+    Hr, Sr = _reduced(basis, hbasis)
+    w, v = scipy.linalg.eigh(Hr, Sr)
+    eps, vecs = w[:nb], v[:, :nb]
+    todo = np.arange(nb)                    # the first step corrects every band
+    conv = np.zeros(nb, bool)
+    it = 0
+    for it in range(1, max_iter + 1):
+        # 2. correction vectors (H_diag - eps_i S_diag)^-1 (H - eps_i S)|phi_i>, S_diag = 1
+        ritz = vecs[:, todo].T @ basis
+        hritz = vecs[:, todo].T @ hbasis
+        resid = hritz - eps[todo, None] * ritz
+        corr = resid / _precondition_denominator(h_diag[None, :] - eps[todo, None])
+        # 3. normalisation
+        corr /= np.linalg.norm(corr, axis=1, keepdims=True)
+        # restart with the current Ritz vectors when the basis would grow too large
+        if basis.shape[0] + len(todo) > max_basis:
+            basis = vecs.T @ basis
+            hbasis = vecs.T @ hbasis
+        # 4. extended reduced Hamiltonian and overlap
+        basis = np.vstack([basis, corr])
+        hbasis = np.vstack([hbasis, apply_h(corr)])
+        napply += len(todo)
+        Hr, Sr = _reduced(basis, hbasis)
+        # 5. diagonalise the N_base x N_base reduced problem
+        w, v = scipy.linalg.eigh(Hr, Sr)
+        eps_new, vecs = w[:nb], v[:, :nb]
+        # 6. bands whose eigenvalue moved by more than eps_th still need a correction
+        moved = np.abs(eps_new - eps) > eth
+        if res_tol is not None:
+            ritz = vecs.T @ basis
+            rn = np.linalg.norm(vecs.T @ hbasis - eps_new[:, None] * ritz, axis=1)
+            moved |= rn > res_tol
+        eps = eps_new
+        todo = np.nonzero(moved)[0]
+        conv = ~moved
+        if len(todo) == 0:
+            break
+    psi = vecs.T @ basis
+    return eps, psi, it, napply, conv
