@@ -1,0 +1,183 @@
+/* pwk.h - C ABI of the many-k plane-wave Kohn-Sham library for one GB300 (sm_103a).
+ *
+ * The library applies the Kohn-Sham Hamiltonian to the Bloch wave-functions of many
+ * k-points and bands at once (Gong & Dal Corso, arXiv:2412.01695, Sec. 2.2 and Sec. 4),
+ * drives a batched block-Davidson eigensolver (Sec. 2.1, Algorithm 2) and a batched DFPT
+ * Sternheimer preconditioned CG (Sec. 2.3-2.4, Algorithm 4) on the device.
+ *
+ * Units: Rydberg atomic units.  Lengths in bohr, wave-vectors in bohr^-1, energies in Ry;
+ * the kinetic energy of a plane wave is |k+G|^2 (the Ry form of the paper's 1/2|k+G|^2 Ha).
+ *
+ * Layout conventions shared by every entry point:
+ *   complex numbers are interleaved (re, im): complex128 = 2 x double, complex64 = 2 x float;
+ *   wave-function arrays are [nk][nvec][npw_max], coefficient index fastest; entries
+ *   beyond npw(k) are padding: they must be zero on input and are written as zero on output;
+ *   real-space grids are [N1][N2][N3] with l3 fastest, r_l = sum_i (l_i/N_i) a_i (Sec. 5).
+ *   Miller indices (m1, m2, m3) give G = m1 b1 + m2 b2 + m3 b3 with a_i . b_j = 2 pi delta_ij.
+ *
+ * Ownership: every device array passed in is owned by the caller and must stay alive and
+ * unmodified for as long as the plan that references it (beta, vloc_r) or until the call
+ * returns (everything else).  A plan owns only its own tables and workspaces.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * Kernels are enqueued on it; entry points that iterate (Davidson, CG) synchronise the
+ * stream internally to read convergence counters and return with results complete.
+ *
+ * Errors: every function returns an int.  0 = success; negative values are PWK_ERR_*
+ * codes below (pwk_strerror() gives a message; pwk_last_error_detail() a detailed line
+ * for the calling thread).  Positive values from the solvers count (k, band) pairs that did
+ * not converge within max_iter.  Nothing throws across the ABI, nothing exits the process.
+ */
+#ifndef PWK_H
+#define PWK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PWK_OK 0
+#define PWK_ERR_INVALID (-1)     /* bad argument (null pointer, size, index out of range) */
+#define PWK_ERR_UNSUPPORTED (-2) /* valid but not supported (grid size, basis too large) */
+#define PWK_ERR_NOMEM (-3)       /* device allocation failed */
+#define PWK_ERR_BUDGET (-4)      /* would exceed the plan's HBM budget */
+#define PWK_ERR_CUDA (-5)        /* a CUDA runtime call or kernel launch failed */
+#define PWK_ERR_NOT_POSDEF (-6)  /* reduced overlap S~ not positive definite (Davidson) */
+#define PWK_ERR_NUMERIC (-7)     /* CG breakdown (d^T A d <= 0) or non-finite values */
+
+/* arithmetic of an H|psi> application */
+#define PWK_FP64 0        /* complex128 in/out, FP64 arithmetic                          */
+#define PWK_FP32 1        /* complex64 in/out, FP32 arithmetic                           */
+#define PWK_FP32_C128 2   /* complex128 in/out, FP32 arithmetic (mixed-precision inner)  */
+
+typedef struct pwk_plan pwk_plan; /* opaque */
+
+/* ---------------------------------------------------------------------------- plans
+ * pwk_plan_create: describe one cell, one FFT grid and one set of nk k-points with their
+ * plane-wave spheres and projectors (paper Sec. 4: the data loaded on the GPU for a block
+ * of N_k k-points before the Davidson or CG starts; Sec. 5 for the grids).
+ *   A        host [3][3]   lattice vectors a_i as rows (bohr)
+ *   N1,N2,N3               FFT grid; N1 = N2 = N3 = N with N in pwk_supported_grid()
+ *   nk                     number of k-points (>= 1)
+ *   kcart    host [nk][3]  k in cartesian coordinates (bohr^-1)
+ *   npw      host [nk]     plane waves of each k (1 <= npw[k] <= npw_max)
+ *   miller   host [nk][npw_max][3] Miller indices of the sphere of each k; every
+ *                          |m_i| < N/2 and the npw[k] indices of one k distinct
+ *   nkb                    total number of projectors over all atoms (0 allowed)
+ *   beta     device [nk][nkb][npw_max] complex128: beta_i(k+G) (Eq. lambdah), zero padded
+ *   D        host [nkb][nkb] real symmetric D^I_mn in Ry, zero between different atoms
+ *   vloc_r   device [N1][N2][N3] float64: V_eff on the real-space grid (Sec. 2.2.2)
+ *   hbm_budget bytes the plan may allocate on the device in total (0 = no limit)
+ * The plan keeps FP32 copies of beta, D and V for the FP32 paths.  Returns PWK_OK and
+ * *out, or an error (then *out is NULL).  Uses the current CUDA device; the caller must
+ * make the same device current for every later call on the plan. */
+int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int nk,
+                    const double* kcart, const int* npw, int npw_max, const int* miller,
+                    int nkb, const void* beta, const double* D, const double* vloc_r,
+                    size_t hbm_budget);
+
+/* Free every device table and workspace of the plan.  NULL is ignored. */
+void pwk_plan_destroy(pwk_plan* plan);
+
+/* Device bytes currently held by the plan (tables + workspaces). */
+size_t pwk_plan_device_bytes(const pwk_plan* plan);
+
+/* 1 if an N x N x N grid is supported by the fused kernels, else 0. */
+int pwk_supported_grid(int N);
+
+/* ---------------------------------------------------------------------------- H|psi>
+ * pwk_hpsi_batched: hpsi = H_KS psi for nb bands of every k of the plan (paper Sec. 2.2,
+ * Sec. 4 "routine that applies H_KS ... for N_k k points"):
+ *   kinetic |k+G|^2 C (Sec. 2.2.1), local V_eff by scatter G->r, inverse 3D transform,
+ *   V(r) u(r), forward 3D transform with 1/N_r and gather r->G (Sec. 2.2.2, Sec. 5),
+ *   nonlocal lambda = sum_G beta* C (Eq. lambdah), gamma = D lambda (Eq. gamma),
+ *   add-back sum gamma beta (Eq. finalnl).  S = I (norm-conserving; no q_mn).
+ *   precision  PWK_FP64, PWK_FP32 or PWK_FP32_C128
+ *   psi        device [nk][nb][npw_max] complex128 (complex64 for PWK_FP32)
+ *   hpsi       device, same shape and type; may be the same pointer as psi (in place),
+ *              must not otherwise overlap it
+ * Asynchronous on `stream`. */
+int pwk_hpsi_batched(pwk_plan* plan, int precision, const void* psi, void* hpsi, int nb,
+                     void* stream);
+
+/* pwk_hpsi_items: the same operator on an explicit work list, for uneven batches (only the
+ * listed vectors are transformed; the others are not touched).
+ *   psi, hpsi   device [nk][nvec_per_k][npw_max] of the precision's complex type
+ *   items       device int[nitems][3]: (k, in_slot, out_slot): hpsi[k][out_slot] =
+ *               H(k) psi[k][in_slot].  An entry with k outside [0, nk) or a slot outside
+ *               [0, nvec_per_k) is skipped (its output is left unchanged).
+ *   nitems      number of entries (0 allowed: nothing is launched)
+ * Two entries must not write the same output vector, and no output vector may be an input
+ * of another entry.  Asynchronous on `stream`. */
+int pwk_hpsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, const int* items,
+                   int nitems, int nvec_per_k, void* stream);
+
+/* ---------------------------------------------------------------------------- Davidson
+ * pwk_davidson_batched: lowest nb eigenpairs of H(k) for every k of the plan by the block
+ * Davidson iteration of Sec. 2.1, run for all k at once (Algorithm 2):
+ *   Rayleigh-Ritz on the basis (H~ = <phi|H|phi>, S~ = <phi|phi>, FP64 Cholesky of S~ and
+ *   Hermitian eigensolve, Sec. 6), correction vectors (H_diag - eps)^-1 (H - eps) phi,
+ *   normalisation, basis expansion, restart with the Ritz vectors when the basis would
+ *   exceed max_basis, per-band test |eps^(n+1) - eps^(n)| > eth.
+ *   mode     PWK_FP64: every H application in FP64.
+ *            PWK_FP32_C128: expansion steps use FP32 H applications until the eigenvalue
+ *            changes fall below max(eth, 1e-5 Ry); then the Ritz vectors get FP64 H
+ *            applications and the iteration continues in FP64 to eth (FP64 refinement).
+ *            Reduced matrices, the eigensolve, norms and residuals are FP64 in both modes.
+ *   psi      device [nk][nb][npw_max] complex128: trial vectors in, eigenvectors out
+ *   eig      device [nk][nb] float64: eigenvalues out (Ry), ascending per k
+ *   eth      eigenvalue threshold (Ry), > 0
+ *   res_tol  if > 0, a band also needs ||H phi - eps phi|| < res_tol to be converged
+ *   max_iter iterations (>= 1); max_basis 2*nb <= max_basis <= 160 (0 = 4*nb, capped at 160)
+ *   iters_out, notconv_out  host int[nk] or NULL: iterations used and bands left
+ *                           unconverged per k
+ *   napply_out host long long[2] or NULL: number of band H applications (FP64, FP32)
+ * Workspaces are allocated in the plan on first use (and grown when needed).
+ * Returns the number of unconverged (k, band) pairs (0 = all converged) or an error. */
+int pwk_davidson_batched(pwk_plan* plan, int mode, void* psi, double* eig, int nb, double eth,
+                         double res_tol, int max_iter, int max_basis, int* iters_out,
+                         int* notconv_out, long long* napply_out, void* stream);
+
+/* ---------------------------------------------------------------------------- Sternheimer
+ * pwk_sternheimer_cg_batched: for every k of plan_k and every occupied band n, solve the
+ * DFPT linear system of Eq. linear_system with S = I and dS = 0,
+ *   [H_{k+q} + alpha_k P_v - eps_{k,n}] dpsi_{k,n} = - P_c dV psi_{k,n},
+ * P_v = sum_{v < nocc} |psi_{k+q,v}><psi_{k+q,v}| (Eq. projector, Eqs. compute_mu,
+ * use_mu with S = I), P_c = 1 - P_v, dV = e^{iq.r} dv(r), by the preconditioned CG of
+ * Sec. 2.4 (Eqs. ax1 .. updatedold) for all (k, n) at once (Algorithm 4), with the
+ * preconditioner M_GG = max(1, |k+q+G|^2 / <psi_{k+q,n}|T|psi_{k+q,n}>).
+ *   plan_kq   plan of the k+q points (the operator); plan_k  plan of the k points; both
+ *             have the same nk, cell and grid, point i of plan_kq being k_i + q
+ *   mode      PWK_FP64: FP64 operator.  PWK_FP32_C128: FP32 H inside an FP64 iterative
+ *             refinement (true residual with the FP64 operator, FP32-operator PCG on the
+ *             correction); CG vectors, dot products and scalars are FP64 in both modes.
+ *   psi_k     device [nk][nocc][npw_max(k)] complex128    occupied states at k
+ *   eps_k     device [nk][nocc] float64                   their eigenvalues (Ry)
+ *   psi_kq    device [nk][nocc][npw_max(k+q)] complex128  occupied states at k+q
+ *   alpha     device [nk] float64                         alpha of each k (Ry)
+ *   dv_r      device [N1][N2][N3] complex128              lattice-periodic part of dV
+ *   dpsi      device [nk][nocc][npw_max(k+q)] complex128  solution out
+ *   tol       relative residual ||A x - b|| / ||b|| to reach, per (k, n)
+ *   max_iter  CG iterations per solve (per refinement step in mixed mode)
+ *   iters_out host int[nk*nocc] or NULL: CG iterations used
+ *   resid_out host double[nk*nocc] or NULL: final true relative residual (FP64 operator)
+ * Workspaces are allocated in plan_kq on first use.  Returns the number of (k, n) pairs
+ * above tol, or an error. */
+int pwk_sternheimer_cg_batched(pwk_plan* plan_kq, pwk_plan* plan_k, int mode,
+                               const void* psi_k, const double* eps_k, const void* psi_kq,
+                               int nocc, const double* alpha, const void* dv_r, void* dpsi,
+                               double tol, int max_iter, int* iters_out, double* resid_out,
+                               void* stream);
+
+/* ---------------------------------------------------------------------------- misc */
+const char* pwk_strerror(int code);
+/* Last detailed error message of the calling thread ("" if none). */
+const char* pwk_last_error_detail(void);
+/* Library version string. */
+const char* pwk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PWK_H */

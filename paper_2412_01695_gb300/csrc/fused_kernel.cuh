@@ -1,0 +1,265 @@
+// Fused H|psi> kernel: one CTA applies the Hamiltonian to one band of one k-point with a
+// single round trip to HBM (read C, write H C).
+//
+// Per work item (paper Sec. 2.2 and Sec. 5, Fig. 2 flow, here fused into one kernel):
+//   1. load C(G) and scatter it onto the z-sticks held in shared memory (Sec. 4 "sets the
+//      non zero elements of this grid"); in the same pass lambda_n = sum_G beta_n* C
+//      (Eq. lambdah), one warp per projector;
+//   2. inverse z transforms, only on the sticks (m1, m2) that carry coefficients (Eq. zfft);
+//      gamma = D lambda (Eq. gamma);
+//   3. for each chunk of L planes l3: inverse y transforms on the m1 planes that carry
+//      sticks (Eq. yfft); for every x line (l2, l3): inverse x transform (Eq. xfft),
+//      u'(r) = V(r) u(r) (Sec. 2.2.2), forward x transform keeping only the m1 planes that
+//      are carried back; forward y transforms written back onto the sticks;
+//   4. forward z transforms on the sticks (Eq. fwFFT);
+//   5. gather r -> G with the 1/N_r of Eq. fwFFT, add the kinetic term |k+G|^2 C
+//      (Sec. 2.2.1, Ry) and the nonlocal add-back sum_m gamma_m beta_m (Eq. finalnl).
+// The pruning skips transforms of lines that are identically zero or whose results are
+// discarded; the result equals the full 3D transform pair exactly (up to rounding).
+//
+// Template parameters: T arithmetic type, TI io type (complex of TI in memory), N grid
+// size, CPLXV: V is a complex128 field and the kinetic/nonlocal terms are absent (the
+// lattice-periodic dV psi product of the DFPT right-hand side, Eq. linear_system).
+#pragma once
+#include "fft_line.cuh"
+#include "pwk_internal.h"
+
+namespace pwk {
+
+// plane index p of grid slot i (signed m1 = i or i - N) in the window [m1lo, m1lo + P):
+// p = (i - m1lo) mod N; the caller tests p < P.  m1lo lies in (-N/2, N/2).
+template <int N>
+__device__ __forceinline__ int plane_of_slot(int i, int m1lo) {
+  int p = i - m1lo;
+  return p < 0 ? p + N : (p >= N ? p - N : p);
+}
+
+template <typename T, typename TI, int N, bool CPLXV>
+__global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
+  using V = c2_t<T>;
+  using VI = c2_t<TI>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+
+  const int item = blockIdx.x;
+  if (a.d_count != nullptr && item >= *a.d_count) return;
+  int k, vin, vout;
+  if (a.items != nullptr) {
+    k = a.items[3 * item];
+    vin = a.items[3 * item + 1];
+    vout = a.items[3 * item + 2];
+    if (k < 0 || k >= a.nk || vin < 0 || vin >= a.nvec_in || vout < 0 || vout >= a.nvec_out) {
+      if (threadIdx.x == 0 && a.err != nullptr) atomicOr(a.err, 1);
+      return;
+    }
+  } else {
+    k = item / a.nvec_in;
+    vin = vout = item - k * a.nvec_in;
+  }
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int npi = a.npw_in[k], npo = a.npw_out[k];
+  const int ns = a.nstick[k];
+  const int zs = a.zs, P = a.P, L = a.L;
+
+  V* Z = reinterpret_cast<V*>(smem_raw);
+  V* Y = Z + (size_t)a.nstick_max * zs;
+  V* psis = Y + (size_t)P * N * L;
+  V* lam = psis + a.npw_in_max;
+  V* gam = lam + a.nkb;
+  short* sid = reinterpret_cast<short*>(gam + a.nkb);
+
+  const VI* pin = static_cast<const VI*>(a.in) + ((size_t)k * a.nvec_in + vin) * a.npw_in_max;
+  VI* pout = static_cast<VI*>(a.out) + ((size_t)k * a.nvec_out + vout) * a.npw_out_max;
+
+  // ---- 0: zero the sticks, stage the stick table and C(G)
+  for (int i = tid; i < ns * zs; i += nth) Z[i] = V{T(0), T(0)};
+  {
+    const short* sk = a.sid + (size_t)k * P * N;
+    for (int i = tid; i < P * N; i += nth) sid[i] = sk[i];
+  }
+  for (int g = tid; g < npi; g += nth) {
+    VI v = pin[g];
+    psis[g] = V{T(v.x), T(v.y)};
+  }
+  __syncthreads();
+
+  // ---- 1: scatter onto the sticks; projections lambda (Eq. lambdah)
+  {
+    const int* gin = a.gin + (size_t)k * a.npw_in_max;
+    for (int g = tid; g < npi; g += nth) {
+      const int m = gin[g];
+      Z[(m >> 8) * zs + (m & 255)] = psis[g];
+    }
+  }
+  if constexpr (!CPLXV) {
+    if (a.nkb > 0) {
+      const V* bk = static_cast<const V*>(a.beta) + (size_t)k * a.nkb * a.npw_out_max;
+      const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+      for (int i = warp; i < a.nkb; i += nw) {
+        T sr = T(0), si = T(0);
+        const V* bi = bk + (size_t)i * a.npw_out_max;
+        for (int g = lane; g < npi; g += 32) {
+          const V b = bi[g], c = psis[g];
+          sr += b.x * c.x + b.y * c.y;   // conj(beta) * C
+          si += b.x * c.y - b.y * c.x;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          sr += __shfl_xor_sync(0xffffffffu, sr, o);
+          si += __shfl_xor_sync(0xffffffffu, si, o);
+        }
+        if (lane == 0) lam[i] = V{sr, si};
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---- 2: inverse z transforms on the sticks; gamma = D lambda (Eq. gamma)
+  for (int s = tid; s < ns; s += nth) {
+    V x[N];
+    V* zr = Z + s * zs;
+    PWK_SFOR(N, j, x[j] = zr[j]);
+    LineFFT<T, N, +1>::run(x);
+    PWK_SFOR(N, j, zr[j] = x[OutSlot<N, j>::value]);
+  }
+  if constexpr (!CPLXV) {
+    for (int i = tid; i < a.nkb; i += nth) {
+      const T* Dm = static_cast<const T*>(a.D) + (size_t)i * a.nkb;
+      T gr = T(0), gi = T(0);
+      for (int j = 0; j < a.nkb; ++j) {
+        const T d = Dm[j];
+        gr += d * lam[j].x;
+        gi += d * lam[j].y;
+      }
+      gam[i] = V{gr, gi};
+    }
+  }
+  __syncthreads();
+
+  // ---- 3: planes l3 in chunks of L
+  for (int l0 = 0; l0 < N; l0 += L) {
+    const int lc = min(L, N - l0);
+    // 3a: inverse y transforms of the carried m1 planes (Eq. yfft)
+    for (int t = tid; t < P * lc; t += nth) {
+      const int p = t / lc, c = t - p * lc;
+      V x[N];
+      PWK_SFOR(N, j, {
+        const int s = sid[p * N + j];
+        x[j] = s >= 0 ? Z[s * zs + l0 + c] : V{T(0), T(0)};
+      });
+      LineFFT<T, N, +1>::run(x);
+      V* yp = Y + (size_t)p * N * L + c;
+      PWK_SFOR(N, l2, yp[l2 * L] = x[OutSlot<N, l2>::value]);
+    }
+    __syncthreads();
+    // 3b: x lines: inverse x (Eq. xfft), V(r) product, forward x (Eq. fwFFT, x part)
+    for (int t = tid; t < N * lc; t += nth) {
+      const int l2 = t / lc, c = t - l2 * lc;
+      V x[N];
+      PWK_SFOR(N, i, {
+        const int p = plane_of_slot<N>(i, a.m1lo);
+        x[i] = ((unsigned)p < (unsigned)P) ? Y[((size_t)p * N + l2) * L + c] : V{T(0), T(0)};
+      });
+      LineFFT<T, N, +1>::run(x);
+      V y[N];
+      const size_t vb = (size_t)l2 * N + l0 + c;
+      if constexpr (CPLXV) {
+        const double2* dv = static_cast<const double2*>(a.V);
+        PWK_SFOR(N, l1, {
+          const double2 w = dv[(size_t)l1 * N * N + vb];
+          const V u = x[OutSlot<N, l1>::value];
+          y[l1] = V{T(u.x * w.x - u.y * w.y), T(u.x * w.y + u.y * w.x)};
+        });
+      } else {
+        const T* vr = static_cast<const T*>(a.V);
+        PWK_SFOR(N, l1, {
+          const T w = vr[(size_t)l1 * N * N + vb];
+          const V u = x[OutSlot<N, l1>::value];
+          y[l1] = V{u.x * w, u.y * w};
+        });
+      }
+      LineFFT<T, N, -1>::run(y);
+      PWK_SFOR(N, i, {
+        const int p = plane_of_slot<N>(i, a.m1lo);
+        if ((unsigned)p < (unsigned)P) Y[((size_t)p * N + l2) * L + c] = y[OutSlot<N, i>::value];
+      });
+    }
+    __syncthreads();
+    // 3c: forward y transforms, written back onto the sticks
+    for (int t = tid; t < P * lc; t += nth) {
+      const int p = t / lc, c = t - p * lc;
+      V x[N];
+      const V* yp = Y + (size_t)p * N * L + c;
+      PWK_SFOR(N, l2, x[l2] = yp[l2 * L]);
+      LineFFT<T, N, -1>::run(x);
+      PWK_SFOR(N, j, {
+        const int s = sid[p * N + j];
+        if (s >= 0) Z[s * zs + l0 + c] = x[OutSlot<N, j>::value];
+      });
+    }
+    __syncthreads();
+  }
+
+  // ---- 4: forward z transforms on the sticks
+  for (int s = tid; s < ns; s += nth) {
+    V x[N];
+    V* zr = Z + s * zs;
+    PWK_SFOR(N, j, x[j] = zr[j]);
+    LineFFT<T, N, -1>::run(x);
+    PWK_SFOR(N, j, zr[j] = x[OutSlot<N, j>::value]);
+  }
+  __syncthreads();
+
+  // ---- 5: gather with 1/N_r; kinetic and nonlocal add-back (Eq. finalnl)
+  {
+    const int* gout = a.gout + (size_t)k * a.npw_out_max;
+    const T sc = T(a.scale);
+    const double* g2k = a.g2 != nullptr ? a.g2 + (size_t)k * a.npw_out_max : nullptr;
+    const V* bk = nullptr;
+    if constexpr (!CPLXV) bk = static_cast<const V*>(a.beta) + (size_t)k * a.nkb * a.npw_out_max;
+    for (int g = tid; g < npo; g += nth) {
+      const int m = gout[g];
+      const V z = Z[(m >> 8) * zs + (m & 255)];
+      V acc = V{z.x * sc, z.y * sc};
+      if constexpr (!CPLXV) {
+        if (g2k != nullptr) {
+          const T t2 = T(g2k[g]);
+          acc.x += t2 * psis[g].x;
+          acc.y += t2 * psis[g].y;
+        }
+        for (int i = 0; i < a.nkb; ++i) {
+          const V b = bk[(size_t)i * a.npw_out_max + g];
+          const V c = gam[i];
+          acc.x += c.x * b.x - c.y * b.y;
+          acc.y += c.x * b.y + c.y * b.x;
+        }
+      }
+      pout[g] = VI{TI(acc.x), TI(acc.y)};
+    }
+    for (int g = npo + tid; g < a.npw_out_max; g += nth) pout[g] = VI{TI(0), TI(0)};
+  }
+}
+
+template <typename T, typename TI, bool CPLXV>
+int launch_fused(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {
+  if (nblocks <= 0) return PWK_OK;
+  switch (N) {
+#define PWK_CASE(n)                                                                             \
+  case n: {                                                                                     \
+    auto kern = fused_kernel<T, TI, n, CPLXV>;                                                  \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                         (int)s.smem);                                          \
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");                   \
+    kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \
+    e = cudaGetLastError();                                                                     \
+    if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");                           \
+    return PWK_OK;                                                                              \
+  }
+    PWK_FOR_EACH_N(PWK_CASE)
+#undef PWK_CASE
+    default:
+      set_error("unsupported grid size");
+      return PWK_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace pwk

@@ -1,0 +1,8 @@
+// Instantiation of the fused H|psi> kernel: arithmetic float, io complex of float.
+#include "fused_kernel.cuh"
+
+namespace pwk {
+int launch_fused_f32(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {
+  return launch_fused<float, float, false>(N, a, nblocks, s, st);
+}
+}  // namespace pwk

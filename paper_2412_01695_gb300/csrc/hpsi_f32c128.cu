@@ -1,0 +1,8 @@
+// Instantiation of the fused H|psi> kernel: arithmetic float, io complex of double.
+#include "fused_kernel.cuh"
+
+namespace pwk {
+int launch_fused_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {
+  return launch_fused<float, double, false>(N, a, nblocks, s, st);
+}
+}  // namespace pwk

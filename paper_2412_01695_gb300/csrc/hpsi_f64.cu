@@ -1,0 +1,8 @@
+// Instantiation of the fused H|psi> kernel: arithmetic double, io complex of double.
+#include "fused_kernel.cuh"
+
+namespace pwk {
+int launch_fused_f64(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {
+  return launch_fused<double, double, false>(N, a, nblocks, s, st);
+}
+}  // namespace pwk

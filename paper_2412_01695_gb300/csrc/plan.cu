@@ -1,0 +1,492 @@
+// Plans: the per-k tables of a block of k-points kept resident on the device (paper Sec. 4:
+// projectors and wave-function layout loaded for all N_k points before the solvers run),
+// the sphere -> stick maps of the pruned transforms (Sec. 5), and the H|psi> entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fft_line.cuh"
+#include "pwk_internal.h"
+#include "solvers.h"
+
+namespace pwk {
+
+static thread_local std::string g_detail;
+
+void set_error(const std::string& msg) { g_detail = msg; }
+
+int cuda_fail(cudaError_t e, const char* what) {
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+  set_error(buf);
+  return e == cudaErrorMemoryAllocation ? PWK_ERR_NOMEM : PWK_ERR_CUDA;
+}
+
+int plan_alloc(pwk_plan* p, void** ptr, size_t bytes) {
+  *ptr = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (p->budget != 0 && p->bytes + bytes > p->budget) {
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "allocation of %zu bytes exceeds the plan budget (%zu of %zu used)",
+                  bytes, p->bytes, p->budget);
+    set_error(buf);
+    return PWK_ERR_BUDGET;
+  }
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return cuda_fail(e, "cudaMalloc");
+  }
+  p->bytes += bytes;
+  p->allocs.push_back(*ptr);
+  p->alloc_sizes.push_back(bytes);
+  return PWK_OK;
+}
+
+void plan_free(pwk_plan* p, void* ptr) {
+  if (ptr == nullptr) return;
+  for (size_t i = 0; i < p->allocs.size(); ++i) {
+    if (p->allocs[i] == ptr) {
+      cudaFree(ptr);
+      p->bytes -= p->alloc_sizes[i];
+      p->allocs.erase(p->allocs.begin() + i);
+      p->alloc_sizes.erase(p->alloc_sizes.begin() + i);
+      return;
+    }
+  }
+}
+
+bool grid_supported(int N) {
+  switch (N) {
+#define PWK_CASE(n) case n:
+    PWK_FOR_EACH_N(PWK_CASE)
+#undef PWK_CASE
+    return true;
+    default:
+      return false;
+  }
+}
+
+size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int npw_in_max,
+                        int nkb) {
+  const int zs = (N % 2 == 0) ? N + 1 : N;
+  size_t elems = (size_t)nstick_max * zs + (size_t)P * N * L + npw_in_max + 2 * (size_t)nkb;
+  return elems * elem_bytes + (size_t)P * N * sizeof(short) + 16;
+}
+
+// ---------------------------------------------------------------- setup kernels
+// |k+G|^2 (Ry) for every basis vector of every k (paper Sec. 2.2.1), zero padding.
+__global__ void kinetic_table_kernel(int nk, int npw_max, const int* npw, const double* kc,
+                                     const int* miller, const double* B, double* g2) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)nk * npw_max) return;
+  const int k = (int)(i / npw_max), g = (int)(i % npw_max);
+  if (g >= npw[k]) {
+    g2[i] = 0.0;
+    return;
+  }
+  const int* m = miller + 3 * i;
+  double q[3];
+  for (int c = 0; c < 3; ++c) q[c] = kc[3 * k + c] + m[0] * B[c] + m[1] * B[3 + c] + m[2] * B[6 + c];
+  g2[i] = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+}
+
+__global__ void to_f32_kernel(size_t n, const double* in, float* out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (float)in[i];
+}
+
+__global__ void sum_kernel(size_t n, const double* in, double* out) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    s += in[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(out, sh[0]);
+}
+
+static int blocks_for(size_t n, int t = 256) { return (int)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- sphere maps
+// Build the stick tables for input spheres (miller_in) and output spheres (miller_out).
+int build_sphere_map(pwk_plan* p, SphereMap& sm, int nk, const int* npw_in, int npw_in_max,
+                     const int* miller_in, const int* npw_out, int npw_out_max,
+                     const int* miller_out, const int* d_npw_in, const int* d_npw_out) {
+  const int N = p->N;
+  const int half = (N - 1) / 2;
+  int m1lo = N, m1hi = -N;
+  auto check_range = [&](const int* mil, const int* npw, int npw_max) -> int {
+    for (int k = 0; k < nk; ++k)
+      for (int g = 0; g < npw[k]; ++g)
+        for (int c = 0; c < 3; ++c) {
+          const int m = mil[((size_t)k * npw_max + g) * 3 + c];
+          if (m < -half || m > half) {  // strictly |m| < N/2: one grid slot per index
+            char buf[160];
+            std::snprintf(buf, sizeof(buf), "Miller index %d (k %d, G %d) outside |m| < N/2 = %d", m, k, g, N / 2);
+            set_error(buf);
+            return PWK_ERR_INVALID;
+          }
+          if (c == 0) {
+            m1lo = std::min(m1lo, m);
+            m1hi = std::max(m1hi, m);
+          }
+        }
+    return PWK_OK;
+  };
+  int rc = check_range(miller_in, npw_in, npw_in_max);
+  if (rc) return rc;
+  rc = check_range(miller_out, npw_out, npw_out_max);
+  if (rc) return rc;
+  const int P = m1hi - m1lo + 1;
+  std::vector<int> nstick(nk), gin((size_t)nk * npw_in_max, 0), gout((size_t)nk * npw_out_max, 0);
+  std::vector<short> sid((size_t)nk * P * N, (short)-1);
+  int nsmax = 0;
+  auto wrap = [N](int m) { return ((m % N) + N) % N; };
+  for (int k = 0; k < nk; ++k) {
+    std::map<std::pair<int, int>, int> st;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int* mil = pass ? miller_out : miller_in;
+      const int nmax = pass ? npw_out_max : npw_in_max;
+      const int n = pass ? npw_out[k] : npw_in[k];
+      for (int g = 0; g < n; ++g) {
+        const int* m = mil + ((size_t)k * nmax + g) * 3;
+        st.emplace(std::make_pair(m[0], m[1]), 0);
+      }
+    }
+    int s = 0;
+    for (auto& kv : st) kv.second = s++;
+    nstick[k] = s;
+    nsmax = std::max(nsmax, s);
+    if (s >= (1 << 23) || s > 32767) {
+      set_error("too many z-sticks");
+      return PWK_ERR_UNSUPPORTED;
+    }
+    for (auto& kv : st) sid[((size_t)k * P + (kv.first.first - m1lo)) * N + wrap(kv.first.second)] = (short)kv.second;
+    for (int pass = 0; pass < 2; ++pass) {
+      const int* mil = pass ? miller_out : miller_in;
+      const int nmax = pass ? npw_out_max : npw_in_max;
+      const int n = pass ? npw_out[k] : npw_in[k];
+      std::vector<int>& dst = pass ? gout : gin;
+      std::vector<char> seen((size_t)s * N, 0);
+      for (int g = 0; g < n; ++g) {
+        const int* m = mil + ((size_t)k * nmax + g) * 3;
+        const int sk = st[std::make_pair(m[0], m[1])];
+        const int slot = wrap(m[2]);
+        if (seen[(size_t)sk * N + slot]) {
+          char buf[160];
+          std::snprintf(buf, sizeof(buf), "k %d: two basis vectors map to the same grid point (G %d)", k, g);
+          set_error(buf);
+          return PWK_ERR_INVALID;
+        }
+        seen[(size_t)sk * N + slot] = 1;
+        dst[(size_t)k * nmax + g] = (sk << 8) | slot;
+      }
+    }
+  }
+  sm.nstick_max = nsmax;
+  sm.m1lo = m1lo;
+  sm.P = P;
+  sm.npw_in_max = npw_in_max;
+  sm.npw_out_max = npw_out_max;
+  sm.d_npw_in = d_npw_in;
+  sm.d_npw_out = d_npw_out;
+  if ((rc = plan_alloc(p, (void**)&sm.d_nstick, sizeof(int) * nk))) return rc;
+  if ((rc = plan_alloc(p, (void**)&sm.d_gin, sizeof(int) * gin.size()))) return rc;
+  if ((rc = plan_alloc(p, (void**)&sm.d_gout, sizeof(int) * gout.size()))) return rc;
+  if ((rc = plan_alloc(p, (void**)&sm.d_sid, sizeof(short) * sid.size()))) return rc;
+  cudaError_t e;
+  if ((e = cudaMemcpy(sm.d_nstick, nstick.data(), sizeof(int) * nk, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(sm.d_gin, gin.data(), sizeof(int) * gin.size(), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(sm.d_gout, gout.data(), sizeof(int) * gout.size(), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(sm.d_sid, sid.data(), sizeof(short) * sid.size(), cudaMemcpyHostToDevice)))
+    return cuda_fail(e, "cudaMemcpy(sphere map)");
+  return PWK_OK;
+}
+
+// Launch shape: the largest l3 chunk that keeps two CTAs per SM (FP64: one) within the
+// 227 KB of shared memory per CTA, threads 256.
+LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int nkb, int ctas_per_sm) {
+  LaunchShape s;
+  s.threads = 256;
+  const size_t sm_total = 228 * 1024, per_cta_max = 227 * 1024;
+  const size_t target = std::min(per_cta_max, sm_total / ctas_per_sm - 1024);
+  int best = 1;
+  for (int L = N; L >= 1; --L) {
+    if (fused_smem_bytes(N, elem_bytes, sm.nstick_max, sm.P, L, sm.npw_in_max, nkb) <= target) {
+      best = L;
+      break;
+    }
+  }
+  s.L = best;
+  s.smem = fused_smem_bytes(N, elem_bytes, sm.nstick_max, sm.P, best, sm.npw_in_max, nkb);
+  return s;
+}
+
+FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out) {
+  FusedArgs a;
+  a.in = in;
+  a.out = out;
+  a.nk = p->nk;
+  a.npw_in_max = a.npw_out_max = p->npw_max;
+  a.npw_in = a.npw_out = p->d_npw;
+  a.nstick = p->self.d_nstick;
+  a.gin = p->self.d_gin;
+  a.gout = p->self.d_gout;
+  a.sid = p->self.d_sid;
+  a.nstick_max = p->self.nstick_max;
+  a.m1lo = p->self.m1lo;
+  a.P = p->self.P;
+  a.L = p->shape[precision].L;
+  a.zs = (p->N % 2 == 0) ? p->N + 1 : p->N;
+  a.g2 = p->d_g2;
+  a.nkb = p->nkb;
+  if (precision == PWK_FP64) {
+    a.beta = p->d_beta;
+    a.D = p->d_D;
+    a.V = p->d_V;
+  } else {
+    a.beta = p->d_beta32;
+    a.D = p->d_D32;
+    a.V = p->d_V32;
+  }
+  a.scale = 1.0 / (double)p->Nr;
+  a.err = p->d_err;
+  return a;
+}
+
+int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* items,
+             const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st) {
+  FusedArgs a = hpsi_args(p, precision, in, out);
+  a.items = items;
+  a.d_count = d_count;
+  a.nvec_in = nvec_in;
+  a.nvec_out = nvec_out;
+  switch (precision) {
+    case PWK_FP64: return launch_fused_f64(p->N, a, nblocks, p->shape[0], st);
+    case PWK_FP32: return launch_fused_f32(p->N, a, nblocks, p->shape[1], st);
+    case PWK_FP32_C128: return launch_fused_f32c128(p->N, a, nblocks, p->shape[2], st);
+    default: set_error("unknown precision"); return PWK_ERR_INVALID;
+  }
+}
+
+}  // namespace pwk
+
+using namespace pwk;
+
+extern "C" {
+
+int pwk_supported_grid(int N) { return grid_supported(N) ? 1 : 0; }
+
+const char* pwk_version(void) { return "pwk 0.1 (sm_103a)"; }
+
+const char* pwk_last_error_detail(void) { return g_detail.c_str(); }
+
+const char* pwk_strerror(int code) {
+  switch (code) {
+    case PWK_OK: return "success";
+    case PWK_ERR_INVALID: return "invalid argument";
+    case PWK_ERR_UNSUPPORTED: return "unsupported size or configuration";
+    case PWK_ERR_NOMEM: return "device allocation failed";
+    case PWK_ERR_BUDGET: return "plan HBM budget exceeded";
+    case PWK_ERR_CUDA: return "CUDA error";
+    case PWK_ERR_NOT_POSDEF: return "reduced overlap matrix not positive definite";
+    case PWK_ERR_NUMERIC: return "numerical breakdown";
+    default: return code > 0 ? "not converged" : "unknown error";
+  }
+}
+
+size_t pwk_plan_device_bytes(const pwk_plan* p) { return p ? p->bytes : 0; }
+
+void pwk_plan_destroy(pwk_plan* p) {
+  if (p == nullptr) return;
+  destroy_solver_work(p);
+  for (void* q : p->allocs) cudaFree(q);
+  delete p;
+}
+
+int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int nk,
+                    const double* kcart, const int* npw, int npw_max, const int* miller, int nkb,
+                    const void* beta, const double* D, const double* vloc_r, size_t hbm_budget) {
+  if (out == nullptr) {
+    set_error("out is NULL");
+    return PWK_ERR_INVALID;
+  }
+  *out = nullptr;
+  if (A == nullptr || kcart == nullptr || npw == nullptr || miller == nullptr || vloc_r == nullptr ||
+      (nkb > 0 && (beta == nullptr || D == nullptr)) || nk < 1 || npw_max < 1 || nkb < 0) {
+    set_error("null pointer or non-positive size");
+    return PWK_ERR_INVALID;
+  }
+  if (N1 != N2 || N2 != N3 || !grid_supported(N1)) {
+    set_error("grid must be N x N x N with N in the supported set");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  for (int k = 0; k < nk; ++k)
+    if (npw[k] < 1 || npw[k] > npw_max) {
+      set_error("npw[k] outside [1, npw_max]");
+      return PWK_ERR_INVALID;
+    }
+  if (nkb > 1024) {
+    set_error("more than 1024 projectors");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  pwk_plan* p = new pwk_plan();
+  cudaGetDevice(&p->device);
+  p->N = N1;
+  p->Nr = N1 * N2 * N3;
+  p->nk = nk;
+  p->npw_max = npw_max;
+  p->nkb = nkb;
+  p->budget = hbm_budget;
+  std::memcpy(p->A, A, sizeof(p->A));
+  {
+    // reciprocal rows b_i with a_i . b_j = 2 pi delta_ij: B = 2 pi (A^-1)^T
+    const double* a = A;
+    const double det = a[0] * (a[4] * a[8] - a[5] * a[7]) - a[1] * (a[3] * a[8] - a[5] * a[6]) +
+                       a[2] * (a[3] * a[7] - a[4] * a[6]);
+    if (std::fabs(det) < 1e-12) {
+      delete p;
+      set_error("singular lattice");
+      return PWK_ERR_INVALID;
+    }
+    double inv[9];
+    inv[0] = (a[4] * a[8] - a[5] * a[7]) / det;
+    inv[1] = (a[2] * a[7] - a[1] * a[8]) / det;
+    inv[2] = (a[1] * a[5] - a[2] * a[4]) / det;
+    inv[3] = (a[5] * a[6] - a[3] * a[8]) / det;
+    inv[4] = (a[0] * a[8] - a[2] * a[6]) / det;
+    inv[5] = (a[2] * a[3] - a[0] * a[5]) / det;
+    inv[6] = (a[3] * a[7] - a[4] * a[6]) / det;
+    inv[7] = (a[1] * a[6] - a[0] * a[7]) / det;
+    inv[8] = (a[0] * a[4] - a[1] * a[3]) / det;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) p->B[3 * i + j] = 2.0 * kPi * inv[3 * j + i];
+  }
+  p->h_npw.assign(npw, npw + nk);
+  p->h_kcart.assign(kcart, kcart + 3 * (size_t)nk);
+  p->h_miller.assign(miller, miller + 3 * (size_t)nk * npw_max);
+  if (nkb > 0) p->h_D.assign(D, D + (size_t)nkb * nkb);
+  p->d_beta = static_cast<const double2*>(beta);
+  p->d_V = vloc_r;
+
+  int rc = PWK_OK;
+  cudaError_t e;
+  int* d_miller = nullptr;
+  double* d_B = nullptr;
+  double* d_vsum = nullptr;
+#define TRY(x)          \
+  do {                  \
+    rc = (x);           \
+    if (rc) goto fail;  \
+  } while (0)
+#define TRYC(x, what)                  \
+  do {                                 \
+    e = (x);                           \
+    if (e != cudaSuccess) {            \
+      rc = cuda_fail(e, what);         \
+      goto fail;                       \
+    }                                  \
+  } while (0)
+  TRY(plan_alloc(p, (void**)&p->d_err, sizeof(int)));
+  TRYC(cudaMemset(p->d_err, 0, sizeof(int)), "cudaMemset");
+  TRY(plan_alloc(p, (void**)&p->d_npw, sizeof(int) * nk));
+  TRYC(cudaMemcpy(p->d_npw, npw, sizeof(int) * nk, cudaMemcpyHostToDevice), "cudaMemcpy(npw)");
+  TRY(plan_alloc(p, (void**)&p->d_kcart, sizeof(double) * 3 * nk));
+  TRYC(cudaMemcpy(p->d_kcart, kcart, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice), "cudaMemcpy(k)");
+  TRY(plan_alloc(p, (void**)&p->d_g2, sizeof(double) * (size_t)nk * npw_max));
+  TRYC(cudaMalloc(&d_miller, sizeof(int) * 3 * (size_t)nk * npw_max), "cudaMalloc(tmp)");
+  TRYC(cudaMalloc(&d_B, sizeof(double) * 9), "cudaMalloc(tmp)");
+  TRYC(cudaMemcpy(d_miller, miller, sizeof(int) * 3 * (size_t)nk * npw_max, cudaMemcpyHostToDevice),
+       "cudaMemcpy(miller)");
+  TRYC(cudaMemcpy(d_B, p->B, sizeof(double) * 9, cudaMemcpyHostToDevice), "cudaMemcpy(B)");
+  kinetic_table_kernel<<<blocks_for((size_t)nk * npw_max), 256>>>(nk, npw_max, p->d_npw, p->d_kcart,
+                                                                  d_miller, d_B, p->d_g2);
+  TRYC(cudaGetLastError(), "kinetic_table_kernel");
+  if (nkb > 0) {
+    const size_t nb2 = (size_t)nk * nkb * npw_max * 2;
+    TRY(plan_alloc(p, (void**)&p->d_beta32, sizeof(float) * nb2));
+    to_f32_kernel<<<blocks_for(nb2), 256>>>(nb2, static_cast<const double*>(beta), (float*)p->d_beta32);
+    TRYC(cudaGetLastError(), "beta to f32");
+    std::vector<float> D32(p->h_D.begin(), p->h_D.end());
+    TRY(plan_alloc(p, (void**)&p->d_D, sizeof(double) * nkb * nkb));
+    TRY(plan_alloc(p, (void**)&p->d_D32, sizeof(float) * nkb * nkb));
+    TRYC(cudaMemcpy(p->d_D, D, sizeof(double) * nkb * nkb, cudaMemcpyHostToDevice), "cudaMemcpy(D)");
+    TRYC(cudaMemcpy(p->d_D32, D32.data(), sizeof(float) * nkb * nkb, cudaMemcpyHostToDevice), "cudaMemcpy(D32)");
+  }
+  TRY(plan_alloc(p, (void**)&p->d_V32, sizeof(float) * (size_t)p->Nr));
+  to_f32_kernel<<<blocks_for(p->Nr), 256>>>((size_t)p->Nr, vloc_r, p->d_V32);
+  TRYC(cudaGetLastError(), "V to f32");
+  TRYC(cudaMalloc(&d_vsum, sizeof(double)), "cudaMalloc(tmp)");
+  TRYC(cudaMemset(d_vsum, 0, sizeof(double)), "cudaMemset");
+  sum_kernel<<<64, 256>>>((size_t)p->Nr, vloc_r, d_vsum);
+  TRYC(cudaGetLastError(), "sum_kernel");
+  TRYC(cudaMemcpy(&p->v_mean, d_vsum, sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy(vsum)");
+  p->v_mean /= (double)p->Nr;
+  TRY(build_sphere_map(p, p->self, nk, npw, npw_max, miller, npw, npw_max, miller, p->d_npw, p->d_npw));
+  p->shape[PWK_FP64] = choose_shape(p->N, 16, p->self, nkb, 1);
+  p->shape[PWK_FP32] = choose_shape(p->N, 8, p->self, nkb, 2);
+  p->shape[PWK_FP32_C128] = p->shape[PWK_FP32];
+  if (p->shape[PWK_FP64].smem > 227 * 1024) {
+    set_error("the z-sticks and one plane of the carried m1 window do not fit in shared memory");
+    rc = PWK_ERR_UNSUPPORTED;
+    goto fail;
+  }
+  TRYC(cudaDeviceSynchronize(), "plan setup");
+  cudaFree(d_miller);
+  cudaFree(d_B);
+  cudaFree(d_vsum);
+  *out = p;
+  return PWK_OK;
+fail:
+  if (d_miller) cudaFree(d_miller);
+  if (d_B) cudaFree(d_B);
+  if (d_vsum) cudaFree(d_vsum);
+  pwk_plan_destroy(p);
+  return rc;
+#undef TRY
+#undef TRYC
+}
+
+int pwk_hpsi_batched(pwk_plan* p, int precision, const void* psi, void* hpsi, int nb, void* stream) {
+  if (p == nullptr || psi == nullptr || hpsi == nullptr || nb < 1) {
+    set_error("null pointer or nb < 1");
+    return PWK_ERR_INVALID;
+  }
+  if (precision < 0 || precision > 2) {
+    set_error("unknown precision");
+    return PWK_ERR_INVALID;
+  }
+  const long long nblocks = (long long)p->nk * nb;
+  if (nblocks > 0x7fffffffLL) {
+    set_error("nk * nb too large for one launch");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  return run_hpsi(p, precision, psi, hpsi, nullptr, nullptr, (int)nblocks, nb, nb,
+                  static_cast<cudaStream_t>(stream));
+}
+
+int pwk_hpsi_items(pwk_plan* p, int precision, const void* psi, void* hpsi, const int* items,
+                   int nitems, int nvec_per_k, void* stream) {
+  if (p == nullptr || psi == nullptr || hpsi == nullptr || (nitems > 0 && items == nullptr) ||
+      nitems < 0 || nvec_per_k < 1) {
+    set_error("null pointer or bad size");
+    return PWK_ERR_INVALID;
+  }
+  if (precision < 0 || precision > 2) {
+    set_error("unknown precision");
+    return PWK_ERR_INVALID;
+  }
+  return run_hpsi(p, precision, psi, hpsi, items, nullptr, nitems, nvec_per_k, nvec_per_k,
+                  static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,125 @@
+// Internal declarations shared by the translation units of libpwk.so.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/pwk.h"
+
+// Grid sizes N (N1 = N2 = N3 = N) with an instantiated fused kernel.
+#define PWK_FOR_EACH_N(X) X(12) X(15) X(16) X(18) X(20) X(24) X(25) X(27) X(30) X(32) X(36) X(40) X(45) X(48)
+
+namespace pwk {
+
+void set_error(const std::string& msg);  // thread-local detail for pwk_last_error_detail()
+int cuda_fail(cudaError_t e, const char* what);
+
+// Device tables that place the coefficients of one sphere (input) on the FFT sticks and
+// gather the coefficients of another (output) back: for H|psi> the two are the same
+// sphere; for the DFPT right-hand side the input is the k sphere and the output the k+q one.
+struct SphereMap {
+  int nstick_max = 0;   // largest number of z-sticks over the k-points
+  int m1lo = 0, P = 0;  // the m1 planes carried after the z-pass: m1 in [m1lo, m1lo + P)
+  int npw_in_max = 0, npw_out_max = 0;
+  int* d_nstick = nullptr;   // [nk]
+  int* d_gin = nullptr;      // [nk][npw_in_max]  (stick << 8) | (m3 mod N)
+  int* d_gout = nullptr;     // [nk][npw_out_max]
+  short* d_sid = nullptr;    // [nk][P][N]: stick of (m1 = m1lo + p, m2 = slot) or -1
+  const int* d_npw_in = nullptr;
+  const int* d_npw_out = nullptr;
+};
+
+// Launch shape of the fused kernel for one precision.
+struct LaunchShape {
+  int threads = 256;
+  int L = 0;            // l3 planes per chunk of the y/x passes
+  size_t smem = 0;
+};
+
+struct DavWork;     // davidson.cu
+struct CgWork;      // sternheimer.cu
+
+}  // namespace pwk
+
+struct pwk_plan {
+  int device = 0;
+  int N = 0, Nr = 0;
+  int nk = 0, npw_max = 0, nkb = 0;
+  double A[9] = {0}, B[9] = {0};
+  std::vector<int> h_npw;
+  std::vector<double> h_kcart;
+  std::vector<int> h_miller;
+  std::vector<double> h_D;
+  // device tables
+  int* d_npw = nullptr;
+  double* d_kcart = nullptr;     // [nk][3]
+  double* d_g2 = nullptr;        // [nk][npw_max] |k+G|^2
+  const double2* d_beta = nullptr;   // caller-owned
+  float2* d_beta32 = nullptr;
+  double* d_D = nullptr;
+  float* d_D32 = nullptr;
+  const double* d_V = nullptr;   // caller-owned
+  float* d_V32 = nullptr;
+  double v_mean = 0.0;           // average of V over the grid (diagonal of the local term)
+  pwk::SphereMap self;
+  pwk::SphereMap xfer;           // from xfer_src's spheres to this plan's (DFPT rhs)
+  const pwk_plan* xfer_src = nullptr;
+  pwk::LaunchShape shape[3];     // per precision
+  pwk::LaunchShape xshape;       // transfer kernel (complex dv, FP64)
+  int* d_err = nullptr;          // device error word (bad work items)
+  // accounting
+  size_t bytes = 0, budget = 0;
+  std::vector<void*> allocs;
+  std::vector<size_t> alloc_sizes;
+  pwk::DavWork* dav = nullptr;
+  pwk::CgWork* cg = nullptr;
+};
+
+namespace pwk {
+int plan_alloc(pwk_plan* p, void** ptr, size_t bytes);   // budget-checked cudaMalloc
+void plan_free(pwk_plan* p, void* ptr);
+
+// Arguments of the fused local-potential kernel (one CTA per work item).
+struct FusedArgs {
+  const void* in = nullptr;   // input vectors (complex of the io type)
+  void* out = nullptr;        // output vectors
+  const int* items = nullptr; // [n][3] (k, in_slot, out_slot) or null: item = k * nvec + band
+  const int* d_count = nullptr;  // if set, CTAs with blockIdx.x >= *d_count exit
+  int nvec_in = 0, nvec_out = 0; // vectors per k in the in/out arrays
+  int nk = 0;
+  int npw_in_max = 0, npw_out_max = 0;
+  const int* npw_in = nullptr;
+  const int* npw_out = nullptr;
+  const int* nstick = nullptr;
+  const int* gin = nullptr;
+  const int* gout = nullptr;
+  const short* sid = nullptr;
+  int nstick_max = 0, m1lo = 0, P = 0, L = 0, zs = 0;
+  const double* g2 = nullptr;      // kinetic table [nk][npw_out_max] or null
+  const void* beta = nullptr;      // [nk][nkb][npw_out_max] complex of the arithmetic type
+  const void* D = nullptr;         // [nkb][nkb] real of the arithmetic type
+  int nkb = 0;
+  const void* V = nullptr;         // real [N^3] of the arithmetic type, or complex128 dv
+  double scale = 1.0;              // 1/N_r
+  int* err = nullptr;
+};
+
+size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int npw_in_max,
+                        int nkb);
+
+// launchers (one per arithmetic/io variant), defined in hpsi_*.cu
+int launch_fused_f64(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_fused_f32(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_fused_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchShape& s,
+                         cudaStream_t st);
+int launch_fused_xfer(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+
+// fill FusedArgs for H|psi> with this plan
+FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out);
+int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* items,
+             const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st);
+
+bool grid_supported(int N);
+}  // namespace pwk

@@ -1,0 +1,198 @@
+"""Thin ctypes binding of libpwk.so (include/pwk.h): argument marshalling only.
+
+Every function here forwards to the C ABI with device pointers taken from torch tensors
+(torch is used for device memory and streams only).  There is no CPU fallback: if the
+library is missing or no CUDA device is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libpwk.so")
+
+PWK_FP64, PWK_FP32, PWK_FP32_C128 = 0, 1, 2
+PRECISIONS = {"fp64": PWK_FP64, "fp32": PWK_FP32, "fp32_c128": PWK_FP32_C128}
+
+# every symbol declared in include/pwk.h
+EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes", "pwk_supported_grid",
+           "pwk_hpsi_batched", "pwk_hpsi_items", "pwk_davidson_batched",
+           "pwk_sternheimer_cg_batched", "pwk_strerror", "pwk_last_error_detail", "pwk_version")
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+
+
+def load(path: str = LIB_PATH):
+    """Load libpwk.so and declare its signatures (no CUDA call is made)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2412_01695_gb300.build")
+    L = ctypes.CDLL(path)
+    sig = {
+        "pwk_plan_create": (_I, [ctypes.POINTER(_P), _P, _I, _I, _I, _I, _P, _P, _I, _P, _I, _P, _P,
+                                 _P, _SZ]),
+        "pwk_plan_destroy": (None, [_P]),
+        "pwk_plan_device_bytes": (_SZ, [_P]),
+        "pwk_supported_grid": (_I, [_I]),
+        "pwk_hpsi_batched": (_I, [_P, _I, _P, _P, _I, _P]),
+        "pwk_hpsi_items": (_I, [_P, _I, _P, _P, _P, _I, _I, _P]),
+        "pwk_davidson_batched": (_I, [_P, _I, _P, _P, _I, _D, _D, _I, _I, _P, _P, _P, _P]),
+        "pwk_sternheimer_cg_batched": (_I, [_P, _P, _I, _P, _P, _P, _I, _P, _P, _P, _D, _I, _P,
+                                            _P, _P]),
+        "pwk_strerror": (ctypes.c_char_p, [_I]),
+        "pwk_last_error_detail": (ctypes.c_char_p, []),
+        "pwk_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+class PwkError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        L = load()
+        super().__init__(f"{where}: {L.pwk_strerror(code).decode()} ({code}): "
+                         f"{L.pwk_last_error_detail().decode()}")
+        self.code = code
+
+
+def _check(code: int, where: str) -> int:
+    if code < 0:
+        raise PwkError(code, where)
+    return code
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Plan:
+    """Owns a pwk_plan*; keeps the caller-owned device arrays (beta, V) alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    @property
+    def device_bytes(self) -> int:
+        return int(load().pwk_plan_device_bytes(self.handle))
+
+    def close(self):
+        if self.handle:
+            load().pwk_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_create(A, N, kcart, npw, miller, beta_dev, D, vloc_dev, hbm_budget: int = 0) -> Plan:
+    """pwk_plan_create.  A, kcart, npw, miller, D host numpy; beta_dev (complex128) and
+    vloc_dev (float64) torch CUDA tensors."""
+    L = load()
+    A = np.ascontiguousarray(A, np.float64)
+    kcart = np.ascontiguousarray(kcart, np.float64)
+    npw = np.ascontiguousarray(npw, np.int32)
+    miller = np.ascontiguousarray(miller, np.int32)
+    nk, npw_max = miller.shape[0], miller.shape[1]
+    nkb = 0 if beta_dev is None else int(beta_dev.shape[1])
+    D = np.ascontiguousarray(D if D is not None else np.zeros((0, 0)), np.float64)
+    h = ctypes.c_void_p()
+    rc = L.pwk_plan_create(ctypes.byref(h), _np_ptr(A), N, N, N, nk, _np_ptr(kcart), _np_ptr(npw),
+                           npw_max, _np_ptr(miller), nkb, _ptr(beta_dev) if nkb else None,
+                           _np_ptr(D) if nkb else None, _ptr(vloc_dev), hbm_budget)
+    _check(rc, "pwk_plan_create")
+    return Plan(h, (beta_dev, vloc_dev))
+
+
+def plan_from_problem(prob, device="cuda", hbm_budget: int = 0) -> Plan:
+    """Upload a synth.Problem's beta and V and create its plan."""
+    import torch
+    beta = torch.from_numpy(np.ascontiguousarray(prob.beta)).to(device) if prob.nkb else None
+    v = torch.from_numpy(np.ascontiguousarray(prob.V_r)).to(device)
+    return plan_create(prob.A, prob.N, prob.kpts, prob.npw, prob.miller, beta, prob.D, v,
+                       hbm_budget)
+
+
+def hpsi_batched(plan: Plan, precision: int, psi, hpsi, nb: int, stream=None) -> None:
+    _check(load().pwk_hpsi_batched(plan.handle, precision, _ptr(psi), _ptr(hpsi), nb,
+                                   _stream(stream)), "pwk_hpsi_batched")
+
+
+def hpsi_items(plan: Plan, precision: int, psi, hpsi, items, nvec_per_k: int, stream=None):
+    n = 0 if items is None else int(items.shape[0])
+    _check(load().pwk_hpsi_items(plan.handle, precision, _ptr(psi), _ptr(hpsi),
+                                 _ptr(items) if n else None, n, nvec_per_k, _stream(stream)),
+           "pwk_hpsi_items")
+
+
+def davidson_batched(plan: Plan, mode: int, psi, eig, nb: int, eth: float, res_tol: float = 0.0,
+                     max_iter: int = 100, max_basis: int = 0, stream=None):
+    """Returns (unconverged count, iters[nk], notconv[nk], napply[2])."""
+    L = load()
+    nk = psi.shape[0]
+    iters = np.zeros(nk, np.int32)
+    notc = np.zeros(nk, np.int32)
+    napply = np.zeros(2, np.int64)
+    rc = L.pwk_davidson_batched(plan.handle, mode, _ptr(psi), _ptr(eig), nb, eth, res_tol,
+                                max_iter, max_basis, _np_ptr(iters), _np_ptr(notc),
+                                _np_ptr(napply), _stream(stream))
+    _check(rc, "pwk_davidson_batched")
+    return rc, iters, notc, napply
+
+
+def sternheimer_cg_batched(plan_kq: Plan, plan_k: Plan, mode: int, psi_k, eps_k, psi_kq,
+                           nocc: int, alpha, dv, dpsi, tol: float, max_iter: int = 500,
+                           stream=None):
+    """Returns (count above tol, iters[nk*nocc], resid[nk*nocc])."""
+    L = load()
+    nk = psi_k.shape[0]
+    iters = np.zeros(nk * nocc, np.int32)
+    resid = np.zeros(nk * nocc, np.float64)
+    rc = L.pwk_sternheimer_cg_batched(plan_kq.handle, plan_k.handle, mode, _ptr(psi_k),
+                                      _ptr(eps_k), _ptr(psi_kq), nocc, _ptr(alpha), _ptr(dv),
+                                      _ptr(dpsi), tol, max_iter, _np_ptr(iters), _np_ptr(resid),
+                                      _stream(stream))
+    _check(rc, "pwk_sternheimer_cg_batched")
+    return rc, iters, resid
+
+
+def supported_grid(N: int) -> bool:
+    return bool(load().pwk_supported_grid(N))
+
+
+def version() -> str:
+    return load().pwk_version().decode()

@@ -1,0 +1,162 @@
+"""GPU parity of pwk_hpsi_batched / pwk_hpsi_items against the FP64 oracle (through the C ABI).
+
+Tolerances: FP64 path <= 1e-12 relative per band-k (||dH psi||_2 / ||H psi||_2), the stated
+bound of the FP64 path.  FP32 paths <= 5e-6: FP32 unit roundoff 6e-8 times the growth of
+the transform pair (about 2 log2 N^3 ~ 30 rounding steps) and the ratio
+max|V| ||psi|| / ||H psi|| (<= 4 on these cells) gives <= 7e-6 as a worst case; the
+measured errors are about ten times smaller.
+"""
+import numpy as np
+import pytest
+
+from oracle import hamiltonian as ham
+from paper_2412_01695_gb300 import synth
+
+from gpu_util import max_rel_err, oracle_hpsi, run_hpsi, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 5e-6
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return synth.make_config(1)
+
+
+def test_fp64_cfg1_all(cfg1):
+    ref = oracle_hpsi(cfg1)
+    out = run_hpsi(cfg1, "fp64")
+    assert max_rel_err(out, ref, cfg1) <= TOL64
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_c128"])
+def test_fp32_cfg1_all(cfg1, precision):
+    ref = oracle_hpsi(cfg1)
+    psi = cfg1.psi.astype(np.complex64).astype(np.complex128) if precision == "fp32" else None
+    out = run_hpsi(cfg1, precision, psi=psi)
+    if psi is not None:
+        ref = oracle_hpsi(cfg1, psi=psi)
+    err = max_rel_err(out, ref, cfg1)
+    assert err <= TOL32, err
+
+
+@pytest.mark.parametrize("cfg,nks", [(2, 6), (3, 3), (4, 5)])
+def test_fp64_subsets(cfg, nks):
+    """Ragged npw(k), N = 24 / 36 / 20, nkb = 9 / 36 / 9; several tiles and chunks."""
+    nkfull = int(np.prod(synth.CONFIGS[cfg]["mp"]))
+    prob = synth.make_config(cfg, k_subset=synth.sample_k(nkfull, nks), nb=min(6, synth.CONFIGS[cfg]["nb"]))
+    assert len(set(prob.npw.tolist())) > 1 or nks == 1
+    ref = oracle_hpsi(prob)
+    out = run_hpsi(prob, "fp64")
+    assert max_rel_err(out, ref, prob) <= TOL64
+    out32 = run_hpsi(prob, "fp32_c128")
+    assert max_rel_err(out32, ref, prob) <= TOL32
+
+
+def test_kq_points():
+    """The k+q set of the DFPT cell (shifted grid, same spheres' shape)."""
+    prob = synth.make_config(4, k_subset=[0, 1, 77, 4095], shift_q=True, nb=4)
+    ref = oracle_hpsi(prob)
+    assert max_rel_err(run_hpsi(prob, "fp64"), ref, prob) <= TOL64
+
+
+def test_free_electron_exact():
+    """V = 0, D = 0: H psi = |k+G|^2 psi up to the rounding of the transform pair of zeros."""
+    prob = synth.make_config(1)
+    prob.V_r = np.zeros_like(prob.V_r)
+    prob.D = np.zeros_like(prob.D)
+    out = run_hpsi(prob, "fp64")
+    for ik in range(prob.nk):
+        n = prob.npw[ik]
+        g2 = ham.kinetic(prob.kpts[ik], prob.miller[ik, :n], prob.B)
+        np.testing.assert_allclose(out[ik][:, :n], prob.psi[ik][:, :n] * g2, rtol=0, atol=1e-14)
+
+
+def test_constant_potential_shift(cfg1):
+    """Adding a constant c to V adds c psi exactly (up to rounding)."""
+    a = run_hpsi(cfg1, "fp64")
+    p2 = synth.make_config(1)
+    p2.V_r = p2.V_r + 0.37
+    b = run_hpsi(p2, "fp64")
+    for ik in range(cfg1.nk):
+        n = cfg1.npw[ik]
+        np.testing.assert_allclose(b[ik][:, :n] - a[ik][:, :n], 0.37 * cfg1.psi[ik][:, :n], atol=1e-12)
+
+
+def test_no_projectors_single_band_single_k():
+    prob = synth.make_config(2, k_subset=[5], nb=1)
+    prob.beta = prob.beta[:, :0, :]
+    prob.D = np.zeros((0, 0))
+    ref = oracle_hpsi(prob)
+    assert max_rel_err(run_hpsi(prob, "fp64"), ref, prob) <= TOL64
+
+
+def test_items_uneven_and_inplace():
+    """pwk_hpsi_items on an uneven list: only listed vectors change; invalid entries are
+    skipped; in-place (psi == hpsi) works for pwk_hpsi_batched."""
+    torch = torch_cuda()
+    from paper_2412_01695_gb300 import pwk
+    prob = synth.make_config(2, k_subset=[0, 100, 200, 511], nb=5)
+    ref = oracle_hpsi(prob)
+    plan = pwk.plan_from_problem(prob)
+    x = torch.from_numpy(prob.psi.copy()).cuda()
+    y = torch.zeros_like(x)
+    items = np.array([[0, 0, 4], [3, 4, 0], [1, 2, 2], [2, 1, 3], [1, 3, 1],
+                      [9, 0, 0], [0, 7, 0], [-1, 0, 0]], np.int32)   # last three invalid
+    pwk.hpsi_items(plan, pwk.PWK_FP64, x, y, torch.from_numpy(items).cuda(), 5)
+    torch.cuda.synchronize()
+    out = y.cpu().numpy()
+    touched = set()
+    for k, i, o in items[:5]:
+        n = prob.npw[k]
+        e = ham.relative_error(out[k, o, :n], ref[k][i, :n])
+        assert e <= TOL64
+        touched.add((k, o))
+    for k in range(4):
+        for o in range(5):
+            if (k, o) not in touched:
+                assert np.all(out[k, o] == 0)
+    # in place
+    pwk.hpsi_batched(plan, pwk.PWK_FP64, x, x, 5)
+    torch.cuda.synchronize()
+    assert max_rel_err(x.cpu().numpy(), ref, prob) <= TOL64
+    plan.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", TOL64), ("fp32", TOL32)])
+def test_full_size_cfg2_sampled(precision, tol):
+    """Full 512 k x 20 bands batch in the launch configuration the benchmark times; the
+    oracle checks a seeded sample of k-points (all their bands)."""
+    prob = synth.make_config(2)
+    psi = prob.psi.astype(np.complex64).astype(np.complex128) if precision == "fp32" else prob.psi
+    out = run_hpsi(prob, precision, psi=psi)
+    ks = synth.sample_k(prob.nk, 6, seed=11)
+    ref = oracle_hpsi(prob, psi=psi, ks=ks)
+    assert max_rel_err(out, ref, prob, ks=ks) <= tol
+    assert np.all(np.isfinite(out))
+
+
+def test_large_grid_n48():
+    """Largest instantiated grid (N = 48) on a small simple-cubic cell."""
+    A = synth.sc_lattice(6.0)
+    B = synth.reciprocal_rows(A)
+    k = synth.mp_grid(B, (2, 2, 2))[[0, 7]]
+    prob = synth.build_problem(A, np.zeros((1, 3)), (0, 1, 2), 48, 40.0, k, 3, 9)
+    ref = oracle_hpsi(prob)
+    assert max_rel_err(run_hpsi(prob, "fp64"), ref, prob) <= TOL64
+    assert max_rel_err(run_hpsi(prob, "fp32_c128"), ref, prob) <= TOL32
+
+
+def test_sphere_too_large_for_shared_memory_is_rejected():
+    """A sphere whose z-sticks do not fit in shared memory is refused at plan creation
+    (PWK_ERR_UNSUPPORTED), never launched."""
+    from paper_2412_01695_gb300 import pwk
+    A = synth.sc_lattice(8.0)
+    B = synth.reciprocal_rows(A)
+    k = synth.mp_grid(B, (1, 1, 1))
+    prob = synth.build_problem(A, np.zeros((1, 3)), (0,), 48, 75.0, k, 1, 9, with_psi=False)
+    with pytest.raises(pwk.PwkError) as ei:
+        pwk.plan_from_problem(prob)
+    assert ei.value.code == -2
