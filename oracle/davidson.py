@@ -9,7 +9,13 @@ Readings of points the paper leaves open (listed with the design notes):
   * the preconditioner denominator x = H_GG - eps_i is clamped to sign(x) max(|x|, 1e-2 Ry);
   * a band is converged when |eps_i^(n+1) - eps_i^(n)| < eps_th; an optional residual
     bound ||H phi - eps phi|| < res_tol may be required as well;
-  * a restart keeps the current Ritz vectors (the "restart with {phi^(n+1), eps^(n+1)}" step).
+  * a restart keeps the current Ritz vectors (the "restart with {phi^(n+1), eps^(n+1)}" step);
+  * when the preconditioned residual is numerically parallel to its Ritz vector
+    (|cos| > 1 - 1e-6, which happens when H is diagonal in the plane-wave basis and the
+    diagonal preconditioner is exact) the unpreconditioned residual is used instead, so the
+    correction always brings a new direction;
+  * basis vectors that are numerically dependent on the earlier ones (the Cholesky pivot of
+    S~ below 1e-9 of its diagonal) are left out of the reduced problem.
 """
 from __future__ import annotations
 
@@ -21,6 +27,27 @@ def lowest_eigenpairs(H: np.ndarray, nb: int):
     """Exact lowest nb eigenpairs of the dense Hermitian H(k) (Eq. ks with S = I)."""
     w, v = np.linalg.eigh(H)
     return w[:nb], v[:, :nb].T
+
+
+def _reduced_eig(Hr, Sr, nb, drop_tol=1e-9):
+    """Lowest nb eigenpairs of (H~ - eps S~) v = 0 on the basis vectors that are independent:
+    a vector whose Cholesky pivot falls below drop_tol of its S~ diagonal is left out (its
+    coefficients are zero)."""
+    n = len(Sr)
+    keep = []
+    for j in range(n):
+        idx = keep + [j]
+        S = Sr[np.ix_(idx, idx)]
+        try:
+            L = np.linalg.cholesky(S)
+        except np.linalg.LinAlgError:
+            continue
+        if L[-1, -1].real ** 2 > drop_tol * Sr[j, j].real:
+            keep.append(j)
+    w, v = scipy.linalg.eigh(Hr[np.ix_(keep, keep)], Sr[np.ix_(keep, keep)])
+    full = np.zeros((n, nb), np.complex128)
+    full[keep] = v[:, :nb]
+    return w[:nb], full
 
 
 def _reduced(basis, hbasis):
@@ -50,8 +77,7 @@ def davidson(apply_h, h_diag: np.ndarray, psi0: np.ndarray, eth: float = 1e-10,
     napply = nb
     # 1. reduced problem on the trial vectors, eigenpairs {phi^(n), eps^(n)}
     Hr, Sr = _reduced(basis, hbasis)
-    w, v = scipy.linalg.eigh(Hr, Sr)
-    eps, vecs = w[:nb], v[:, :nb]
+    eps, vecs = _reduced_eig(Hr, Sr, nb)
     todo = np.arange(nb)                    # the first step corrects every band
     conv = np.zeros(nb, bool)
     it = 0
@@ -61,6 +87,10 @@ def davidson(apply_h, h_diag: np.ndarray, psi0: np.ndarray, eth: float = 1e-10,
         hritz = vecs[:, todo].T @ hbasis
         resid = hritz - eps[todo, None] * ritz
         corr = resid / _precondition_denominator(h_diag[None, :] - eps[todo, None])
+        cos = np.abs(np.sum(ritz.conj() * corr, axis=1)) / (
+            np.linalg.norm(ritz, axis=1) * np.linalg.norm(corr, axis=1))
+        parallel = cos > 1.0 - 1e-6
+        corr[parallel] = resid[parallel]
         # 3. normalisation
         corr /= np.linalg.norm(corr, axis=1, keepdims=True)
         # restart with the current Ritz vectors when the basis would grow too large
@@ -73,8 +103,7 @@ def davidson(apply_h, h_diag: np.ndarray, psi0: np.ndarray, eth: float = 1e-10,
         napply += len(todo)
         Hr, Sr = _reduced(basis, hbasis)
         # 5. diagonalise the N_base x N_base reduced problem
-        w, v = scipy.linalg.eigh(Hr, Sr)
-        eps_new, vecs = w[:nb], v[:, :nb]
+        eps_new, vecs = _reduced_eig(Hr, Sr, nb)
         # 6. bands whose eigenvalue moved by more than eps_th still need a correction
         moved = np.abs(eps_new - eps) > eth
         if res_tol is not None:

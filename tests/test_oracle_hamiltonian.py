@@ -232,3 +232,19 @@ def test_davidson_restart_path(cfg1):
                                               max_basis=8, res_tol=1e-7)
     assert conv.all()
     np.testing.assert_allclose(eps, w_ref, atol=1e-9)
+
+
+def test_davidson_free_electron_degenerate():
+    """V = D = 0: H is diagonal and the diagonal preconditioner is exact, so the preconditioned
+    residual is parallel to the Ritz vector; the iteration still reaches the degenerate
+    free-electron levels (closed form of the golden table)."""
+    prob = _free(synth.make_config(1))
+    H = ham.problem_h(prob, 0)
+    n = prob.npw[0]
+    eps, psi, it, napply, conv = dav.davidson(lambda X: X @ H.T, np.real(np.diag(H)),
+                                              prob.psi[0][:, :n], eth=1e-11, max_iter=300,
+                                              res_tol=1e-7)
+    rows = np.loadtxt(os.path.join(GOLDEN, "free_electron_fcc_k0.txt"))
+    expect = (2 * math.pi / 7.5) ** 2 * rows[:prob.nb, 1] / 16.0
+    assert conv.all()
+    np.testing.assert_allclose(eps, expect, atol=1e-9)
