@@ -83,6 +83,14 @@ void pwk_plan_destroy(pwk_plan* plan);
 /* Device bytes currently held by the plan (tables + workspaces). */
 size_t pwk_plan_device_bytes(const pwk_plan* plan);
 
+/* Launch shape the plan chose for the fused H|psi> kernel of one precision (PWK_FP64,
+ * PWK_FP32 or PWK_FP32_C128): threads per CTA, l3 planes per shared-memory chunk and the
+ * dynamic shared memory per CTA.  pwk_plan_create times a few candidate shapes on the plan's
+ * own k-points and keeps the fastest; every shape gives bitwise the same result.  Any output
+ * pointer may be NULL. */
+int pwk_plan_launch_shape(const pwk_plan* plan, int precision, int* threads, int* l3_chunk,
+                          size_t* smem_bytes);
+
 /* 1 if an N x N x N grid is supported by the fused kernels, else 0. */
 int pwk_supported_grid(int N);
 
@@ -105,8 +113,9 @@ int pwk_hpsi_batched(pwk_plan* plan, int precision, const void* psi, void* hpsi,
  * listed vectors are transformed; the others are not touched).
  *   psi, hpsi   device [nk][nvec_per_k][npw_max] of the precision's complex type
  *   items       device int[nitems][3]: (k, in_slot, out_slot): hpsi[k][out_slot] =
- *               H(k) psi[k][in_slot].  An entry with k outside [0, nk) or a slot outside
- *               [0, nvec_per_k) is skipped (its output is left unchanged).
+ *               H(k) psi[k][in_slot].  An entry with k = -1 is an empty slot; an entry
+ *               with another k outside [0, nk) or a slot outside [0, nvec_per_k) is
+ *               skipped too (its output is left unchanged).
  *   nitems      number of entries (0 allowed: nothing is launched)
  * Two entries must not write the same output vector, and no output vector may be an input
  * of another entry.  Asynchronous on `stream`. */
@@ -122,8 +131,10 @@ int pwk_hpsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, c
  *   exceed max_basis, per-band test |eps^(n+1) - eps^(n)| > eth.
  *   mode     PWK_FP64: every H application in FP64.
  *            PWK_FP32_C128: expansion steps use FP32 H applications until the eigenvalue
- *            changes fall below max(eth, 1e-5 Ry); then the Ritz vectors get FP64 H
- *            applications and the iteration continues in FP64 to eth (FP64 refinement).
+ *            changes fall below max(eth, 1e-4 Ry) and the residuals below
+ *            max(res_tol, 1e-3) (the FP32 noise floor), or for at most max_iter/2
+ *            iterations; then the Ritz vectors get FP64 H applications and the iteration
+ *            continues in FP64 to eth and res_tol (FP64 refinement).
  *            Reduced matrices, the eigensolve, norms and residuals are FP64 in both modes.
  *   psi      device [nk][nb][npw_max] complex128: trial vectors in, eigenvectors out
  *   eig      device [nk][nb] float64: eigenvalues out (Ry), ascending per k
@@ -138,6 +149,23 @@ int pwk_hpsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, c
 int pwk_davidson_batched(pwk_plan* plan, int mode, void* psi, double* eig, int nb, double eth,
                          double res_tol, int max_iter, int max_basis, int* iters_out,
                          int* notconv_out, long long* napply_out, void* stream);
+
+/* pwk_eigh_batched: the batched generalized Hermitian eigensolver of the Davidson reduced
+ * problem as a stand-alone call (paper Sec. 6: ZHEGV for many k-points at once).  For each
+ * problem p < nprob: H_p v = eps S_p v, the nev lowest eigenpairs, FP64, one CTA per problem
+ * (Cholesky of S, reduction to standard form, Householder tridiagonalisation, implicit QL).
+ *   H, S    device complex128 [nprob][n][n], row-major, full Hermitian; S positive definite
+ *   eig     device float64 [nprob][nev], ascending
+ *   vec     device complex128 [nprob][n][nev]: column j is the eigenvector of eig[p][j],
+ *           S-orthonormal
+ *   status  device int [nprob] or NULL: 0, PWK_ERR_NOT_POSDEF (one of the first nev rows of
+ *           S is dependent on the earlier ones) or PWK_ERR_NUMERIC (QL did not converge)
+ * A row j >= nev whose Cholesky pivot falls below 1e-9 S_jj is treated as dependent and left
+ * out of the problem (its eigenvector entries are zero).  1 <= nev <= n <= 160.
+ * Allocates a workspace of 3 n^2 complex128 per problem for the call and synchronises
+ * `stream` before returning. */
+int pwk_eigh_batched(int nprob, int n, int nev, const void* H, const void* S, double* eig,
+                     void* vec, int* status, void* stream);
 
 /* ---------------------------------------------------------------------------- Sternheimer
  * pwk_sternheimer_cg_batched: for every k of plan_k and every occupied band n, solve the

@@ -1,0 +1,603 @@
+// Batched block-Davidson diagonalisation of H(k) for every k of a plan (paper Sec. 2.1 and
+// Algorithm 2: the Davidson steps run for all N_k k-points at once).
+//
+// Per k the basis phi (up to max_basis vectors), H phi, the reduced matrices H~, S~ and the
+// reduced eigenvectors live on the device.  Every step is a kernel over all active k:
+//   resid   : residual of each Ritz vector, correction (H_diag - eps)^-1 (H - eps) phi and
+//             its normalisation (Sec. 2.1, second and third steps)
+//   select  : which bands still need a correction (|eps^(n+1) - eps^(n)| > eth, plus an
+//             optional residual bound); a k with none left is done
+//   restart : when the basis would exceed max_basis, phi <- phi v, H phi <- (H phi) v
+//             (restart with the current Ritz vectors)
+//   append  : new vectors at the end of the basis; H applied to them with the fused kernel
+//   gram    : new rows/columns of H~ and S~ (FP64 dot products)
+//   rr      : batched FP64 generalized eigensolve (rr.cu)
+// The host only reads one counter per iteration (bands left) to decide whether to stop.
+// A k-point whose reduced problem fails (S~ numerically singular in its leading block, or QL
+// not converging) drops the vectors of that step and restarts from its Ritz vectors; after
+// more than three failures it is given up and its bands are reported unconverged.
+// Mixed mode: FP32 H applications until the bands stop moving by more than
+// max(eth, 1e-4 Ry) (and ||r|| < max(res_tol, 1e-3)); then the Ritz vectors get FP64 H
+// applications and the iteration goes on in FP64 to eth.  Reduced matrices, eigensolve, norms and residuals are FP64 always.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "solvers.h"
+
+namespace pwk {
+
+struct DavWork {
+  int nk = 0, nb = 0, MB = 0, npw_max = 0;
+  double2 *phi = nullptr, *hphi = nullptr, *corr = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;
+  double2 *Hr = nullptr, *Sr = nullptr, *W = nullptr, *ev = nullptr;
+  double *eps = nullptr, *eps_new = nullptr, *hdiag = nullptr, *rnorm = nullptr;
+  int *nbase = nullptr, *nnc = nullptr, *todo = nullptr, *active = nullptr, *moved = nullptr;
+  int *restart = nullptr, *items = nullptr, *counters = nullptr, *iters = nullptr,
+      *status = nullptr, *failcount = nullptr, *force = nullptr;
+  std::vector<void*> ptrs;
+};
+
+void destroy_dav_work(pwk_plan* p) {
+  if (p->dav == nullptr) return;
+  for (void* q : p->dav->ptrs) plan_free(p, q);
+  delete p->dav;
+  p->dav = nullptr;
+}
+
+template <typename T>
+static int dalloc(pwk_plan* p, DavWork* w, T** ptr, size_t n) {
+  int rc = plan_alloc(p, (void**)ptr, n * sizeof(T));
+  if (rc == PWK_OK) w->ptrs.push_back(*ptr);
+  return rc;
+}
+
+static int ensure_dav_work(pwk_plan* p, int nb, int MB) {
+  if (p->dav && p->dav->nb == nb && p->dav->MB == MB) return PWK_OK;
+  destroy_dav_work(p);
+  DavWork* w = new DavWork();
+  p->dav = w;
+  w->nk = p->nk;
+  w->nb = nb;
+  w->MB = MB;
+  w->npw_max = p->npw_max;
+  const size_t nk = p->nk, np = p->npw_max;
+  int rc;
+  if ((rc = dalloc(p, w, &w->phi, nk * MB * np)) || (rc = dalloc(p, w, &w->hphi, nk * MB * np)) ||
+      (rc = dalloc(p, w, &w->corr, nk * nb * np)) || (rc = dalloc(p, w, &w->tmp1, nk * nb * np)) ||
+      (rc = dalloc(p, w, &w->tmp2, nk * nb * np)) || (rc = dalloc(p, w, &w->Hr, nk * MB * MB)) ||
+      (rc = dalloc(p, w, &w->Sr, nk * MB * MB)) || (rc = dalloc(p, w, &w->W, nk * 3 * MB * MB)) ||
+      (rc = dalloc(p, w, &w->ev, nk * MB * nb)) || (rc = dalloc(p, w, &w->eps, nk * nb)) ||
+      (rc = dalloc(p, w, &w->eps_new, nk * nb)) || (rc = dalloc(p, w, &w->hdiag, nk * np)) ||
+      (rc = dalloc(p, w, &w->rnorm, nk * nb)) || (rc = dalloc(p, w, &w->nbase, nk)) ||
+      (rc = dalloc(p, w, &w->nnc, nk)) || (rc = dalloc(p, w, &w->todo, nk * nb)) ||
+      (rc = dalloc(p, w, &w->active, nk)) || (rc = dalloc(p, w, &w->moved, nk * nb)) ||
+      (rc = dalloc(p, w, &w->restart, nk)) || (rc = dalloc(p, w, &w->items, nk * nb * 3)) ||
+      (rc = dalloc(p, w, &w->counters, 4)) || (rc = dalloc(p, w, &w->iters, nk)) ||
+      (rc = dalloc(p, w, &w->status, nk)) || (rc = dalloc(p, w, &w->failcount, nk)) ||
+      (rc = dalloc(p, w, &w->force, nk))) {
+    destroy_dav_work(p);
+    return rc;
+  }
+  return PWK_OK;
+}
+
+// ------------------------------------------------------------------ kernels
+__device__ __forceinline__ double2 cmul_(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc_(double2 a, double2 b) {  // conj(a) b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__device__ double bsum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// H_diag(G) = |k+G|^2 + <V> + sum_mn beta_m(G) D_mn conj(beta_n(G))   (diagonal of H in PWs)
+__global__ void hdiag_kernel(int nk, int np, int nkb, const int* npw, const double* g2,
+                             double vmean, const double2* beta, const double* D, double* hd) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)nk * np) return;
+  const int k = (int)(i / np), g = (int)(i % np);
+  if (g >= npw[k]) {
+    hd[i] = 0.0;
+    return;
+  }
+  double s = g2[i] + vmean;
+  const double2* b = beta + (size_t)k * nkb * np + g;
+  for (int m = 0; m < nkb; ++m) {
+    const double2 bm = b[(size_t)m * np];
+    for (int n = 0; n < nkb; ++n) {
+      const double dmn = D[m * nkb + n];
+      if (dmn == 0.0) continue;
+      const double2 bn = b[(size_t)n * np];
+      s += dmn * (bm.x * bn.x + bm.y * bn.y);   // Re(beta_m conj(beta_n))
+    }
+  }
+  hd[i] = s;
+}
+
+// copy nv vectors per k between arrays with different per-k strides
+__global__ void copy_vecs_kernel(int nk, int nv, int np, const double2* src, int src_nvec,
+                                 int src_off, double2* dst, int dst_nvec, int dst_off,
+                                 const int* only) {
+  const int k = blockIdx.x / nv, j = blockIdx.x % nv;
+  if (only != nullptr && !only[k]) return;
+  const double2* s = src + ((size_t)k * src_nvec + src_off + j) * np;
+  double2* d = dst + ((size_t)k * dst_nvec + dst_off + j) * np;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) d[g] = s[g];
+}
+
+// work list: (k, base[k] + t) for t < cnt[k] on active k, else empty slots (k = -1)
+__global__ void items_kernel(int nk, int nb, const int* active, const int* base, int base_const,
+                             const int* cnt, int cnt_const, int* items) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nk * nb) return;
+  const int k = i / nb, t = i % nb;
+  const int b = base ? base[k] : base_const;
+  const int c = cnt ? cnt[k] : cnt_const;
+  const bool on = active[k] && t < c;
+  items[3 * i] = on ? k : -1;
+  items[3 * i + 1] = on ? b + t : 0;
+  items[3 * i + 2] = on ? b + t : 0;
+}
+
+// New columns b = base + t (t < cnt) of H~ and S~: rows a < base + cnt.  Each (a, b) is
+// written by one CTA (rows a >= base only for a <= b) together with its mirror (b, a).
+__global__ void __launch_bounds__(256) gram_kernel(int nb, int MB, int np, const int* npw,
+                                                   const int* active, const int* base,
+                                                   int base_const, const int* cnt, int cnt_const,
+                                                   const double2* phi, const double2* hphi,
+                                                   double2* Hr, double2* Sr) {
+  const int k = blockIdx.x / nb, t = blockIdx.x % nb;
+  if (!active[k]) return;
+  const int b0 = base ? base[k] : base_const, c = cnt ? cnt[k] : cnt_const;
+  if (t >= c) return;
+  const int b = b0 + t, nrow = b0 + c, n = npw[k];
+  extern __shared__ double2 sh[];
+  double2* pb = sh;
+  double2* hb = sh + np;
+  const double2* P = phi + (size_t)k * MB * np;
+  const double2* HP = hphi + (size_t)k * MB * np;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    pb[g] = P[(size_t)b * np + g];
+    hb[g] = HP[(size_t)b * np + g];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double2* H = Hr + (size_t)k * MB * MB;
+  double2* S = Sr + (size_t)k * MB * MB;
+  for (int a = warp; a < nrow; a += nw) {
+    if (a >= b0 && a > b) continue;
+    const double2* pa = P + (size_t)a * np;
+    double hx = 0, hy = 0, sx = 0, sy = 0;
+    for (int g = lane; g < n; g += 32) {
+      const double2 x = pa[g];
+      const double2 h = cmulc_(x, hb[g]);
+      const double2 s = cmulc_(x, pb[g]);
+      hx += h.x;
+      hy += h.y;
+      sx += s.x;
+      sy += s.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      hx += __shfl_xor_sync(0xffffffffu, hx, o);
+      hy += __shfl_xor_sync(0xffffffffu, hy, o);
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) {
+      if (a == b) {
+        H[a * MB + b] = make_double2(hx, 0.0);
+        S[a * MB + b] = make_double2(sx, 0.0);
+      } else {
+        H[a * MB + b] = make_double2(hx, hy);
+        H[b * MB + a] = make_double2(hx, -hy);
+        S[a * MB + b] = make_double2(sx, sy);
+        S[b * MB + a] = make_double2(sx, -sy);
+      }
+    }
+  }
+}
+
+// out[k][j] = sum_{i < nbase} ev[k][i][j] in[k][i]   (j < nb), for k with only[k] != 0
+__global__ void __launch_bounds__(256) rotate_kernel(int nb, int MB, int np, const int* nbase,
+                                                     const int* only, const double2* ev,
+                                                     const double2* in, double2* out,
+                                                     int out_nvec) {
+  const int k = blockIdx.x / nb, j = blockIdx.x % nb;
+  if (only != nullptr && !only[k]) return;
+  const int n = nbase[k];
+  __shared__ double2 c[kMaxBasis];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) c[i] = ev[((size_t)k * MB + i) * nb + j];
+  __syncthreads();
+  const double2* X = in + (size_t)k * MB * np;
+  double2* o = out + ((size_t)k * out_nvec + j) * np;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) {
+    double sx = 0, sy = 0;
+    for (int i = 0; i < n; ++i) {
+      const double2 t = cmul_(c[i], X[(size_t)i * np + g]);
+      sx += t.x;
+      sy += t.y;
+    }
+    o[g] = make_double2(sx, sy);
+  }
+}
+
+// Correction vector of band i (Sec. 2.1): r = sum_j v_ji (H phi_j - eps_i phi_j),
+// c = r / clamp(H_diag - eps_i), c /= ||c||.  ||r|| is stored for the residual test.  When c
+// is numerically parallel to the Ritz vector (|cos| > 1 - 1e-6: H diagonal in plane waves,
+// exact preconditioner) the unpreconditioned r is used, so the correction is a new direction.
+__global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, const int* npw,
+                                                    const int* nbase, const int* active,
+                                                    const int* moved, int all_bands,
+                                                    const double2* ev, const double* eps,
+                                                    const double2* phi, const double2* hphi,
+                                                    const double* hdiag, double2* corr,
+                                                    double* rnorm) {
+  const int k = blockIdx.x / nb, i = blockIdx.x % nb;
+  if (!active[k]) return;
+  if (!all_bands && !moved[k * nb + i]) return;
+  const int n = nbase[k], npk = npw[k];
+  __shared__ double2 c[kMaxBasis];
+  __shared__ double red[32];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) c[j] = ev[((size_t)k * MB + j) * nb + i];
+  __syncthreads();
+  const double e = eps[k * nb + i];
+  const double2* P = phi + (size_t)k * MB * np;
+  const double2* HP = hphi + (size_t)k * MB * np;
+  double2* out = corr + ((size_t)k * nb + i) * np;
+  const double* hd = hdiag + (size_t)k * np;
+  double rr = 0.0, cc = 0.0, zz = 0.0, zcx = 0.0, zcy = 0.0;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    double rx = 0, ry = 0, zx = 0, zy = 0;
+    for (int j = 0; j < n; ++j) {
+      const double2 hp = HP[(size_t)j * np + g], p = P[(size_t)j * np + g];
+      const double2 d = make_double2(hp.x - e * p.x, hp.y - e * p.y);
+      const double2 t = cmul_(c[j], d);
+      const double2 z = cmul_(c[j], p);
+      rx += t.x;
+      ry += t.y;
+      zx += z.x;
+      zy += z.y;
+    }
+    rr += rx * rx + ry * ry;
+    double x = hd[g] - e;
+    const double s = x >= 0.0 ? 1.0 : -1.0;
+    x = s * fmax(fabs(x), 1e-2);
+    const double2 v = make_double2(rx / x, ry / x);
+    cc += v.x * v.x + v.y * v.y;
+    zz += zx * zx + zy * zy;
+    zcx += zx * v.x + zy * v.y;   // <ritz|v>
+    zcy += zx * v.y - zy * v.x;
+    out[g] = make_double2(rx, ry);
+  }
+  rr = bsum(rr, red);
+  cc = bsum(cc, red);
+  zz = bsum(zz, red);
+  zcx = bsum(zcx, red);
+  zcy = bsum(zcy, red);
+  const bool parallel = (zcx * zcx + zcy * zcy) > (1.0 - 1e-6) * (1.0 - 1e-6) * zz * cc;
+  const double nrm2 = parallel ? rr : cc;
+  const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) {
+    if (g < npk) {
+      const double2 r = out[g];
+      double sc = inv;
+      if (!parallel) {
+        double x = hd[g] - e;
+        const double s = x >= 0.0 ? 1.0 : -1.0;
+        sc = inv / (s * fmax(fabs(x), 1e-2));
+      }
+      out[g] = make_double2(r.x * sc, r.y * sc);
+    } else {
+      out[g] = make_double2(0.0, 0.0);
+    }
+  }
+  if (threadIdx.x == 0) rnorm[k * nb + i] = sqrt(rr);
+}
+
+// Which bands still need a correction.  counters[0] += bands left; counters[1] |= a k-point
+// given up after repeated failures of its reduced problem (counters[2], [3]: its k and status).
+__global__ void select_kernel(int nk, int nb, int MB, double res_tol, int* active, const int* moved,
+                              const double* rnorm, const int* nbase, int* todo, int* nnc,
+                              int* restart, int* iters, const int* status, int* force,
+                              const int* failcount, int* counters) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk) return;
+  if (active[k] && failcount[k] > 3) {   // give this k-point up: its bands stay unconverged
+    active[k] = 0;
+    nnc[k] = nb;
+    restart[k] = 0;
+    atomicAdd(&counters[1], nb);
+    if (atomicCAS(&counters[2], -1, k) == -1) counters[3] = status[k];
+    return;
+  }
+  if (!active[k]) {
+    nnc[k] = 0;
+    restart[k] = 0;
+    return;
+  }
+  int c = 0;
+  for (int i = 0; i < nb; ++i) {
+    const bool conv = !moved[k * nb + i] && (res_tol <= 0.0 || rnorm[k * nb + i] <= res_tol);
+    if (!conv) todo[k * nb + c++] = i;
+  }
+  nnc[k] = c;
+  restart[k] = (c > 0 && (nbase[k] + c > MB || force[k])) ? 1 : 0;
+  force[k] = 0;
+  if (c == 0) active[k] = 0;
+  else iters[k] += 1;
+  atomicAdd(&counters[0], c);
+}
+
+__global__ void append_kernel(int nb, int MB, int np, const int* active, const int* nbase,
+                              const int* nnc, const int* todo, const double2* corr, double2* phi) {
+  const int k = blockIdx.x / nb, t = blockIdx.x % nb;
+  if (!active[k] || t >= nnc[k]) return;
+  const int i = todo[k * nb + t];
+  const double2* s = corr + ((size_t)k * nb + i) * np;
+  double2* d = phi + ((size_t)k * MB + nbase[k] + t) * np;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) d[g] = s[g];
+}
+
+__global__ void set_nbase_kernel(int nk, const int* only, int* nbase, int value, const int* add) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nk || (only && !only[k])) return;
+  nbase[k] = add ? nbase[k] + add[k] : value;
+}
+
+// After the eigensolve: moved = |eps_new - eps| > eth, eps = eps_new.  A k-point whose
+// reduced problem failed (status != 0: the eigensolver wrote nothing) drops the vectors of
+// this step (n_base -= added[k]), keeps its previous Ritz pairs, corrects every band again and
+// restarts from its Ritz vectors at the next step; after more than three failures it is
+// given up (reported as an error by the next select).
+__global__ void update_kernel(int nk, int nb, double eth, int* active, int force_all,
+                              const double* eps_new, double* eps, int* moved, const int* status,
+                              const int* added, int* nbase, int* force, int* failcount) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nk * nb) return;
+  const int k = i / nb;
+  if (!active[k]) return;
+  if (status[k] != 0) {
+    moved[i] = 1;
+    if (i % nb == 0) {
+      if (added != nullptr) nbase[k] -= added[k];
+      force[k] = 1;
+      failcount[k] += 1;
+    }
+    return;
+  }
+  moved[i] = force_all ? 1 : (fabs(eps_new[i] - eps[i]) > eth);
+  eps[i] = eps_new[i];
+}
+
+__global__ void fill_int_kernel(int n, int* a, int v) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+static int blocks(size_t n, int t = 256) { return (int)((n + t - 1) / t); }
+
+// Diagnostic: when the environment variable PWK_DUMP_RR names a directory, the reduced
+// H~ and S~ (leading n x n block, complex128, row-major) of a k-point whose reduced problem
+// failed are written there as rr_H_k<k>.bin and rr_S_k<k>.bin.
+static void dump_reduced(const DavWork* w, int k, int n) {
+  const char* dir = std::getenv("PWK_DUMP_RR");
+  if (dir == nullptr || k < 0 || n <= 0 || n > w->MB) return;
+  std::vector<double2> h((size_t)w->MB * w->MB), s((size_t)w->MB * w->MB);
+  const size_t off = (size_t)k * w->MB * w->MB;
+  if (cudaMemcpy(h.data(), w->Hr + off, h.size() * sizeof(double2), cudaMemcpyDeviceToHost) ||
+      cudaMemcpy(s.data(), w->Sr + off, s.size() * sizeof(double2), cudaMemcpyDeviceToHost))
+    return;
+  for (int which = 0; which < 2; ++which) {
+    char path[512];
+    std::snprintf(path, sizeof(path), "%s/rr_%s_k%d.bin", dir, which ? "S" : "H", k);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) continue;
+    const std::vector<double2>& m = which ? s : h;
+    for (int r = 0; r < n; ++r) std::fwrite(m.data() + (size_t)r * w->MB, sizeof(double2), n, f);
+    std::fclose(f);
+  }
+}
+
+#define KCHECK(what)                                 \
+  do {                                               \
+    cudaError_t e_ = cudaGetLastError();             \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+}  // namespace pwk
+
+using namespace pwk;
+
+extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* eig, int nb,
+                                    double eth, double res_tol, int max_iter, int max_basis,
+                                    int* iters_out, int* notconv_out, long long* napply_out,
+                                    void* stream) {
+  if (p == nullptr || psi_v == nullptr || eig == nullptr || nb < 1 || !(eth > 0.0) || max_iter < 1) {
+    set_error("null pointer, nb < 1, eth <= 0 or max_iter < 1");
+    return PWK_ERR_INVALID;
+  }
+  if (mode != PWK_FP64 && mode != PWK_FP32_C128) {
+    set_error("mode must be PWK_FP64 or PWK_FP32_C128");
+    return PWK_ERR_INVALID;
+  }
+  int MB = max_basis > 0 ? max_basis : std::min(4 * nb, kMaxBasis);
+  if (MB < 2 * nb || MB > kMaxBasis) {
+    set_error("need 2*nb <= max_basis <= 160");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  for (int k = 0; k < p->nk; ++k)
+    if (p->h_npw[k] < MB) {
+      set_error("max_basis exceeds the number of plane waves of a k-point");
+      return PWK_ERR_INVALID;
+    }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = ensure_dav_work(p, nb, MB);
+  if (rc) return rc;
+  DavWork* w = p->dav;
+  const int nk = p->nk, np = p->npw_max;
+  double2* psi = static_cast<double2*>(psi_v);
+  const size_t gram_smem = 2 * (size_t)np * sizeof(double2);
+  if (gram_smem > 227 * 1024) {
+    set_error("npw_max too large for the Gram kernel (2 vectors in shared memory)");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  if (gram_smem > 48 * 1024)
+    cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem);
+  long long napply[2] = {0, 0};
+  int total = 0, given_up = 0, host_counters[4] = {0, 0, -1, 0};
+
+  hdiag_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>(nk, np, p->nkb, p->d_npw, p->d_g2, p->v_mean,
+                                                        p->d_beta, p->d_D, w->hdiag);
+  KCHECK("hdiag_kernel");
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, 1);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iters, 0);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->status, 0);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, 0);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->force, 0);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->failcount, 0);
+  copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi, MB, 0, nullptr);
+  KCHECK("davidson init");
+
+  // H on phi[0:nb] in precision prec, reduced matrices of that block, eigensolve
+  auto start_block = [&](int prec, const int* only) -> int {
+    items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, only ? only : w->active, nullptr, 0,
+                                                          nullptr, nb, w->items);
+    KCHECK("items_kernel");
+    int r = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st);
+    if (r) return r;
+    napply[prec == PWK_FP64 ? 0 : 1] += (long long)nk * nb;
+    gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->active, nullptr, 0, nullptr,
+                                                 nb, w->phi, w->hphi, w->Hr, w->Sr);
+    KCHECK("gram_kernel");
+    set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, w->nbase, nb, nullptr);
+    r = launch_rr(nk, MB, nb, w->nbase, w->active, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st);
+    if (r) return r;
+    return PWK_OK;
+  };
+
+  // Phase 1 (mixed mode) stops at the FP32 noise floor: eigenvalues of the reduced problem
+  // built from FP32 H applications move by ~1e-6 |H| between iterations, residuals bottom out
+  // near 1e-5, so phase 1 asks for |d eps| < 1e-4 Ry and ||r|| < 1e-3, and runs at most
+  // max_iter/2 iterations; phase 2 (FP64) reaches eth and res_tol.
+  int phase = (mode == PWK_FP32_C128) ? 1 : 2;
+  int prec = phase == 1 ? PWK_FP32_C128 : PWK_FP64;
+  double eth_cur = phase == 1 ? std::max(eth, 1e-4) : eth;
+  double rt_cur = phase == 1 && res_tol > 0 ? std::max(res_tol, 1e-3) : res_tol;
+  const int phase1_cap = std::max(1, max_iter / 2);
+  if ((rc = start_block(prec, nullptr))) return rc;
+  update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth_cur, w->active, 1, w->eps_new,
+                                                         w->eps, w->moved, w->status, nullptr,
+                                                         w->nbase, w->force, w->failcount);
+  KCHECK("update_kernel");
+
+  int it = 0;
+  for (;;) {
+    resid_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved,
+                                          rt_cur > 0 ? 1 : 0, w->ev, w->eps, w->phi, w->hphi,
+                                          w->hdiag, w->corr, w->rnorm);
+    KCHECK("resid_kernel");
+    cudaMemsetAsync(w->counters, 0, 2 * sizeof(int), st);
+    cudaMemsetAsync(w->counters + 2, 0xff, sizeof(int), st);
+    select_kernel<<<blocks(nk), 256, 0, st>>>(nk, nb, MB, rt_cur, w->active, w->moved, w->rnorm,
+                                              w->nbase, w->todo, w->nnc, w->restart, w->iters,
+                                              w->status, w->force, w->failcount, w->counters);
+    KCHECK("select_kernel");
+    cudaError_t ce = cudaMemcpyAsync(host_counters, w->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "davidson counters");
+    if (host_counters[1]) {
+      given_up += host_counters[1];
+      int nbk = -1;
+      cudaMemcpy(&nbk, w->nbase + host_counters[2], sizeof(int), cudaMemcpyDeviceToHost);
+      dump_reduced(w, host_counters[2], nbk);
+      char buf[200];
+      std::snprintf(buf, sizeof(buf),
+                    "k=%d given up after repeated reduced-problem failures (status %d: %s), "
+                    "iteration %d, phase %d, n_base %d",
+                    host_counters[2], host_counters[3],
+                    host_counters[3] == PWK_ERR_NUMERIC ? "QL did not converge" : "S~ not positive definite",
+                    it, phase, nbk);
+      set_error(buf);
+    }
+    total = host_counters[0];
+    if (total == 0 || (phase == 1 && it >= phase1_cap)) {
+      if (phase == 1) {
+        // FP64 refinement: restart every k from its Ritz vectors with FP64 H applications
+        phase = 2;
+        prec = PWK_FP64;
+        eth_cur = eth;
+        rt_cur = res_tol;
+        fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, 1);
+        rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi, w->tmp1, nb);
+        copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, nullptr);
+        KCHECK("refinement restart");
+        if ((rc = start_block(prec, nullptr))) return rc;
+        update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth_cur, w->active, 0,
+                                                               w->eps_new, w->eps, w->moved,
+                                                               w->status, nullptr, w->nbase,
+                                                               w->force, w->failcount);
+        KCHECK("update_kernel");
+        continue;
+      }
+      break;
+    }
+    if (++it > max_iter) break;
+    // restart the k-points whose basis would overflow
+    rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->phi, w->tmp1, nb);
+    rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->hphi, w->tmp2, nb);
+    copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, w->restart);
+    copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp2, nb, 0, w->hphi, MB, 0, w->restart);
+    gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->restart, nullptr, 0, nullptr,
+                                                 nb, w->phi, w->hphi, w->Hr, w->Sr);
+    set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, w->nbase, nb, nullptr);
+    KCHECK("davidson restart");
+    // append the corrections, apply H to them, extend H~ and S~
+    append_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->active, w->nbase, w->nnc, w->todo, w->corr, w->phi);
+    items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, w->active, w->nbase, 0, w->nnc, 0, w->items);
+    KCHECK("davidson append");
+    if ((rc = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st))) return rc;
+    napply[prec == PWK_FP64 ? 0 : 1] += total;
+    gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->active, w->nbase, 0, w->nnc, 0,
+                                                 w->phi, w->hphi, w->Hr, w->Sr);
+    set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, w->nbase, 0, w->nnc);
+    KCHECK("davidson gram");
+    if ((rc = launch_rr(nk, MB, nb, w->nbase, w->active, w->Hr, w->Sr, w->W, w->ev, w->eps_new,
+                        w->status, st)))
+      return rc;
+    update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth_cur, w->active, 0, w->eps_new,
+                                                           w->eps, w->moved, w->status, w->nnc,
+                                                           w->nbase, w->force, w->failcount);
+    KCHECK("update_kernel");
+  }
+  // eigenvectors out: psi = phi v; eigenvalues out
+  rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi, psi, nb);
+  KCHECK("final rotate");
+  cudaError_t ce = cudaMemcpyAsync(eig, w->eps, sizeof(double) * nk * nb, cudaMemcpyDeviceToDevice, st);
+  std::vector<int> h_iters(nk), h_nnc(nk);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_iters.data(), w->iters, sizeof(int) * nk, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_nnc.data(), w->nnc, sizeof(int) * nk, cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "davidson results");
+  if (iters_out) std::memcpy(iters_out, h_iters.data(), sizeof(int) * nk);
+  if (notconv_out) std::memcpy(notconv_out, h_nnc.data(), sizeof(int) * nk);
+  if (napply_out) {
+    napply_out[0] = napply[0];
+    napply_out[1] = napply[1];
+  }
+  return total + given_up;
+}

@@ -20,11 +20,40 @@
 // Template parameters: T arithmetic type, TI io type (complex of TI in memory), N grid
 // size, CPLXV: V is a complex128 field and the kinetic/nonlocal terms are absent (the
 // lattice-periodic dV psi product of the DFPT right-hand side, Eq. linear_system).
+// The real V(r) is read from a transposed copy [l2][l3][l1] (one x-line contiguous); the
+// complex dv(r) keeps the caller's [l1][l2][l3] layout.
 #pragma once
+#include <type_traits>
+
 #include "fft_line.cuh"
 #include "pwk_internal.h"
 
 namespace pwk {
+
+// Load the N contiguous values of one V(r) x-line (layout [l2][l3][l1], l1 fastest) with
+// 16-byte vector loads when the line is 16-byte aligned (N * sizeof(T) a multiple of 16).
+template <typename T, int N>
+__device__ __forceinline__ void load_vline(const T* __restrict__ p, T (&w)[N]) {
+  constexpr int VEC = 16 / sizeof(T);
+  if constexpr ((N * sizeof(T)) % 16 == 0) {
+    using VT = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+    const VT* q = reinterpret_cast<const VT*>(p);
+    PWK_SFOR(N / VEC, j, {
+      const VT v = __ldg(q + j);
+      if constexpr (sizeof(T) == 4) {
+        w[4 * j] = v.x;
+        w[4 * j + 1] = v.y;
+        w[4 * j + 2] = v.z;
+        w[4 * j + 3] = v.w;
+      } else {
+        w[2 * j] = v.x;
+        w[2 * j + 1] = v.y;
+      }
+    });
+  } else {
+    PWK_SFOR(N, j, w[j] = __ldg(p + j));
+  }
+}
 
 // plane index p of grid slot i (signed m1 = i or i - N) in the window [m1lo, m1lo + P):
 // p = (i - m1lo) mod N; the caller tests p < P.  m1lo lies in (-N/2, N/2).
@@ -47,6 +76,7 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
     k = a.items[3 * item];
     vin = a.items[3 * item + 1];
     vout = a.items[3 * item + 2];
+    if (k == -1) return;   // an empty slot of a fixed-size work list
     if (k < 0 || k >= a.nk || vin < 0 || vin >= a.nvec_in || vout < 0 || vout >= a.nvec_out) {
       if (threadIdx.x == 0 && a.err != nullptr) atomicOr(a.err, 1);
       return;
@@ -170,11 +200,12 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
           y[l1] = V{T(u.x * w.x - u.y * w.y), T(u.x * w.y + u.y * w.x)};
         });
       } else {
-        const T* vr = static_cast<const T*>(a.V);
+        // V transposed: the x-line (l2, l3) is contiguous
+        T w[N];
+        load_vline<T, N>(static_cast<const T*>(a.V) + ((size_t)l2 * N + l0 + c) * N, w);
         PWK_SFOR(N, l1, {
-          const T w = vr[(size_t)l1 * N * N + vb];
           const V u = x[OutSlot<N, l1>::value];
-          y[l1] = V{u.x * w, u.y * w};
+          y[l1] = V{u.x * w[l1], u.y * w[l1]};
         });
       }
       LineFFT<T, N, -1>::run(y);

@@ -100,6 +100,16 @@ __global__ void to_f32_kernel(size_t n, const double* in, float* out) {
   if (i < n) out[i] = (float)in[i];
 }
 
+// Vt[(l2 N + l3) N + l1] = V[(l1 N + l2) N + l3]: one x-line of the grid contiguous
+template <typename T>
+__global__ void transpose_v_kernel(int N, const double* V, T* Vt) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t n3 = (size_t)N * N * N;
+  if (i >= n3) return;
+  const int l1 = (int)(i % N), l3 = (int)((i / N) % N), l2 = (int)(i / ((size_t)N * N));
+  Vt[i] = (T)V[((size_t)l1 * N + l2) * N + l3];
+}
+
 __global__ void sum_kernel(size_t n, const double* in, double* out) {
   __shared__ double sh[256];
   double s = 0.0;
@@ -231,6 +241,80 @@ LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int nkb, in
   return s;
 }
 
+static int launch_variant(int precision, int N, const FusedArgs& a, int nblocks,
+                          const LaunchShape& s, cudaStream_t st) {
+  switch (precision) {
+    case PWK_FP64: return launch_fused_f64(N, a, nblocks, s, st);
+    case PWK_FP32: return launch_fused_f32(N, a, nblocks, s, st);
+    default: return launch_fused_f32c128(N, a, nblocks, s, st);
+  }
+}
+
+// Pick the launch shape (threads per CTA, l3 chunk L) of one precision by timing the fused
+// kernel on a sample of the plan's k-points (8 zero vectors per k; the work of the kernel
+// does not depend on the values).  Every candidate gives bitwise the same result: the
+// arithmetic of each line and the order of every reduction do not depend on the shape.
+int autotune_shape(pwk_plan* p, int precision) {
+  const int N = p->N;
+  const int elem = precision == PWK_FP64 ? 16 : 8;
+  const int io_elem = precision == PWK_FP32 ? 8 : 16;
+  std::vector<LaunchShape> cands;
+  const int Ls[3] = {N, (N + 1) / 2, (N + 2) / 3};
+  for (int T : {128, 192, 256})
+    for (int li = 0; li < 3; ++li) {
+      const int L = Ls[li];
+      if (li > 0 && L == Ls[li - 1]) continue;
+      LaunchShape c;
+      c.threads = T;
+      c.L = L;
+      c.smem = fused_smem_bytes(N, elem, p->self.nstick_max, p->self.P, L, p->npw_max, p->nkb);
+      if (c.smem <= 227 * 1024) cands.push_back(c);
+    }
+  if (cands.empty()) return PWK_OK;   // the default shape stands (plan creation checked it)
+  const int nv = 8, nkt = std::min(p->nk, 192);
+  const size_t bytes = (size_t)nkt * nv * p->npw_max * io_elem;
+  void *in = nullptr, *out = nullptr;
+  if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&out, bytes) != cudaSuccess) {
+    cudaFree(in);
+    cudaGetLastError();
+    return PWK_OK;   // no room to tune: keep the default
+  }
+  cudaMemset(in, 0, bytes);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  FusedArgs a = hpsi_args(p, precision, in, out);
+  a.nvec_in = a.nvec_out = nv;
+  float best = 1e30f;
+  LaunchShape pick = p->shape[precision];
+  for (const LaunchShape& c : cands) {
+    a.L = c.L;
+    if (launch_variant(precision, N, a, nkt * nv, c, 0) != PWK_OK) {
+      cudaGetLastError();
+      continue;
+    }
+    cudaEventRecord(e0, 0);
+    for (int r = 0; r < 3; ++r) launch_variant(precision, N, a, nkt * nv, c, 0);
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(in);
+  cudaFree(out);
+  p->shape[precision] = pick;
+  return PWK_OK;
+}
+
 FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out) {
   FusedArgs a;
   a.in = in;
@@ -252,7 +336,7 @@ FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out)
   if (precision == PWK_FP64) {
     a.beta = p->d_beta;
     a.D = p->d_D;
-    a.V = p->d_V;
+    a.V = p->d_Vt64;
   } else {
     a.beta = p->d_beta32;
     a.D = p->d_D32;
@@ -305,6 +389,18 @@ const char* pwk_strerror(int code) {
 }
 
 size_t pwk_plan_device_bytes(const pwk_plan* p) { return p ? p->bytes : 0; }
+
+int pwk_plan_launch_shape(const pwk_plan* p, int precision, int* threads, int* l3_chunk,
+                          size_t* smem_bytes) {
+  if (p == nullptr || precision < 0 || precision > 2) {
+    set_error("null plan or unknown precision");
+    return PWK_ERR_INVALID;
+  }
+  if (threads) *threads = p->shape[precision].threads;
+  if (l3_chunk) *l3_chunk = p->shape[precision].L;
+  if (smem_bytes) *smem_bytes = p->shape[precision].smem;
+  return PWK_OK;
+}
 
 void pwk_plan_destroy(pwk_plan* p) {
   if (p == nullptr) return;
@@ -423,8 +519,10 @@ int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int
     TRYC(cudaMemcpy(p->d_D32, D32.data(), sizeof(float) * nkb * nkb, cudaMemcpyHostToDevice), "cudaMemcpy(D32)");
   }
   TRY(plan_alloc(p, (void**)&p->d_V32, sizeof(float) * (size_t)p->Nr));
-  to_f32_kernel<<<blocks_for(p->Nr), 256>>>((size_t)p->Nr, vloc_r, p->d_V32);
-  TRYC(cudaGetLastError(), "V to f32");
+  TRY(plan_alloc(p, (void**)&p->d_Vt64, sizeof(double) * (size_t)p->Nr));
+  transpose_v_kernel<float><<<blocks_for(p->Nr), 256>>>(p->N, vloc_r, p->d_V32);
+  transpose_v_kernel<double><<<blocks_for(p->Nr), 256>>>(p->N, vloc_r, p->d_Vt64);
+  TRYC(cudaGetLastError(), "V transpose");
   TRYC(cudaMalloc(&d_vsum, sizeof(double)), "cudaMalloc(tmp)");
   TRYC(cudaMemset(d_vsum, 0, sizeof(double)), "cudaMemset");
   sum_kernel<<<64, 256>>>((size_t)p->Nr, vloc_r, d_vsum);
@@ -440,6 +538,8 @@ int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int
     rc = PWK_ERR_UNSUPPORTED;
     goto fail;
   }
+  TRYC(cudaDeviceSynchronize(), "plan setup");
+  for (int prec = 0; prec < 3; ++prec) TRY(autotune_shape(p, prec));
   TRYC(cudaDeviceSynchronize(), "plan setup");
   cudaFree(d_miller);
   cudaFree(d_B);

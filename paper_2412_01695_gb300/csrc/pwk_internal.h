@@ -61,7 +61,8 @@ struct pwk_plan {
   double* d_D = nullptr;
   float* d_D32 = nullptr;
   const double* d_V = nullptr;   // caller-owned
-  float* d_V32 = nullptr;
+  float* d_V32 = nullptr;         // transposed [l2][l3][l1]
+  double* d_Vt64 = nullptr;       // transposed [l2][l3][l1]
   double v_mean = 0.0;           // average of V over the grid (diagonal of the local term)
   pwk::SphereMap self;
   pwk::SphereMap xfer;           // from xfer_src's spheres to this plan's (DFPT rhs)
@@ -122,4 +123,8 @@ int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* i
              const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st);
 
 bool grid_supported(int N);
+int build_sphere_map(pwk_plan* p, SphereMap& sm, int nk, const int* npw_in, int npw_in_max,
+                     const int* miller_in, const int* npw_out, int npw_out_max,
+                     const int* miller_out, const int* d_npw_in, const int* d_npw_out);
+LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int nkb, int ctas_per_sm);
 }  // namespace pwk

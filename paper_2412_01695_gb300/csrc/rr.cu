@@ -1,0 +1,429 @@
+// Batched generalized Hermitian eigensolver for the Davidson reduced problem (paper Sec. 6):
+//   H~ v = eps S~ v,   n = N_base <= 160,   lowest nb eigenpairs, one CTA per k-point, FP64.
+//
+// The paper runs LAPACK ZHEGV(X) converted to device routines, one thread per k, with a
+// non-recursive Cholesky (ZPOTRF2 rewritten).  Here a whole CTA works on one k:
+//   1. Cholesky S~ = L L^H (right-looking, column by column);
+//   2. C = L^-1 H~ L^-H by two triangular solves (one thread per right-hand side);
+//   3. Householder reduction of C to a real symmetric tridiagonal T = Q^H C Q
+//      (reflectors H = I - tau v v^H, beta real, two-sided rank-2 updates);
+//   4. implicit QL iteration with Wilkinson shifts on T; thread 0 chases the bulge and
+//      records the Givens rotations of one sweep, every thread then applies them to one row
+//      of the eigenvector matrix Z (column-major, so a column is a coalesced access);
+//   5. the nb lowest eigenvalues are selected; their vectors are mapped back,
+//      x = L^-H Q z (reflectors applied in reverse order, then back substitution).
+// All matrices live in a per-k global workspace (L2-resident while the CTA works on it).
+// A non-positive pivot in step 1 marks the k-point with status PWK_ERR_NOT_POSDEF; an
+// eigenvalue that does not converge in 60 QL sweeps marks it PWK_ERR_NUMERIC.
+#include <cmath>
+
+#include "solvers.h"
+
+namespace pwk {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // conj(a) * b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+// block-wide sum of a double (all threads get the result)
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+__device__ double2 block_sum2(double2 v, double* red) {
+  return make_double2(block_sum(v.x, red), block_sum(v.y, red));
+}
+
+// Rayleigh-Ritz of every active k (active[k] != 0).
+// Hr, Sr: [nk][ld][ld] (row-major, full Hermitian in the leading n x n block)
+// W: [nk][3][ld][ld] workspace; ev: [nk][ld][nb]; eps: [nk][nb]; status [nk]
+// nbase == nullptr: every problem has size ld.  status may be null (not written).
+__global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const int* nbase,
+                                                 const int* active, const double2* Hr,
+                                                 const double2* Sr, double2* W, double2* ev,
+                                                 double* eps, int* status) {
+  const int k = blockIdx.x;
+  if (k >= nk || (active != nullptr && !active[k])) return;
+  const int n = nbase != nullptr ? nbase[k] : ld;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  __shared__ double red[32];
+  __shared__ double d[kMaxBasis], e[kMaxBasis], rc[kMaxBasis], rs[kMaxBasis];
+  __shared__ double2 tau[kMaxBasis];
+  __shared__ int rank[kMaxBasis];
+  __shared__ int flag, nrot, rot_lo, qstate;
+  __shared__ unsigned char dropped[kMaxBasis];
+  const size_t ldsq = (size_t)ld * ld;
+  const double2* H = Hr + k * ldsq;
+  const double2* S = Sr + k * ldsq;
+  double2* Lm = W + 3 * k * ldsq;     // Cholesky factor (lower), row-major
+  double2* X = Lm + ldsq;             // L^-1 H, then Z (real, column-major)
+  double2* C = X + ldsq;              // L^-1 H L^-H, then Householder vectors
+  if (tid == 0) flag = 0;
+  // ---- 1. Cholesky of S (lower).  A basis vector whose pivot falls below 1e-9 of its S~
+  //      diagonal is numerically dependent on the earlier ones: it is dropped (its row and
+  //      column of L become e_j and it is decoupled from the reduced problem below).
+  for (int i = tid; i < n * n; i += nth) {
+    const int r = i / n, c = i - r * n;
+    Lm[r * ld + c] = S[r * ld + c];
+  }
+  for (int i = tid; i < n; i += nth) dropped[i] = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid == 0) {
+      const double p = Lm[j * ld + j].x;
+      const bool drop = !(p > 1e-9 * S[j * ld + j].x);
+      dropped[j] = drop ? 1 : 0;
+      if (drop && j < nb) flag = 1;   // the leading nb vectors must be independent
+      Lm[j * ld + j] = make_double2(drop ? 1.0 : sqrt(p), 0.0);
+    }
+    __syncthreads();
+    if (dropped[j]) {
+      for (int r = j + 1 + tid; r < n; r += nth) Lm[r * ld + j] = make_double2(0.0, 0.0);
+      for (int q = tid; q < j; q += nth) Lm[j * ld + q] = make_double2(0.0, 0.0);
+      __syncthreads();
+      continue;
+    }
+    const double piv = Lm[j * ld + j].x;
+    for (int r = j + 1 + tid; r < n; r += nth) Lm[r * ld + j] = make_double2(Lm[r * ld + j].x / piv, Lm[r * ld + j].y / piv);
+    __syncthreads();
+    // trailing update, lower triangle: L[r][c] -= L[r][j] conj(L[c][j]), c <= r
+    const int m = n - j - 1;
+    for (int i = tid; i < m * m; i += nth) {
+      const int r = j + 1 + i / m, c = j + 1 + i % m;
+      if (c <= r) {
+        const double2 a = Lm[r * ld + j], b = Lm[c * ld + j];
+        const double2 t = cmul(a, cconj(b));
+        Lm[r * ld + c].x -= t.x;
+        Lm[r * ld + c].y -= t.y;
+      }
+    }
+    __syncthreads();
+  }
+  if (flag) {
+    if (tid == 0 && status != nullptr) status[k] = PWK_ERR_NOT_POSDEF;
+    return;
+  }
+  // ---- 2. X = L^-1 H (column c per thread), then C = L^-1 X^H (column c per thread)
+  for (int c = tid; c < n; c += nth) {
+    for (int r = 0; r < n; ++r) {
+      double2 s = H[r * ld + c];
+      for (int q = 0; q < r; ++q) {
+        const double2 t = cmul(Lm[r * ld + q], X[q * ld + c]);
+        s.x -= t.x;
+        s.y -= t.y;
+      }
+      const double l = Lm[r * ld + r].x;
+      X[r * ld + c] = make_double2(s.x / l, s.y / l);
+    }
+  }
+  __syncthreads();
+  for (int c = tid; c < n; c += nth) {
+    for (int r = 0; r < n; ++r) {
+      double2 s = cconj(X[c * ld + r]);   // (X^H)[r][c]
+      for (int q = 0; q < r; ++q) {
+        const double2 t = cmul(Lm[r * ld + q], C[q * ld + c]);
+        s.x -= t.x;
+        s.y -= t.y;
+      }
+      const double l = Lm[r * ld + r].x;
+      C[r * ld + c] = make_double2(s.x / l, s.y / l);
+    }
+  }
+  __syncthreads();
+  // symmetrise (C is Hermitian up to rounding)
+  for (int i = tid; i < n * n; i += nth) {
+    const int r = i / n, c = i - r * n;
+    if (c < r) {
+      const double2 a = C[r * ld + c], b = C[c * ld + r];
+      const double2 m = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
+      C[r * ld + c] = m;
+      C[c * ld + r] = cconj(m);
+    } else if (c == r) {
+      C[r * ld + c].y = 0.0;
+    }
+  }
+  __syncthreads();
+  // dropped vectors: decouple their row/column and park their eigenvalue above the spectrum
+  {
+    double f = 0.0;
+    for (int i = tid; i < n * n; i += nth) {
+      const int r = i / n, c = i - r * n;
+      const double2 v = C[r * ld + c];
+      f += v.x * v.x + v.y * v.y;
+    }
+    f = block_sum(f, red);
+    const double big = 4.0 * sqrt(f) + 1.0;
+    for (int i = tid; i < n * n; i += nth) {
+      const int r = i / n, c = i - r * n;
+      if (dropped[r] || dropped[c]) C[r * ld + c] = make_double2(r == c ? big : 0.0, 0.0);
+    }
+    __syncthreads();
+  }
+  // ---- 3. Householder tridiagonalisation; v_j stored in C[j+1..n-1][j] with v[0] = 1
+  double2* wv = X;   // w vector scratch (first column block of X, reused)
+  for (int j = 0; j + 1 < n; ++j) {
+    const int m = n - j - 1;       // length of x = C[j+1..n-1][j]
+    double xn2 = 0.0;
+    for (int i = 1 + tid; i < m; i += nth) {
+      const double2 v = C[(j + 1 + i) * ld + j];
+      xn2 += v.x * v.x + v.y * v.y;
+    }
+    xn2 = block_sum(xn2, red);
+    const double2 alpha = C[(j + 1) * ld + j];
+    double2 t = make_double2(0.0, 0.0);
+    double beta = alpha.x;
+    if (xn2 > 0.0 || alpha.y != 0.0) {
+      const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+      beta = alpha.x >= 0.0 ? -nrm : nrm;
+      t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+      // u = x / (alpha - beta)
+      const double2 den = make_double2(alpha.x - beta, alpha.y);
+      const double dd = den.x * den.x + den.y * den.y;
+      const double2 inv = make_double2(den.x / dd, -den.y / dd);
+      for (int i = 1 + tid; i < m; i += nth) {
+        const int r = j + 1 + i;
+        C[r * ld + j] = cmul(C[r * ld + j], inv);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      tau[j] = t;
+      e[j] = beta;
+      d[j] = C[j * ld + j].x;
+      C[(j + 1) * ld + j] = make_double2(1.0, 0.0);   // v[0] = 1
+    }
+    __syncthreads();
+    if (t.x != 0.0 || t.y != 0.0) {
+      // w = tau * C22 v  (C22 = C[j+1.., j+1..], full Hermitian)
+      for (int r = tid; r < m; r += nth) {
+        double2 s = make_double2(0.0, 0.0);
+        const double2* row = C + (size_t)(j + 1 + r) * ld + (j + 1);
+        for (int q = 0; q < m; ++q) {
+          const double2 a = row[q], v = C[(j + 1 + q) * ld + j];
+          s.x += a.x * v.x - a.y * v.y;
+          s.y += a.x * v.y + a.y * v.x;
+        }
+        wv[r] = cmul(t, s);
+      }
+      __syncthreads();
+      // alpha2 = -1/2 tau (w^H v)
+      double2 wv_dot = make_double2(0.0, 0.0);
+      for (int r = tid; r < m; r += nth) {
+        const double2 p = cmulc(wv[r], C[(j + 1 + r) * ld + j]);
+        wv_dot.x += p.x;
+        wv_dot.y += p.y;
+      }
+      wv_dot = block_sum2(wv_dot, red);
+      const double2 a2 = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), wv_dot);
+      for (int r = tid; r < m; r += nth) {
+        const double2 v = C[(j + 1 + r) * ld + j];
+        const double2 av = cmul(a2, v);
+        wv[r].x += av.x;
+        wv[r].y += av.y;
+      }
+      __syncthreads();
+      // C22 -= v w^H + w v^H
+      for (int i = tid; i < m * m; i += nth) {
+        const int r = i / m, c = i - r * m;
+        const double2 vr = C[(j + 1 + r) * ld + j], vc = C[(j + 1 + c) * ld + j];
+        const double2 a = cmul(vr, cconj(wv[c])), b = cmul(wv[r], cconj(vc));
+        double2& x = C[(size_t)(j + 1 + r) * ld + (j + 1 + c)];
+        x.x -= a.x + b.x;
+        x.y -= a.y + b.y;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    d[n - 1] = C[(n - 1) * ld + (n - 1)].x;
+    e[n - 1] = 0.0;
+  }
+  // ---- 4. implicit QL on (d, e); Z = I (real, column-major in X)
+  double* Z = reinterpret_cast<double*>(X);
+  for (int i = tid; i < n * n; i += nth) Z[i] = (i / n == i % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int l = 0; l < n; ++l) {
+    int iter = 0;
+    while (true) {
+      if (tid == 0) {
+        int m = l;
+        for (; m < n - 1; ++m) {
+          const double dd = fabs(d[m]) + fabs(d[m + 1]);
+          if (fabs(e[m]) + dd == dd) break;
+        }
+        nrot = 0;
+        rot_lo = m - 1;
+        if (m == l) {
+          qstate = 0;                       // d[l] is an eigenvalue
+        } else if (++iter > 60) {
+          qstate = 2;
+          flag = 2;
+        } else {
+          qstate = 1;
+          // shift from the leading 2x2 block of the unreduced part (Wilkinson)
+          double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+          double r = hypot(g, 1.0);
+          g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+          double s = 1.0, c = 1.0, p = 0.0;
+          bool early = false;
+          for (int i = m - 1; i >= l; --i) {
+            const double f = s * e[i], b = c * e[i];
+            r = hypot(f, g);
+            e[i + 1] = r;
+            if (r == 0.0) {   // exact split inside the chase
+              d[i + 1] -= p;
+              e[m] = 0.0;
+              early = true;
+              break;
+            }
+            s = f / r;
+            c = g / r;
+            g = d[i + 1] - p;
+            r = (d[i] - g) * s + 2.0 * c * b;
+            p = s * r;
+            d[i + 1] = g + p;
+            g = c * r - b;
+            rc[nrot] = c;          // rotation nrot acts on columns (m-1-nrot, m-nrot)
+            rs[nrot] = s;
+            ++nrot;
+          }
+          if (!early) {
+            d[l] -= p;
+            e[l] = g;
+            e[m] = 0.0;
+          }
+        }
+      }
+      __syncthreads();
+      const int st = qstate, nr = nrot, top = rot_lo;
+      // every thread has read the shared step state before thread 0 may write the next one
+      __syncthreads();
+      if (st != 1) break;
+      for (int row = tid; row < n; row += nth) {
+        for (int q = 0; q < nr; ++q) {
+          const int i = top - q;
+          const double c = rc[q], s = rs[q];
+          const double zi = Z[(size_t)i * n + row], zi1 = Z[(size_t)(i + 1) * n + row];
+          Z[(size_t)(i + 1) * n + row] = s * zi + c * zi1;
+          Z[(size_t)i * n + row] = c * zi - s * zi1;
+        }
+      }
+      __syncthreads();
+    }
+    if (flag == 2) break;
+  }
+  __syncthreads();
+  if (flag == 2) {
+    if (tid == 0 && status != nullptr) status[k] = PWK_ERR_NUMERIC;
+    return;
+  }
+  // ---- 5. select the nb lowest; back-transform x = L^-H Q z
+  for (int i = tid; i < n; i += nth) {
+    int r = 0;
+    for (int j = 0; j < n; ++j) r += (d[j] < d[i]) || (d[j] == d[i] && j < i);
+    rank[i] = r;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += nth)
+    if (rank[i] < nb) eps[k * nb + rank[i]] = d[i];
+  double2* E = ev + (size_t)k * ld * nb;
+  // one warp per selected vector
+  const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+  for (int i = 0; i < n; ++i) {
+    const int j = rank[i];
+    if (j >= nb || (i % nw) != warp) continue;
+    // y = z (real) in E[:, j]
+    for (int r = lane; r < n; r += 32) E[r * nb + j] = make_double2(Z[(size_t)i * n + r], 0.0);
+    __syncwarp();
+    // y = H_0 H_1 ... H_{n-2} y : apply H_{n-2} first
+    for (int h = n - 2; h >= 0; --h) {
+      const double2 th = tau[h];
+      if (th.x == 0.0 && th.y == 0.0) continue;
+      double2 s = make_double2(0.0, 0.0);   // v^H y over rows h+1..n-1
+      for (int r = h + 1 + lane; r < n; r += 32) {
+        const double2 p = cmulc(C[r * ld + h], E[r * nb + j]);
+        s.x += p.x;
+        s.y += p.y;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      const double2 ts = cmul(th, s);
+      for (int r = h + 1 + lane; r < n; r += 32) {
+        const double2 t = cmul(C[r * ld + h], ts);
+        E[r * nb + j].x -= t.x;
+        E[r * nb + j].y -= t.y;
+      }
+      __syncwarp();
+    }
+    // x = L^-H y: back substitution, x_r = (y_r - sum_{q>r} conj(L[q][r]) x_q) / L[r][r]
+    for (int r = n - 1; r >= 0; --r) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int q = r + 1 + lane; q < n; q += 32) {
+        const double2 p = cmulc(Lm[q * ld + r], E[q * nb + j]);
+        s.x += p.x;
+        s.y += p.y;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      }
+      if (lane == 0) {
+        const double l = Lm[r * ld + r].x;
+        E[r * nb + j] = make_double2((E[r * nb + j].x - s.x) / l, (E[r * nb + j].y - s.y) / l);
+      }
+      __syncwarp();
+    }
+  }
+  if (tid == 0 && status != nullptr) status[k] = PWK_OK;
+}
+
+int launch_rr(int nk, int ld, int nb, const int* nbase, const int* active, const double2* Hr,
+              const double2* Sr, double2* W, double2* ev, double* eps, int* status,
+              cudaStream_t st) {
+  rr_kernel<<<nk, 256, 0, st>>>(nk, ld, nb, nbase, active, Hr, Sr, W, ev, eps, status);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? PWK_OK : cuda_fail(e, "rr_kernel");
+}
+
+}  // namespace pwk
+
+using namespace pwk;
+
+// Batched generalized Hermitian eigensolver as a library entry point (workspace allocated
+// per call).
+extern "C" int pwk_eigh_batched(int nprob, int n, int nev, const void* H, const void* S,
+                                double* eig, void* vec, int* status, void* stream) {
+  if (nprob < 0 || n < 1 || nev < 1 || nev > n || (nprob > 0 && (H == nullptr || S == nullptr ||
+      eig == nullptr || vec == nullptr))) {
+    set_error("null pointer or bad size (need 1 <= nev <= n)");
+    return PWK_ERR_INVALID;
+  }
+  if (n > kMaxBasis) {
+    set_error("n > 160");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  if (nprob == 0) return PWK_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double2* W = nullptr;
+  cudaError_t e = cudaMalloc(&W, sizeof(double2) * 3 * (size_t)n * n * nprob);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(eigh workspace)");
+  int rc = launch_rr(nprob, n, nev, nullptr, nullptr, static_cast<const double2*>(H),
+                     static_cast<const double2*>(S), W, static_cast<double2*>(vec), eig, status, st);
+  e = cudaStreamSynchronize(st);
+  cudaFree(W);
+  if (rc) return rc;
+  return e == cudaSuccess ? PWK_OK : cuda_fail(e, "eigh");
+}

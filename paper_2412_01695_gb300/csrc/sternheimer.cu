@@ -1,0 +1,471 @@
+// Batched DFPT Sternheimer solver (paper Sec. 2.3-2.4, Algorithm 4): for every k of the
+// block and every occupied band n
+//   [H_{k+q} + alpha_k P_v - eps_{k,n}] x_{k,n} = b_{k,n} = -P_c dV psi_{k,n}
+// (Eq. linear_system with S = I, dS = 0; Eqs. projector, compute_mu, use_mu with S = I),
+// solved by the preconditioned CG of Eqs. ax1 .. updatedold for all (k, n) at once.
+//
+// Kernels (one CTA per (k, n) unless noted):
+//   rhs     : fused transfer kernel (inverse transform of psi_k on the k sphere, dv(r) u(r),
+//             forward transform gathered on the k+q sphere), then b = -(w - P_v w)
+//   aop     : mu_v = <psi_{k+q,v}|d> (Eq. compute_mu), y = sum_v psi_v mu_v (Eq. use_mu),
+//             t = H d - eps d + alpha y   (the H d part is the fused H|psi> kernel)
+//   cg_dir  : d = M^-1 r (Eq. row2), rho = Re<d|r> (Eq. row3), gamma (Eq. row4), d += gamma
+//             d_old (Eq. updated); ||r|| for the stopping test
+//   cg_step : lambda = -Re<d|r>/Re<d|t> (Eq. lambda), x += lambda d, r += lambda t,
+//             d_old = d, rho_old = rho (Eqs. updatex, updater, updatedold)
+// All vectors, dot products and scalars are FP64 and stay on the device; the host reads one
+// counter (pairs still iterating) per iteration.  Mixed mode: the H d inside the CG uses FP32
+// arithmetic and the solve is wrapped in FP64 iterative refinement (the CG restarts from the
+// true FP64 residual of the current x, each inner solve reducing it by 1e-4).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "solvers.h"
+
+namespace pwk {
+
+struct CgWork {
+  int nk = 0, nocc = 0, np = 0;
+  double2 *b = nullptr, *r = nullptr, *d = nullptr, *dold = nullptr, *t = nullptr;
+  double *rho = nullptr, *rho_old = nullptr, *bnorm = nullptr, *thr = nullptr, *tkin = nullptr;
+  double *rnorm = nullptr;
+  int *active = nullptr, *first = nullptr, *iters = nullptr, *items = nullptr, *counters = nullptr;
+  std::vector<void*> ptrs;
+};
+
+void destroy_cg_work(pwk_plan* p) {
+  if (p->cg == nullptr) return;
+  for (void* q : p->cg->ptrs) plan_free(p, q);
+  delete p->cg;
+  p->cg = nullptr;
+}
+
+template <typename T>
+static int calloc_(pwk_plan* p, CgWork* w, T** ptr, size_t n) {
+  int rc = plan_alloc(p, (void**)ptr, n * sizeof(T));
+  if (rc == PWK_OK) w->ptrs.push_back(*ptr);
+  return rc;
+}
+
+static int ensure_cg_work(pwk_plan* p, int nocc) {
+  if (p->cg && p->cg->nocc == nocc) return PWK_OK;
+  destroy_cg_work(p);
+  CgWork* w = new CgWork();
+  p->cg = w;
+  w->nk = p->nk;
+  w->nocc = nocc;
+  w->np = p->npw_max;
+  const size_t nv = (size_t)p->nk * nocc, nv2 = nv * p->npw_max;
+  int rc;
+  if ((rc = calloc_(p, w, &w->b, nv2)) || (rc = calloc_(p, w, &w->r, nv2)) ||
+      (rc = calloc_(p, w, &w->d, nv2)) || (rc = calloc_(p, w, &w->dold, nv2)) ||
+      (rc = calloc_(p, w, &w->t, nv2)) || (rc = calloc_(p, w, &w->rho, nv)) ||
+      (rc = calloc_(p, w, &w->rho_old, nv)) || (rc = calloc_(p, w, &w->bnorm, nv)) ||
+      (rc = calloc_(p, w, &w->thr, nv)) || (rc = calloc_(p, w, &w->tkin, nv)) ||
+      (rc = calloc_(p, w, &w->rnorm, nv)) || (rc = calloc_(p, w, &w->active, nv)) ||
+      (rc = calloc_(p, w, &w->first, nv)) || (rc = calloc_(p, w, &w->iters, nv)) ||
+      (rc = calloc_(p, w, &w->items, nv * 3)) || (rc = calloc_(p, w, &w->counters, 4))) {
+    destroy_cg_work(p);
+    return rc;
+  }
+  return PWK_OK;
+}
+
+// ------------------------------------------------------------------ kernels
+__device__ __forceinline__ double2 cmc(double2 a, double2 b) {  // conj(a) b
+  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__device__ double bsum2(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// out = a_u u + a_w w + a_p sum_v psi_v <psi_v|w>  for (k, n) with active (or all if null).
+// a_w = wmode ? -eps[k][n] : -1;  a_p = pmode ? alpha[k] : 1;  u may be null (a_u = 0).
+// The norm of out is written to onorm (if non-null).
+__global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, const int* npw,
+                                                           const int* active,
+                                                           const double2* psi_kq,
+                                                           const double2* u, const double2* w,
+                                                           int wmode, const double* eps,
+                                                           int pmode, const double* alpha,
+                                                           double2* out, double* onorm) {
+  const int k = blockIdx.x / nocc, n = blockIdx.x % nocc;
+  if (active != nullptr && !active[blockIdx.x]) return;
+  const int npk = npw[k];
+  __shared__ double2 mu[64];
+  __shared__ double red[32];
+  const double2* W = w + (size_t)blockIdx.x * np;
+  const double2* Pk = psi_kq + (size_t)k * nocc * np;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int v = warp; v < nocc; v += nw) {
+    double sx = 0, sy = 0;
+    const double2* pv = Pk + (size_t)v * np;
+    for (int g = lane; g < npk; g += 32) {
+      const double2 c = cmc(pv[g], W[g]);
+      sx += c.x;
+      sy += c.y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) mu[v] = make_double2(sx, sy);
+  }
+  __syncthreads();
+  const double aw = wmode ? -eps[blockIdx.x] : -1.0;
+  const double ap = pmode ? alpha[k] : 1.0;
+  const double2* U = u ? u + (size_t)blockIdx.x * np : nullptr;
+  double2* O = out + (size_t)blockIdx.x * np;
+  double nn = 0.0;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) {
+    if (g >= npk) {
+      O[g] = make_double2(0.0, 0.0);
+      continue;
+    }
+    double2 y = make_double2(0.0, 0.0);
+    for (int v = 0; v < nocc; ++v) {
+      const double2 p = Pk[(size_t)v * np + g], m = mu[v];
+      y.x += p.x * m.x - p.y * m.y;
+      y.y += p.x * m.y + p.y * m.x;
+    }
+    const double2 wg = W[g];
+    double2 o = make_double2(aw * wg.x + ap * y.x, aw * wg.y + ap * y.y);
+    if (U) {
+      o.x += U[g].x;
+      o.y += U[g].y;
+    }
+    nn += o.x * o.x + o.y * o.y;
+    O[g] = o;
+  }
+  nn = bsum2(nn, red);
+  if (onorm != nullptr && threadIdx.x == 0) onorm[blockIdx.x] = sqrt(nn);
+}
+
+// <psi_{k+q,n}|T|psi_{k+q,n}> / <psi|psi> for the preconditioner of Sec. 2.4
+__global__ void tkin_kernel(int nocc, int np, const int* npw, const double* g2, const double2* psi,
+                            double* tkin) {
+  const int k = blockIdx.x / nocc;
+  __shared__ double red[32];
+  const double2* P = psi + (size_t)blockIdx.x * np;
+  const double* G = g2 + (size_t)k * np;
+  double a = 0.0, b = 0.0;
+  for (int g = threadIdx.x; g < npw[k]; g += blockDim.x) {
+    const double m = P[g].x * P[g].x + P[g].y * P[g].y;
+    a += G[g] * m;
+    b += m;
+  }
+  a = bsum2(a, red);
+  b = bsum2(b, red);
+  if (threadIdx.x == 0) tkin[blockIdx.x] = b > 0.0 ? a / b : 1.0;
+}
+
+// r = t - b (or -b when t is null); relative norm; thresholds and activity for the inner solve
+__global__ void residual_kernel(int nocc, int np, const int* npw, const double2* t, const double2* b,
+                                const double* bnorm, double tol, double eta, double2* r,
+                                double* rnorm, double* thr, int* active, int* first,
+                                int* counters) {
+  const int i = blockIdx.x, k = i / nocc;
+  __shared__ double red[32];
+  const double2* T = t ? t + (size_t)i * np : nullptr;
+  const double2* B = b + (size_t)i * np;
+  double2* R = r + (size_t)i * np;
+  double nn = 0.0;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) {
+    double2 v = make_double2(-B[g].x, -B[g].y);
+    if (T && g < npw[k]) {
+      v.x += T[g].x;
+      v.y += T[g].y;
+    }
+    R[g] = v;
+    nn += v.x * v.x + v.y * v.y;
+  }
+  nn = bsum2(nn, red);
+  if (threadIdx.x == 0) {
+    const double rn = sqrt(nn), bn = bnorm[i];
+    rnorm[i] = bn > 0.0 ? rn / bn : 0.0;
+    const bool on = bn > 0.0 && rn > tol * bn;
+    active[i] = on ? 1 : 0;
+    first[i] = 1;
+    const double th = fmax(tol * bn, eta * rn);
+    thr[i] = th * th;
+    if (on) atomicAdd(&counters[0], 1);
+  }
+}
+
+// d = M^-1 r (+ gamma d_old); rho = Re<d|r>; stop when ||r||^2 <= thr
+__global__ void __launch_bounds__(256) cg_dir_kernel(int nocc, int np, const int* npw,
+                                                     const double* g2, const double* tkin,
+                                                     const double2* r, double2* d,
+                                                     const double2* dold, double* rho,
+                                                     const double* rho_old, const double* thr,
+                                                     int* active, int* first, int* counters) {
+  const int i = blockIdx.x, k = i / nocc;
+  if (!active[i]) return;
+  __shared__ double red[32];
+  const int npk = npw[k];
+  const double* G = g2 + (size_t)k * np;
+  const double tk = tkin[i];
+  const double2* R = r + (size_t)i * np;
+  double rr = 0.0, rh = 0.0;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    const double2 x = R[g];
+    const double m = fmax(1.0, G[g] / tk);
+    rr += x.x * x.x + x.y * x.y;
+    rh += (x.x * x.x + x.y * x.y) / m;   // Re<M^-1 r | r>
+  }
+  rr = bsum2(rr, red);
+  rh = bsum2(rh, red);
+  if (rr <= thr[i]) {
+    if (threadIdx.x == 0) active[i] = 0;
+    return;
+  }
+  const bool f = first[i] != 0;
+  const double gam = f ? 0.0 : rh / rho_old[i];
+  const double2* DO = dold + (size_t)i * np;
+  double2* D = d + (size_t)i * np;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) {
+    if (g >= npk) {
+      D[g] = make_double2(0.0, 0.0);
+      continue;
+    }
+    const double m = fmax(1.0, G[g] / tk);
+    double2 v = make_double2(R[g].x / m, R[g].y / m);
+    if (!f) {
+      v.x += gam * DO[g].x;
+      v.y += gam * DO[g].y;
+    }
+    D[g] = v;
+  }
+  if (threadIdx.x == 0) {
+    rho[i] = rh;
+    first[i] = 0;
+    atomicAdd(&counters[0], 1);
+  }
+}
+
+__global__ void cg_items_kernel(int n_pairs, int nocc, const int* active, int* items) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_pairs) return;
+  const bool on = active == nullptr || active[i] != 0;   // null: every pair
+  items[3 * i] = on ? i / nocc : -1;
+  items[3 * i + 1] = on ? i % nocc : 0;
+  items[3 * i + 2] = on ? i % nocc : 0;
+}
+
+// lambda = -Re<d|r>/Re<d|t>; x += lambda d; r += lambda t; d_old = d; rho_old = rho
+__global__ void __launch_bounds__(256) cg_step_kernel(int nocc, int np, const int* npw,
+                                                      int* active, const double2* d,
+                                                      const double2* t, double2* x, double2* r,
+                                                      double2* dold, const double* rho,
+                                                      double* rho_old, int* iters,
+                                                      int* counters) {
+  const int i = blockIdx.x, k = i / nocc;
+  if (!active[i]) return;
+  __shared__ double red[32];
+  const int npk = npw[k];
+  const double2* D = d + (size_t)i * np;
+  const double2* T = t + (size_t)i * np;
+  double2* R = r + (size_t)i * np;
+  double dr = 0.0, dt = 0.0;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    dr += D[g].x * R[g].x + D[g].y * R[g].y;
+    dt += D[g].x * T[g].x + D[g].y * T[g].y;
+  }
+  dr = bsum2(dr, red);
+  dt = bsum2(dt, red);
+  if (!(dt > 0.0) || !isfinite(dr)) {   // indefinite direction or breakdown: stop this pair
+    if (threadIdx.x == 0) {
+      active[i] = 0;
+      atomicOr(&counters[1], 1);
+    }
+    return;
+  }
+  const double lam = -dr / dt;
+  double2* X = x + (size_t)i * np;
+  double2* DO = dold + (size_t)i * np;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    const double2 dg = D[g], tg = T[g];
+    X[g].x += lam * dg.x;
+    X[g].y += lam * dg.y;
+    R[g].x += lam * tg.x;
+    R[g].y += lam * tg.y;
+    DO[g] = dg;
+  }
+  if (threadIdx.x == 0) {
+    rho_old[i] = rho[i];
+    iters[i] += 1;
+  }
+}
+
+static int nblk(size_t n, int t = 256) { return (int)((n + t - 1) / t); }
+
+#define KCK(what)                                      \
+  do {                                                 \
+    cudaError_t e_ = cudaGetLastError();               \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+}  // namespace pwk
+
+using namespace pwk;
+
+extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, const void* psi_k_v,
+                                          const double* eps_k, const void* psi_kq_v, int nocc,
+                                          const double* alpha, const void* dv_r, void* dpsi_v,
+                                          double tol, int max_iter, int* iters_out,
+                                          double* resid_out, void* stream) {
+  if (pq == nullptr || pk == nullptr || psi_k_v == nullptr || eps_k == nullptr ||
+      psi_kq_v == nullptr || alpha == nullptr || dv_r == nullptr || dpsi_v == nullptr ||
+      nocc < 1 || !(tol > 0.0) || max_iter < 1) {
+    set_error("null pointer, nocc < 1, tol <= 0 or max_iter < 1");
+    return PWK_ERR_INVALID;
+  }
+  if (mode != PWK_FP64 && mode != PWK_FP32_C128) {
+    set_error("mode must be PWK_FP64 or PWK_FP32_C128");
+    return PWK_ERR_INVALID;
+  }
+  if (nocc > 64) {
+    set_error("nocc > 64");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  if (pq->nk != pk->nk || pq->N != pk->N) {
+    set_error("plan_k and plan_kq must have the same nk and grid");
+    return PWK_ERR_INVALID;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  // transfer map k sphere -> k+q sphere (built once per pair of plans)
+  if (pq->xfer_src != pk) {
+    if (pq->xfer.d_nstick) {
+      plan_free(pq, pq->xfer.d_nstick);
+      plan_free(pq, pq->xfer.d_gin);
+      plan_free(pq, pq->xfer.d_gout);
+      plan_free(pq, pq->xfer.d_sid);
+      pq->xfer = SphereMap();
+      pq->xfer_src = nullptr;
+    }
+    rc = build_sphere_map(pq, pq->xfer, pq->nk, pk->h_npw.data(), pk->npw_max, pk->h_miller.data(),
+                          pq->h_npw.data(), pq->npw_max, pq->h_miller.data(), pk->d_npw, pq->d_npw);
+    if (rc) return rc;
+    pq->xshape = choose_shape(pq->N, 16, pq->xfer, 0, 1);
+    if (pq->xshape.smem > 227 * 1024) {
+      set_error("transfer kernel does not fit in shared memory");
+      return PWK_ERR_UNSUPPORTED;
+    }
+    pq->xfer_src = pk;
+  }
+  if ((rc = ensure_cg_work(pq, nocc))) return rc;
+  CgWork* w = pq->cg;
+  const int nk = pq->nk, np = pq->npw_max, npairs = nk * nocc;
+  const double2* psi_kq = static_cast<const double2*>(psi_kq_v);
+  double2* x = static_cast<double2*>(dpsi_v);
+  int hc[2] = {0, 0};
+  auto read_counters = [&]() -> int {
+    cudaError_t e = cudaMemcpyAsync(hc, w->counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return e == cudaSuccess ? PWK_OK : cuda_fail(e, "cg counters");
+  };
+
+  // ---- right-hand side: w = dV psi_k on the k+q sphere (into t), b = -(w - P_v w)
+  {
+    FusedArgs a;
+    a.in = psi_k_v;
+    a.out = w->t;
+    a.nvec_in = a.nvec_out = nocc;
+    a.nk = nk;
+    a.npw_in_max = pk->npw_max;
+    a.npw_out_max = np;
+    a.npw_in = pk->d_npw;
+    a.npw_out = pq->d_npw;
+    a.nstick = pq->xfer.d_nstick;
+    a.gin = pq->xfer.d_gin;
+    a.gout = pq->xfer.d_gout;
+    a.sid = pq->xfer.d_sid;
+    a.nstick_max = pq->xfer.nstick_max;
+    a.m1lo = pq->xfer.m1lo;
+    a.P = pq->xfer.P;
+    a.L = pq->xshape.L;
+    a.zs = (pq->N % 2 == 0) ? pq->N + 1 : pq->N;
+    a.V = dv_r;
+    a.scale = 1.0 / (double)pq->Nr;
+    a.err = pq->d_err;
+    if ((rc = launch_fused_xfer(pq->N, a, npairs, pq->xshape, st))) return rc;
+  }
+  proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, nullptr, w->t, 0,
+                                              nullptr, 0, nullptr, w->b, w->bnorm);
+  tkin_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, psi_kq, w->tkin);
+  cudaMemsetAsync(w->iters, 0, sizeof(int) * npairs, st);
+  cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)npairs * np, st);
+  KCK("sternheimer setup");
+
+  const int inner_prec = (mode == PWK_FP64) ? PWK_FP64 : PWK_FP32_C128;
+  const double eta = (mode == PWK_FP64) ? 0.0 : 1e-4;
+  bool x_zero = true;
+  for (int outer = 0; outer < 8; ++outer) {
+    cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
+    if (x_zero) {
+      residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, w->b, w->bnorm, tol, eta,
+                                              w->r, w->rnorm, w->thr, w->active, w->first, w->counters);
+    } else {
+      // t = H x (FP64) on every pair, then t = t - eps x + alpha P_v x, r = t - b
+      cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
+      if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st))) return rc;
+      proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, w->t, x, 1,
+                                                  eps_k, 1, alpha, w->t, nullptr);
+      residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, eta,
+                                              w->r, w->rnorm, w->thr, w->active, w->first, w->counters);
+    }
+    KCK("sternheimer residual");
+    if ((rc = read_counters())) return rc;
+    if (hc[0] == 0) break;
+    x_zero = false;
+    for (int it = 0; it < max_iter; ++it) {
+      cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
+      cg_dir_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, w->tkin, w->r, w->d, w->dold,
+                                            w->rho, w->rho_old, w->thr, w->active, w->first, w->counters);
+      KCK("cg_dir_kernel");
+      if ((rc = read_counters())) return rc;
+      if (hc[0] == 0) break;
+      cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->items);
+      if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, npairs, nocc, nocc, st))) return rc;
+      proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, psi_kq, w->t, w->d, 1,
+                                                  eps_k, 1, alpha, w->t, nullptr);
+      cg_step_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, w->d, w->t, x, w->r, w->dold,
+                                             w->rho, w->rho_old, w->iters, w->counters);
+      KCK("cg_step_kernel");
+    }
+  }
+  // final true residual with the FP64 operator
+  cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
+  {
+    cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
+    if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st))) return rc;
+    proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, w->t, x, 1, eps_k,
+                                                1, alpha, w->t, nullptr);
+    residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, 0.0, w->r,
+                                            w->rnorm, w->thr, w->active, w->first, w->counters);
+    KCK("sternheimer final residual");
+    std::vector<double> h_rn(npairs);
+    std::vector<int> h_it(npairs);
+    cudaError_t e = cudaMemcpyAsync(h_rn.data(), w->rnorm, sizeof(double) * npairs, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_it.data(), w->iters, sizeof(int) * npairs, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "sternheimer results");
+    if (resid_out) std::memcpy(resid_out, h_rn.data(), sizeof(double) * npairs);
+    if (iters_out) std::memcpy(iters_out, h_it.data(), sizeof(int) * npairs);
+    int above = 0;
+    for (double v : h_rn) above += (v > tol);
+    return above;
+  }
+}

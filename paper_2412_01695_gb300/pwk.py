@@ -19,9 +19,10 @@ PWK_FP64, PWK_FP32, PWK_FP32_C128 = 0, 1, 2
 PRECISIONS = {"fp64": PWK_FP64, "fp32": PWK_FP32, "fp32_c128": PWK_FP32_C128}
 
 # every symbol declared in include/pwk.h
-EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes", "pwk_supported_grid",
+EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
+           "pwk_plan_launch_shape", "pwk_supported_grid",
            "pwk_hpsi_batched", "pwk_hpsi_items", "pwk_davidson_batched",
-           "pwk_sternheimer_cg_batched", "pwk_strerror", "pwk_last_error_detail", "pwk_version")
+           "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_strerror", "pwk_last_error_detail", "pwk_version")
 
 _lib = None
 
@@ -44,12 +45,14 @@ def load(path: str = LIB_PATH):
                                  _P, _SZ]),
         "pwk_plan_destroy": (None, [_P]),
         "pwk_plan_device_bytes": (_SZ, [_P]),
+        "pwk_plan_launch_shape": (_I, [_P, _I, _P, _P, _P]),
         "pwk_supported_grid": (_I, [_I]),
         "pwk_hpsi_batched": (_I, [_P, _I, _P, _P, _I, _P]),
         "pwk_hpsi_items": (_I, [_P, _I, _P, _P, _P, _I, _I, _P]),
         "pwk_davidson_batched": (_I, [_P, _I, _P, _P, _I, _D, _D, _I, _I, _P, _P, _P, _P]),
         "pwk_sternheimer_cg_batched": (_I, [_P, _P, _I, _P, _P, _P, _I, _P, _P, _P, _D, _I, _P,
                                             _P, _P]),
+        "pwk_eigh_batched": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
         "pwk_strerror": (ctypes.c_char_p, [_I]),
         "pwk_last_error_detail": (ctypes.c_char_p, []),
         "pwk_version": (ctypes.c_char_p, []),
@@ -106,6 +109,13 @@ class Plan:
     @property
     def device_bytes(self) -> int:
         return int(load().pwk_plan_device_bytes(self.handle))
+
+    def launch_shape(self, precision: int):
+        """(threads per CTA, l3 chunk, shared memory bytes) chosen for a precision."""
+        t, l, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(load().pwk_plan_launch_shape(self.handle, precision, ctypes.byref(t), ctypes.byref(l),
+                                            ctypes.byref(sm)), "pwk_plan_launch_shape")
+        return t.value, l.value, sm.value
 
     def close(self):
         if self.handle:
@@ -188,6 +198,18 @@ def sternheimer_cg_batched(plan_kq: Plan, plan_k: Plan, mode: int, psi_k, eps_k,
                                       _stream(stream))
     _check(rc, "pwk_sternheimer_cg_batched")
     return rc, iters, resid
+
+
+def eigh_batched(H, S, nev: int, status=None, stream=None):
+    """pwk_eigh_batched on complex128 CUDA tensors H, S [nprob][n][n]; returns (eig, vec)."""
+    import torch
+    nprob, n = int(H.shape[0]), int(H.shape[1])
+    eig = torch.empty((nprob, nev), dtype=torch.float64, device=H.device)
+    vec = torch.empty((nprob, n, nev), dtype=torch.complex128, device=H.device)
+    _check(load().pwk_eigh_batched(nprob, n, nev, _ptr(H), _ptr(S), _ptr(eig), _ptr(vec),
+                                   _ptr(status) if status is not None else None,
+                                   _stream(stream)), "pwk_eigh_batched")
+    return eig, vec
 
 
 def supported_grid(N: int) -> bool:
