@@ -309,8 +309,8 @@ def run_solvers(dev, stream, quick=False):
     # Sternheimer on a block of the DFPT cell
     nk4 = 64 if quick else 256
     ks4 = list(range(nk4))
-    pk = synth.make_config(4, k_subset=ks4)
-    pq = synth.make_config(4, k_subset=ks4, shift_q=True)
+    pk = synth.make_config(4, k_subset=ks4, nb=16)
+    pq = synth.make_config(4, k_subset=ks4, shift_q=True, nb=16)
     plan_k = pwk.plan_from_problem(pk, device=dev)
     plan_q = pwk.plan_from_problem(pq, device=dev)
     nocc, nbx = 12, 16
@@ -344,24 +344,25 @@ def cpu_baseline(prob, gpu_out, budget_s=20.0):
     """The FP64 oracle (dense H per k) on the host cores, on a seeded sample of k-points."""
     from oracle import hamiltonian as ham
     from paper_2412_01695_gb300 import synth
-    ks = synth.sample_k(prob.nk, 32, seed=5)
     vt = ham.grid_coefficients(prob.V_r)
     t0 = time.perf_counter()
-    done = []
+    done = 0
     errs = []
-    for ik in ks:
+    checked = set(int(i) for i in synth.sample_k(prob.nk, 32, seed=5))
+    ik = 0
+    while time.perf_counter() - t0 < budget_s and done < 4 * prob.nk:
         ref = ham.hpsi_dense(prob, ik, prob.psi[ik], vt)
-        done.append(ik)
-        if gpu_out is not None:
+        if gpu_out is not None and ik in checked:
             n = prob.npw[ik]
             errs.append(float(np.max(ham.relative_error(gpu_out[ik][:, :n], ref[:, :n]))))
-        if time.perf_counter() - t0 > budget_s:
-            break
+            checked.discard(ik)
+        done += 1
+        ik = (ik + 1) % prob.nk
     dt = time.perf_counter() - t0
-    return {"value": len(done) * prob.nb / dt, "unit": UNIT, "cores": os.cpu_count(),
+    return {"value": done * prob.nb / dt, "unit": UNIT, "cores": os.cpu_count(),
             "kind": "oracle",
-            "sample": f"{len(done)} of {prob.nk} k-points x {prob.nb} bands (dense H(k) built from "
-                      f"direct Fourier sums, then H psi), {dt:.1f} s"}, errs
+            "sample": f"{done} k-point applications x {prob.nb} bands of the workload (dense FP64 H(k) "
+                      f"built from direct Fourier sums, then H psi), {dt:.1f} s"}, errs
 
 
 def run_reference(args):

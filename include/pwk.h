@@ -83,13 +83,19 @@ void pwk_plan_destroy(pwk_plan* plan);
 /* Device bytes currently held by the plan (tables + workspaces). */
 size_t pwk_plan_device_bytes(const pwk_plan* plan);
 
-/* Launch shape the plan chose for the fused H|psi> kernel of one precision (PWK_FP64,
- * PWK_FP32 or PWK_FP32_C128): threads per CTA, l3 planes per shared-memory chunk and the
- * dynamic shared memory per CTA.  pwk_plan_create times a few candidate shapes on the plan's
- * own k-points and keeps the fastest; every shape gives bitwise the same result.  Any output
- * pointer may be NULL. */
-int pwk_plan_launch_shape(const pwk_plan* plan, int precision, int* threads, int* l3_chunk,
-                          size_t* smem_bytes);
+/* Launch shape of the H|psi> kernel for one precision (PWK_FP64, PWK_FP32 or PWK_FP32_C128):
+ * kernel kind (0: general sphere kernel; 1: window kernel, usable when every |m_i| <= N/4),
+ * threads per CTA, l3 planes per shared-memory chunk and dynamic shared memory per CTA.
+ * pwk_plan_create times the candidate shapes on the plan's own k-points and keeps the
+ * fastest; every shape computes the same operator (bitwise the same result within a kind).
+ * Any output pointer may be NULL. */
+int pwk_plan_launch_shape(const pwk_plan* plan, int precision, int* kind, int* threads,
+                          int* l3_chunk, size_t* smem_bytes);
+
+/* Override the launch shape of one precision: kind 0 or 1, threads 128, 192 or 256,
+ * 1 <= l3_chunk <= N.  Returns PWK_ERR_UNSUPPORTED if the shape does not fit in shared
+ * memory or the window kernel does not apply to the plan (the shape is then unchanged). */
+int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threads, int l3_chunk);
 
 /* 1 if an N x N x N grid is supported by the fused kernels, else 0. */
 int pwk_supported_grid(int N);

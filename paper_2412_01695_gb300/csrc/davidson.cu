@@ -37,7 +37,7 @@ struct DavWork {
   double *eps = nullptr, *eps_new = nullptr, *hdiag = nullptr, *rnorm = nullptr;
   int *nbase = nullptr, *nnc = nullptr, *todo = nullptr, *active = nullptr, *moved = nullptr;
   int *restart = nullptr, *items = nullptr, *counters = nullptr, *iters = nullptr,
-      *status = nullptr, *failcount = nullptr, *force = nullptr;
+      *status = nullptr, *failcount = nullptr, *force = nullptr, *dbg = nullptr;
   std::vector<void*> ptrs;
 };
 
@@ -78,7 +78,7 @@ static int ensure_dav_work(pwk_plan* p, int nb, int MB) {
       (rc = dalloc(p, w, &w->restart, nk)) || (rc = dalloc(p, w, &w->items, nk * nb * 3)) ||
       (rc = dalloc(p, w, &w->counters, 4)) || (rc = dalloc(p, w, &w->iters, nk)) ||
       (rc = dalloc(p, w, &w->status, nk)) || (rc = dalloc(p, w, &w->failcount, nk)) ||
-      (rc = dalloc(p, w, &w->force, nk))) {
+      (rc = dalloc(p, w, &w->force, nk)) || (rc = dalloc(p, w, &w->dbg, 4))) {
     destroy_dav_work(p);
     return rc;
   }
@@ -366,7 +366,7 @@ __global__ void set_nbase_kernel(int nk, const int* only, int* nbase, int value,
 // given up (reported as an error by the next select).
 __global__ void update_kernel(int nk, int nb, double eth, int* active, int force_all,
                               const double* eps_new, double* eps, int* moved, const int* status,
-                              const int* added, int* nbase, int* force, int* failcount) {
+                              const int* added, int* nbase, int* force, int* failcount, int* dbg) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nk * nb) return;
   const int k = i / nb;
@@ -374,6 +374,11 @@ __global__ void update_kernel(int nk, int nb, double eth, int* active, int force
   if (status[k] != 0) {
     moved[i] = 1;
     if (i % nb == 0) {
+      if (atomicAdd(&dbg[0], 1) == 0) {   // first failure of the call: k, size, status
+        dbg[1] = k;
+        dbg[2] = nbase[k];
+        dbg[3] = status[k];
+      }
       if (added != nullptr) nbase[k] -= added[k];
       force[k] = 1;
       failcount[k] += 1;
@@ -384,6 +389,12 @@ __global__ void update_kernel(int nk, int nb, double eth, int* active, int force
   eps[i] = eps_new[i];
 }
 
+// phase switch: every k-point that has not been given up takes part again
+__global__ void reactivate_kernel(int nk, int* active, const int* failcount) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nk) active[k] = failcount[k] <= 3 ? 1 : 0;
+}
+
 __global__ void fill_int_kernel(int n, int* a, int v) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) a[i] = v;
@@ -392,8 +403,8 @@ __global__ void fill_int_kernel(int n, int* a, int v) {
 static int blocks(size_t n, int t = 256) { return (int)((n + t - 1) / t); }
 
 // Diagnostic: when the environment variable PWK_DUMP_RR names a directory, the reduced
-// H~ and S~ (leading n x n block, complex128, row-major) of a k-point whose reduced problem
-// failed are written there as rr_H_k<k>.bin and rr_S_k<k>.bin.
+// H~ and S~ (leading n x n block, complex128, row-major) of the first k-point whose reduced
+// problem failed in a call are written there as rr_H_k<k>.bin and rr_S_k<k>.bin.
 static void dump_reduced(const DavWork* w, int k, int n) {
   const char* dir = std::getenv("PWK_DUMP_RR");
   if (dir == nullptr || k < 0 || n <= 0 || n > w->MB) return;
@@ -459,7 +470,8 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   if (gram_smem > 48 * 1024)
     cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem);
   long long napply[2] = {0, 0};
-  int total = 0, given_up = 0, host_counters[4] = {0, 0, -1, 0};
+  int total = 0, given_up = 0, host_counters[4] = {0, 0, -1, 0}, host_dbg[4] = {0, 0, 0, 0};
+  bool dumped = false;
 
   hdiag_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>(nk, np, p->nkb, p->d_npw, p->d_g2, p->v_mean,
                                                         p->d_beta, p->d_D, w->hdiag);
@@ -470,6 +482,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, 0);
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->force, 0);
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->failcount, 0);
+  fill_int_kernel<<<1, 32, 0, st>>>(4, w->dbg, 0);
   copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi, MB, 0, nullptr);
   KCHECK("davidson init");
 
@@ -502,7 +515,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   if ((rc = start_block(prec, nullptr))) return rc;
   update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth_cur, w->active, 1, w->eps_new,
                                                          w->eps, w->moved, w->status, nullptr,
-                                                         w->nbase, w->force, w->failcount);
+                                                         w->nbase, w->force, w->failcount, w->dbg);
   KCHECK("update_kernel");
 
   int it = 0;
@@ -518,13 +531,17 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
                                               w->status, w->force, w->failcount, w->counters);
     KCHECK("select_kernel");
     cudaError_t ce = cudaMemcpyAsync(host_counters, w->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(host_dbg, w->dbg, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return cuda_fail(ce, "davidson counters");
+    if (host_dbg[0] > 0 && !dumped) {   // H~, S~ are still those of the failed eigensolve
+      dump_reduced(w, host_dbg[1], host_dbg[2]);
+      dumped = true;
+    }
     if (host_counters[1]) {
       given_up += host_counters[1];
       int nbk = -1;
       cudaMemcpy(&nbk, w->nbase + host_counters[2], sizeof(int), cudaMemcpyDeviceToHost);
-      dump_reduced(w, host_counters[2], nbk);
       char buf[200];
       std::snprintf(buf, sizeof(buf),
                     "k=%d given up after repeated reduced-problem failures (status %d: %s), "
@@ -542,7 +559,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
         prec = PWK_FP64;
         eth_cur = eth;
         rt_cur = res_tol;
-        fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, 1);
+        reactivate_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, w->failcount);
         rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi, w->tmp1, nb);
         copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, nullptr);
         KCHECK("refinement restart");
@@ -550,7 +567,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
         update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth_cur, w->active, 0,
                                                                w->eps_new, w->eps, w->moved,
                                                                w->status, nullptr, w->nbase,
-                                                               w->force, w->failcount);
+                                                               w->force, w->failcount, w->dbg);
         KCHECK("update_kernel");
         continue;
       }
@@ -581,7 +598,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       return rc;
     update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth_cur, w->active, 0, w->eps_new,
                                                            w->eps, w->moved, w->status, w->nnc,
-                                                           w->nbase, w->force, w->failcount);
+                                                           w->nbase, w->force, w->failcount, w->dbg);
     KCHECK("update_kernel");
   }
   // eigenvectors out: psi = phi v; eigenvalues out

@@ -1,0 +1,241 @@
+// Window-specialised fused H|psi> kernel.
+//
+// Same operator and the same one-HBM-round-trip structure as fused_kernel (paper Sec. 2.2 and
+// Sec. 5; see fused_kernel.cuh), for spheres whose Miller indices all satisfy |m_i| <= W with
+// W = N/4: a grid chosen to hold the differences G - G' of the basis (Sec. 5: "N_i large
+// enough"), N >= 4 max|m|, always satisfies it.  With the window known at compile time:
+//   * the z-sticks live in a dense (2W+1) x (2W+1) square of rows [m1][m2] (rows without a
+//     stick of this k stay zero), so the y pass reads and writes them without a stick table;
+//   * every transform reads only the 2W+1 window inputs (the others are literal zeros) and
+//     stores only the outputs that are used later; no per-element index arithmetic or
+//     predicated shared-memory access remains.
+// The real sticks of the k-point (for the z passes) and the packed (row, m3) place of every
+// basis vector come from the plan's window tables.
+#pragma once
+#include <type_traits>
+
+#include "fft_line.cuh"
+#include "fused_kernel.cuh"
+#include "pwk_internal.h"
+
+namespace pwk {
+
+template <int N, int W>
+struct Win {
+  static constexpr int NW = 2 * W + 1;
+  __host__ __device__ static constexpr bool in(int i) { return i <= W || i >= N - W; }
+  __host__ __device__ static constexpr int idx(int i) { return i <= W ? i + W : i - N + W; }  // 0 .. 2W
+};
+
+template <typename T, typename TI, int N, int W>
+__global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
+  using V = c2_t<T>;
+  using VI = c2_t<TI>;
+  using Wn = Win<N, W>;
+  constexpr int NW = Wn::NW;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+
+  const int item = blockIdx.x;
+  if (a.d_count != nullptr && item >= *a.d_count) return;
+  int k, vin, vout;
+  if (a.items != nullptr) {
+    k = a.items[3 * item];
+    vin = a.items[3 * item + 1];
+    vout = a.items[3 * item + 2];
+    if (k == -1) return;
+    if (k < 0 || k >= a.nk || vin < 0 || vin >= a.nvec_in || vout < 0 || vout >= a.nvec_out) {
+      if (threadIdx.x == 0 && a.err != nullptr) atomicOr(a.err, 1);
+      return;
+    }
+  } else {
+    k = item / a.nvec_in;
+    vin = vout = item - k * a.nvec_in;
+  }
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int np = a.npw_in[k];
+  const int ns = a.nstick[k];
+  const int zs = a.zs, L = a.L;
+
+  V* Z = reinterpret_cast<V*>(smem_raw);               // [NW*NW][zs]
+  V* Y = Z + (size_t)NW * NW * zs;                      // [NW][N][L]
+  V* psis = Y + (size_t)NW * N * L;                     // [npw_max]
+  V* lam = psis + a.npw_in_max;
+  V* gam = lam + a.nkb;
+  short* rows = reinterpret_cast<short*>(gam + a.nkb);  // [nstick_max]
+
+  const VI* pin = static_cast<const VI*>(a.in) + ((size_t)k * a.nvec_in + vin) * a.npw_in_max;
+  VI* pout = static_cast<VI*>(a.out) + ((size_t)k * a.nvec_out + vout) * a.npw_out_max;
+
+  // ---- 0: zero the stick square, stage the stick rows and C(G)
+  for (int i = tid; i < NW * NW * zs; i += nth) Z[i] = V{T(0), T(0)};
+  {
+    const short* rk = a.sid + (size_t)k * a.nstick_max;
+    for (int i = tid; i < ns; i += nth) rows[i] = rk[i];
+  }
+  for (int g = tid; g < np; g += nth) {
+    VI v = pin[g];
+    psis[g] = V{T(v.x), T(v.y)};
+  }
+  __syncthreads();
+
+  // ---- 1: scatter; projections lambda (Eq. lambdah)
+  {
+    const int* gin = a.gin + (size_t)k * a.npw_in_max;
+    for (int g = tid; g < np; g += nth) {
+      const int m = gin[g];
+      Z[(m >> 8) * zs + (m & 255)] = psis[g];
+    }
+  }
+  if (a.nkb > 0) {
+    const V* bk = static_cast<const V*>(a.beta) + (size_t)k * a.nkb * a.npw_out_max;
+    const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+    for (int i = warp; i < a.nkb; i += nw) {
+      T sr = T(0), si = T(0);
+      const V* bi = bk + (size_t)i * a.npw_out_max;
+      for (int g = lane; g < np; g += 32) {
+        const V b = bi[g], c = psis[g];
+        sr += b.x * c.x + b.y * c.y;
+        si += b.x * c.y - b.y * c.x;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        sr += __shfl_xor_sync(0xffffffffu, sr, o);
+        si += __shfl_xor_sync(0xffffffffu, si, o);
+      }
+      if (lane == 0) lam[i] = V{sr, si};
+    }
+  }
+  __syncthreads();
+
+  // ---- 2: inverse z transforms of the real sticks (inputs only in the m3 window)
+  for (int s = tid; s < ns; s += nth) {
+    V x[N];
+    V* zr = Z + rows[s] * zs;
+    PWK_SFOR(N, j, x[j] = Wn::in(j) ? zr[j] : V{T(0), T(0)});
+    LineFFT<T, N, +1>::run(x);
+    PWK_SFOR(N, j, zr[j] = x[OutSlot<N, j>::value]);
+  }
+  for (int i = tid; i < a.nkb; i += nth) {
+    const T* Dm = static_cast<const T*>(a.D) + (size_t)i * a.nkb;
+    T gr = T(0), gi = T(0);
+    for (int j = 0; j < a.nkb; ++j) {
+      const T d = Dm[j];
+      gr += d * lam[j].x;
+      gi += d * lam[j].y;
+    }
+    gam[i] = V{gr, gi};
+  }
+  __syncthreads();
+
+  // ---- 3: planes l3 in chunks of L
+  for (int l0 = 0; l0 < N; l0 += L) {
+    const int lc = min(L, N - l0);
+    // 3a: inverse y transforms, inputs on the m2 window of plane p
+    for (int t = tid; t < NW * lc; t += nth) {
+      const int p = t / lc, c = t - p * lc;
+      V x[N];
+      const V* zp = Z + (size_t)p * NW * zs + l0 + c;
+      PWK_SFOR(N, j, x[j] = Wn::in(j) ? zp[Wn::idx(j) * zs] : V{T(0), T(0)});
+      LineFFT<T, N, +1>::run(x);
+      V* yp = Y + (size_t)p * N * L + c;
+      PWK_SFOR(N, l2, yp[l2 * L] = x[OutSlot<N, l2>::value]);
+    }
+    __syncthreads();
+    // 3b: x lines: inverse x, V(r) product, forward x (window outputs only)
+    for (int t = tid; t < N * lc; t += nth) {
+      const int l2 = t / lc, c = t - l2 * lc;
+      V x[N];
+      const V* yl = Y + (size_t)l2 * L + c;
+      PWK_SFOR(N, i, x[i] = Wn::in(i) ? yl[(size_t)Wn::idx(i) * N * L] : V{T(0), T(0)});
+      LineFFT<T, N, +1>::run(x);
+      T w[N];
+      load_vline<T, N>(static_cast<const T*>(a.V) + ((size_t)l2 * N + l0 + c) * N, w);
+      V y[N];
+      PWK_SFOR(N, l1, {
+        const V u = x[OutSlot<N, l1>::value];
+        y[l1] = V{u.x * w[l1], u.y * w[l1]};
+      });
+      LineFFT<T, N, -1>::run(y);
+      V* yo = Y + (size_t)l2 * L + c;
+      PWK_SFOR(N, i, {
+        if constexpr (Wn::in(i)) yo[(size_t)Wn::idx(i) * N * L] = y[OutSlot<N, i>::value];
+      });
+    }
+    __syncthreads();
+    // 3c: forward y transforms, window outputs written back to the stick square
+    for (int t = tid; t < NW * lc; t += nth) {
+      const int p = t / lc, c = t - p * lc;
+      V x[N];
+      const V* yp = Y + (size_t)p * N * L + c;
+      PWK_SFOR(N, l2, x[l2] = yp[l2 * L]);
+      LineFFT<T, N, -1>::run(x);
+      V* zp = Z + (size_t)p * NW * zs + l0 + c;
+      PWK_SFOR(N, j, {
+        if constexpr (Wn::in(j)) zp[Wn::idx(j) * zs] = x[OutSlot<N, j>::value];
+      });
+    }
+    __syncthreads();
+  }
+
+  // ---- 4: forward z transforms of the real sticks (window outputs only)
+  for (int s = tid; s < ns; s += nth) {
+    V x[N];
+    V* zr = Z + rows[s] * zs;
+    PWK_SFOR(N, j, x[j] = zr[j]);
+    LineFFT<T, N, -1>::run(x);
+    PWK_SFOR(N, j, {
+      if constexpr (Wn::in(j)) zr[j] = x[OutSlot<N, j>::value];
+    });
+  }
+  __syncthreads();
+
+  // ---- 5: gather with 1/N_r; kinetic and nonlocal add-back (Eq. finalnl)
+  {
+    const int* gout = a.gout + (size_t)k * a.npw_out_max;
+    const T sc = T(a.scale);
+    const double* g2k = a.g2 + (size_t)k * a.npw_out_max;
+    const V* bk = static_cast<const V*>(a.beta) + (size_t)k * a.nkb * a.npw_out_max;
+    for (int g = tid; g < np; g += nth) {
+      const int m = gout[g];
+      const V z = Z[(m >> 8) * zs + (m & 255)];
+      const T t2 = T(g2k[g]);
+      V acc = V{z.x * sc + t2 * psis[g].x, z.y * sc + t2 * psis[g].y};
+      for (int i = 0; i < a.nkb; ++i) {
+        const V b = bk[(size_t)i * a.npw_out_max + g];
+        const V c = gam[i];
+        acc.x += c.x * b.x - c.y * b.y;
+        acc.y += c.x * b.y + c.y * b.x;
+      }
+      pout[g] = VI{TI(acc.x), TI(acc.y)};
+    }
+    for (int g = np + tid; g < a.npw_out_max; g += nth) pout[g] = VI{TI(0), TI(0)};
+  }
+}
+
+// window half-width instantiated for a grid of size N
+__host__ __device__ constexpr int window_of(int N) { return N / 4; }
+
+template <typename T, typename TI>
+int launch_window(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {
+  if (nblocks <= 0) return PWK_OK;
+  switch (N) {
+#define PWK_WCASE(n)                                                                            \
+  case n: {                                                                                     \
+    auto kern = fused_window_kernel<T, TI, n, window_of(n)>;                                    \
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                         (int)s.smem);                                          \
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(window)");                  \
+    kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \
+    e = cudaGetLastError();                                                                     \
+    if (e != cudaSuccess) return cuda_fail(e, "window kernel launch");                          \
+    return PWK_OK;                                                                              \
+  }
+    PWK_FOR_EACH_N(PWK_WCASE)
+#undef PWK_WCASE
+    default:
+      set_error("unsupported grid size");
+      return PWK_ERR_UNSUPPORTED;
+  }
+}
+
+}  // namespace pwk

@@ -78,6 +78,13 @@ size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int
   return elems * elem_bytes + (size_t)P * N * sizeof(short) + 16;
 }
 
+size_t window_smem_bytes(int N, int elem_bytes, int L, int npw_max, int nkb, int nstick_max) {
+  const int W = N / 4, NW = 2 * W + 1;
+  const int zs = (N % 2 == 0) ? N + 1 : N;
+  size_t elems = (size_t)NW * NW * zs + (size_t)NW * N * L + npw_max + 2 * (size_t)nkb;
+  return elems * elem_bytes + (size_t)nstick_max * sizeof(short) + 16;
+}
+
 // ---------------------------------------------------------------- setup kernels
 // |k+G|^2 (Ry) for every basis vector of every k (paper Sec. 2.2.1), zero padding.
 __global__ void kinetic_table_kernel(int nk, int npw_max, const int* npw, const double* kc,
@@ -110,18 +117,18 @@ __global__ void transpose_v_kernel(int N, const double* V, T* Vt) {
   Vt[i] = (T)V[((size_t)l1 * N + l2) * N + l3];
 }
 
+// sum of n values by one CTA in a fixed order (the result is the same on every run)
 __global__ void sum_kernel(size_t n, const double* in, double* out) {
   __shared__ double sh[256];
   double s = 0.0;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    s += in[i];
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) s += in[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) atomicAdd(out, sh[0]);
+  if (threadIdx.x == 0) *out = sh[0];
 }
 
 static int blocks_for(size_t n, int t = 256) { return (int)((n + t - 1) / t); }
@@ -222,6 +229,42 @@ int build_sphere_map(pwk_plan* p, SphereMap& sm, int nk, const int* npw_in, int 
   return PWK_OK;
 }
 
+// Tables of the window-specialised kernel: every Miller index of the plan within
+// |m_i| <= W = N/4; the sticks of a k live at rows (m1+W)(2W+1) + (m2+W) of a dense square.
+int build_window_tables(pwk_plan* p) {
+  const int N = p->N, W = N / 4, NW = 2 * W + 1, nk = p->nk, np = p->npw_max;
+  for (size_t i = 0; i < p->h_miller.size(); ++i) {
+    const int g = (int)((i / 3) % np), k = (int)(i / 3 / np);
+    if (g < p->h_npw[k] && std::abs(p->h_miller[i]) > W) return PWK_OK;   // not eligible
+  }
+  const int nsm = p->self.nstick_max;
+  std::vector<int> gm((size_t)nk * np, 0);
+  std::vector<short> rows((size_t)nk * nsm, (short)0);
+  for (int k = 0; k < nk; ++k) {
+    std::vector<char> seen((size_t)NW * NW, 0);
+    int c = 0;
+    for (int g = 0; g < p->h_npw[k]; ++g) {
+      const int* m = &p->h_miller[((size_t)k * np + g) * 3];
+      const int row = (m[0] + W) * NW + (m[1] + W);
+      gm[(size_t)k * np + g] = (row << 8) | (((m[2] % N) + N) % N);
+      if (!seen[row]) {
+        seen[row] = 1;
+        if (c >= nsm) return PWK_OK;   // cannot happen: same stick count as the self map
+        rows[(size_t)k * nsm + c++] = (short)row;
+      }
+    }
+  }
+  int rc;
+  if ((rc = plan_alloc(p, (void**)&p->d_wgmap, sizeof(int) * gm.size()))) return rc;
+  if ((rc = plan_alloc(p, (void**)&p->d_wrows, sizeof(short) * rows.size()))) return rc;
+  cudaError_t e;
+  if ((e = cudaMemcpy(p->d_wgmap, gm.data(), sizeof(int) * gm.size(), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(p->d_wrows, rows.data(), sizeof(short) * rows.size(), cudaMemcpyHostToDevice)))
+    return cuda_fail(e, "cudaMemcpy(window tables)");
+  p->window_ok = true;
+  return PWK_OK;
+}
+
 // Launch shape: the largest l3 chunk that keeps two CTAs per SM (FP64: one) within the
 // 227 KB of shared memory per CTA, threads 256.
 LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int nkb, int ctas_per_sm) {
@@ -243,10 +286,29 @@ LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int nkb, in
 
 static int launch_variant(int precision, int N, const FusedArgs& a, int nblocks,
                           const LaunchShape& s, cudaStream_t st) {
+  if (s.kind == 1) {
+    switch (precision) {
+      case PWK_FP64: return launch_window_f64(N, a, nblocks, s, st);
+      case PWK_FP32: return launch_window_f32(N, a, nblocks, s, st);
+      default: return launch_window_f32c128(N, a, nblocks, s, st);
+    }
+  }
   switch (precision) {
     case PWK_FP64: return launch_fused_f64(N, a, nblocks, s, st);
     case PWK_FP32: return launch_fused_f32(N, a, nblocks, s, st);
     default: return launch_fused_f32c128(N, a, nblocks, s, st);
+  }
+}
+
+// Point the kernel arguments at the tables of the chosen kernel kind.
+static void use_kind(const pwk_plan* p, FusedArgs& a, int kind) {
+  if (kind == 1) {
+    a.gin = a.gout = p->d_wgmap;
+    a.sid = p->d_wrows;
+  } else {
+    a.gin = p->self.d_gin;
+    a.gout = p->self.d_gout;
+    a.sid = p->self.d_sid;
   }
 }
 
@@ -260,16 +322,19 @@ int autotune_shape(pwk_plan* p, int precision) {
   const int io_elem = precision == PWK_FP32 ? 8 : 16;
   std::vector<LaunchShape> cands;
   const int Ls[3] = {N, (N + 1) / 2, (N + 2) / 3};
-  for (int T : {128, 192, 256})
-    for (int li = 0; li < 3; ++li) {
-      const int L = Ls[li];
-      if (li > 0 && L == Ls[li - 1]) continue;
-      LaunchShape c;
-      c.threads = T;
-      c.L = L;
-      c.smem = fused_smem_bytes(N, elem, p->self.nstick_max, p->self.P, L, p->npw_max, p->nkb);
-      if (c.smem <= 227 * 1024) cands.push_back(c);
-    }
+  for (int kind = 0; kind < (p->window_ok ? 2 : 1); ++kind)
+    for (int T : {128, 192, 256})
+      for (int li = 0; li < 3; ++li) {
+        const int L = Ls[li];
+        if (li > 0 && L == Ls[li - 1]) continue;
+        LaunchShape c;
+        c.kind = kind;
+        c.threads = T;
+        c.L = L;
+        c.smem = kind == 1 ? window_smem_bytes(N, elem, L, p->npw_max, p->nkb, p->self.nstick_max)
+                           : fused_smem_bytes(N, elem, p->self.nstick_max, p->self.P, L, p->npw_max, p->nkb);
+        if (c.smem <= 227 * 1024) cands.push_back(c);
+      }
   if (cands.empty()) return PWK_OK;   // the default shape stands (plan creation checked it)
   const int nv = 8, nkt = std::min(p->nk, 192);
   const size_t bytes = (size_t)nkt * nv * p->npw_max * io_elem;
@@ -289,6 +354,7 @@ int autotune_shape(pwk_plan* p, int precision) {
   LaunchShape pick = p->shape[precision];
   for (const LaunchShape& c : cands) {
     a.L = c.L;
+    use_kind(p, a, c.kind);
     if (launch_variant(precision, N, a, nkt * nv, c, 0) != PWK_OK) {
       cudaGetLastError();
       continue;
@@ -354,12 +420,12 @@ int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* i
   a.d_count = d_count;
   a.nvec_in = nvec_in;
   a.nvec_out = nvec_out;
-  switch (precision) {
-    case PWK_FP64: return launch_fused_f64(p->N, a, nblocks, p->shape[0], st);
-    case PWK_FP32: return launch_fused_f32(p->N, a, nblocks, p->shape[1], st);
-    case PWK_FP32_C128: return launch_fused_f32c128(p->N, a, nblocks, p->shape[2], st);
-    default: set_error("unknown precision"); return PWK_ERR_INVALID;
+  if (precision < 0 || precision > 2) {
+    set_error("unknown precision");
+    return PWK_ERR_INVALID;
   }
+  use_kind(p, a, p->shape[precision].kind);
+  return launch_variant(precision, p->N, a, nblocks, p->shape[precision], st);
 }
 
 }  // namespace pwk
@@ -390,12 +456,40 @@ const char* pwk_strerror(int code) {
 
 size_t pwk_plan_device_bytes(const pwk_plan* p) { return p ? p->bytes : 0; }
 
-int pwk_plan_launch_shape(const pwk_plan* p, int precision, int* threads, int* l3_chunk,
-                          size_t* smem_bytes) {
+int pwk_plan_set_launch_shape(pwk_plan* p, int precision, int kind, int threads, int l3_chunk) {
+  if (p == nullptr || precision < 0 || precision > 2 || kind < 0 || kind > 1 ||
+      (threads != 128 && threads != 192 && threads != 256) || l3_chunk < 1 || l3_chunk > p->N) {
+    set_error("bad plan, precision, kind (0/1), threads (128/192/256) or l3 chunk (1..N)");
+    return PWK_ERR_INVALID;
+  }
+  if (kind == 1 && !p->window_ok) {
+    set_error("the window kernel needs every |m_i| <= N/4");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  const int elem = precision == PWK_FP64 ? 16 : 8;
+  LaunchShape c;
+  c.kind = kind;
+  c.threads = threads;
+  c.L = l3_chunk;
+  c.smem = kind == 1 ? window_smem_bytes(p->N, elem, l3_chunk, p->npw_max, p->nkb, p->self.nstick_max)
+                     : fused_smem_bytes(p->N, elem, p->self.nstick_max, p->self.P, l3_chunk, p->npw_max,
+                                        p->nkb);
+  if (c.smem > 227 * 1024) {
+    set_error("shape needs more than 227 KB of shared memory");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  p->shape[precision] = c;
+  return PWK_OK;
+}
+
+int pwk_plan_launch_shape(const pwk_plan* p, int precision, int* kind, int* threads,
+                          int* l3_chunk, size_t* smem_bytes) {
   if (p == nullptr || precision < 0 || precision > 2) {
     set_error("null plan or unknown precision");
     return PWK_ERR_INVALID;
   }
+
+  if (kind) *kind = p->shape[precision].kind;
   if (threads) *threads = p->shape[precision].threads;
   if (l3_chunk) *l3_chunk = p->shape[precision].L;
   if (smem_bytes) *smem_bytes = p->shape[precision].smem;
@@ -525,7 +619,7 @@ int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int
   TRYC(cudaGetLastError(), "V transpose");
   TRYC(cudaMalloc(&d_vsum, sizeof(double)), "cudaMalloc(tmp)");
   TRYC(cudaMemset(d_vsum, 0, sizeof(double)), "cudaMemset");
-  sum_kernel<<<64, 256>>>((size_t)p->Nr, vloc_r, d_vsum);
+  sum_kernel<<<1, 256>>>((size_t)p->Nr, vloc_r, d_vsum);
   TRYC(cudaGetLastError(), "sum_kernel");
   TRYC(cudaMemcpy(&p->v_mean, d_vsum, sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy(vsum)");
   p->v_mean /= (double)p->Nr;
@@ -538,6 +632,7 @@ int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int
     rc = PWK_ERR_UNSUPPORTED;
     goto fail;
   }
+  TRY(build_window_tables(p));
   TRYC(cudaDeviceSynchronize(), "plan setup");
   for (int prec = 0; prec < 3; ++prec) TRY(autotune_shape(p, prec));
   TRYC(cudaDeviceSynchronize(), "plan setup");

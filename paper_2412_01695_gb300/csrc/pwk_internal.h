@@ -33,6 +33,7 @@ struct SphereMap {
 
 // Launch shape of the fused kernel for one precision.
 struct LaunchShape {
+  int kind = 0;         // 0: generic fused kernel, 1: window-specialised kernel
   int threads = 256;
   int L = 0;            // l3 planes per chunk of the y/x passes
   size_t smem = 0;
@@ -65,6 +66,10 @@ struct pwk_plan {
   double* d_Vt64 = nullptr;       // transposed [l2][l3][l1]
   double v_mean = 0.0;           // average of V over the grid (diagonal of the local term)
   pwk::SphereMap self;
+  // window-specialised kernel tables (|m_i| <= (N-1)/4 on every sphere of the plan)
+  bool window_ok = false;
+  int* d_wgmap = nullptr;        // [nk][npw_max] (row << 8) | (m3 mod N), row = (m1+W)(2W+1)+(m2+W)
+  short* d_wrows = nullptr;      // [nk][nstick_max] rows of the real sticks
   pwk::SphereMap xfer;           // from xfer_src's spheres to this plan's (DFPT rhs)
   const pwk_plan* xfer_src = nullptr;
   pwk::LaunchShape shape[3];     // per precision
@@ -116,6 +121,11 @@ int launch_fused_f32(int N, const FusedArgs& a, int nblocks, const LaunchShape& 
 int launch_fused_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchShape& s,
                          cudaStream_t st);
 int launch_fused_xfer(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_window_f64(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_window_f32(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_window_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchShape& s,
+                          cudaStream_t st);
+size_t window_smem_bytes(int N, int elem_bytes, int L, int npw_max, int nkb, int nstick_max);
 
 // fill FusedArgs for H|psi> with this plan
 FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out);

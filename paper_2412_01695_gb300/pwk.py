@@ -20,7 +20,7 @@ PRECISIONS = {"fp64": PWK_FP64, "fp32": PWK_FP32, "fp32_c128": PWK_FP32_C128}
 
 # every symbol declared in include/pwk.h
 EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
-           "pwk_plan_launch_shape", "pwk_supported_grid",
+           "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_supported_grid",
            "pwk_hpsi_batched", "pwk_hpsi_items", "pwk_davidson_batched",
            "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_strerror", "pwk_last_error_detail", "pwk_version")
 
@@ -45,7 +45,8 @@ def load(path: str = LIB_PATH):
                                  _P, _SZ]),
         "pwk_plan_destroy": (None, [_P]),
         "pwk_plan_device_bytes": (_SZ, [_P]),
-        "pwk_plan_launch_shape": (_I, [_P, _I, _P, _P, _P]),
+        "pwk_plan_launch_shape": (_I, [_P, _I, _P, _P, _P, _P]),
+        "pwk_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
         "pwk_supported_grid": (_I, [_I]),
         "pwk_hpsi_batched": (_I, [_P, _I, _P, _P, _I, _P]),
         "pwk_hpsi_items": (_I, [_P, _I, _P, _P, _P, _I, _I, _P]),
@@ -102,20 +103,26 @@ def _np_ptr(a: np.ndarray):
 class Plan:
     """Owns a pwk_plan*; keeps the caller-owned device arrays (beta, V) alive."""
 
-    def __init__(self, handle, keep):
+    def __init__(self, handle, keep, geom=(0, 0, 0)):
         self.handle = handle
         self._keep = keep
+        self.nk, self.npw_max, self.N = geom
 
     @property
     def device_bytes(self) -> int:
         return int(load().pwk_plan_device_bytes(self.handle))
 
     def launch_shape(self, precision: int):
-        """(threads per CTA, l3 chunk, shared memory bytes) chosen for a precision."""
-        t, l, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
-        _check(load().pwk_plan_launch_shape(self.handle, precision, ctypes.byref(t), ctypes.byref(l),
-                                            ctypes.byref(sm)), "pwk_plan_launch_shape")
-        return t.value, l.value, sm.value
+        """(kernel kind, threads per CTA, l3 chunk, shared memory bytes) of a precision."""
+        kd, t, l, sm = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_size_t()
+        _check(load().pwk_plan_launch_shape(self.handle, precision, ctypes.byref(kd), ctypes.byref(t),
+                                            ctypes.byref(l), ctypes.byref(sm)),
+               "pwk_plan_launch_shape")
+        return kd.value, t.value, l.value, sm.value
+
+    def set_launch_shape(self, precision: int, kind: int, threads: int, l3_chunk: int):
+        _check(load().pwk_plan_set_launch_shape(self.handle, precision, kind, threads, l3_chunk),
+               "pwk_plan_set_launch_shape")
 
     def close(self):
         if self.handle:
@@ -141,11 +148,12 @@ def plan_create(A, N, kcart, npw, miller, beta_dev, D, vloc_dev, hbm_budget: int
     nkb = 0 if beta_dev is None else int(beta_dev.shape[1])
     D = np.ascontiguousarray(D if D is not None else np.zeros((0, 0)), np.float64)
     h = ctypes.c_void_p()
+    geom = (nk, npw_max, int(N))
     rc = L.pwk_plan_create(ctypes.byref(h), _np_ptr(A), N, N, N, nk, _np_ptr(kcart), _np_ptr(npw),
                            npw_max, _np_ptr(miller), nkb, _ptr(beta_dev) if nkb else None,
                            _np_ptr(D) if nkb else None, _ptr(vloc_dev), hbm_budget)
     _check(rc, "pwk_plan_create")
-    return Plan(h, (beta_dev, vloc_dev))
+    return Plan(h, (beta_dev, vloc_dev), geom)
 
 
 def plan_from_problem(prob, device="cuda", hbm_budget: int = 0) -> Plan:
@@ -157,13 +165,32 @@ def plan_from_problem(prob, device="cuda", hbm_budget: int = 0) -> Plan:
                        hbm_budget)
 
 
+def _need(t, shape, dtype, name):
+    """Shape/dtype check of a tensor handed to the library (plain pointers cannot be checked
+    on the C side, so a wrong size here would read or write outside the tensor)."""
+    if tuple(t.shape) != tuple(shape) or t.dtype != dtype:
+        raise ValueError(f"{name}: expected shape {tuple(shape)} {dtype}, got {tuple(t.shape)} {t.dtype}")
+
+
 def hpsi_batched(plan: Plan, precision: int, psi, hpsi, nb: int, stream=None) -> None:
+    import torch
+    dt = torch.complex64 if precision == PWK_FP32 else torch.complex128
+    shape = (plan.nk, nb, plan.npw_max)
+    _need(psi, shape, dt, "psi")
+    _need(hpsi, shape, dt, "hpsi")
     _check(load().pwk_hpsi_batched(plan.handle, precision, _ptr(psi), _ptr(hpsi), nb,
                                    _stream(stream)), "pwk_hpsi_batched")
 
 
 def hpsi_items(plan: Plan, precision: int, psi, hpsi, items, nvec_per_k: int, stream=None):
+    import torch
+    dt = torch.complex64 if precision == PWK_FP32 else torch.complex128
+    shape = (plan.nk, nvec_per_k, plan.npw_max)
+    _need(psi, shape, dt, "psi")
+    _need(hpsi, shape, dt, "hpsi")
     n = 0 if items is None else int(items.shape[0])
+    if n:
+        _need(items, (n, 3), torch.int32, "items")
     _check(load().pwk_hpsi_items(plan.handle, precision, _ptr(psi), _ptr(hpsi),
                                  _ptr(items) if n else None, n, nvec_per_k, _stream(stream)),
            "pwk_hpsi_items")
@@ -172,8 +199,11 @@ def hpsi_items(plan: Plan, precision: int, psi, hpsi, items, nvec_per_k: int, st
 def davidson_batched(plan: Plan, mode: int, psi, eig, nb: int, eth: float, res_tol: float = 0.0,
                      max_iter: int = 100, max_basis: int = 0, stream=None):
     """Returns (unconverged count, iters[nk], notconv[nk], napply[2])."""
+    import torch
     L = load()
-    nk = psi.shape[0]
+    nk = plan.nk
+    _need(psi, (nk, nb, plan.npw_max), torch.complex128, "psi")
+    _need(eig, (nk, nb), torch.float64, "eig")
     iters = np.zeros(nk, np.int32)
     notc = np.zeros(nk, np.int32)
     napply = np.zeros(2, np.int64)
@@ -188,8 +218,15 @@ def sternheimer_cg_batched(plan_kq: Plan, plan_k: Plan, mode: int, psi_k, eps_k,
                            nocc: int, alpha, dv, dpsi, tol: float, max_iter: int = 500,
                            stream=None):
     """Returns (count above tol, iters[nk*nocc], resid[nk*nocc])."""
+    import torch
     L = load()
-    nk = psi_k.shape[0]
+    nk = plan_kq.nk
+    _need(psi_k, (nk, nocc, plan_k.npw_max), torch.complex128, "psi_k")
+    _need(psi_kq, (nk, nocc, plan_kq.npw_max), torch.complex128, "psi_kq")
+    _need(dpsi, (nk, nocc, plan_kq.npw_max), torch.complex128, "dpsi")
+    _need(eps_k, (nk, nocc), torch.float64, "eps_k")
+    _need(alpha, (nk,), torch.float64, "alpha")
+    _need(dv, (plan_kq.N,) * 3, torch.complex128, "dv")
     iters = np.zeros(nk * nocc, np.int32)
     resid = np.zeros(nk * nocc, np.float64)
     rc = L.pwk_sternheimer_cg_batched(plan_kq.handle, plan_k.handle, mode, _ptr(psi_k),

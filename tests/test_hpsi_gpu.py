@@ -160,3 +160,39 @@ def test_sphere_too_large_for_shared_memory_is_rejected():
     with pytest.raises(pwk.PwkError) as ei:
         pwk.plan_from_problem(prob)
     assert ei.value.code == -2
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp32_c128"])
+def test_every_launch_shape_gives_identical_results(precision):
+    """Every (kernel kind, threads, l3 chunk) the autotuner may pick computes the same H|psi>:
+    bitwise identical within a kernel kind, and both kinds within the precision's tolerance
+    of the oracle."""
+    torch = torch_cuda()
+    from paper_2412_01695_gb300 import pwk
+    prob = synth.make_config(2, k_subset=[0, 3, 300], nb=4)
+    ref = oracle_hpsi(prob)
+    plan = pwk.plan_from_problem(prob)
+    prec = pwk.PRECISIONS[precision]
+    dt = torch.complex64 if precision == "fp32" else torch.complex128
+    x = torch.from_numpy(prob.psi).cuda().to(dt)
+    tol = TOL64 if precision == "fp64" else TOL32
+    outs = {}
+    for kind in (0, 1):
+        for T in (128, 192, 256):
+            for L in (24, 12, 8, 5):
+                try:
+                    plan.set_launch_shape(prec, kind, T, L)
+                except pwk.PwkError as e:
+                    assert e.code == -2
+                    continue
+                y = torch.full_like(x, complex(np.nan, np.nan))
+                pwk.hpsi_batched(plan, prec, x, y, prob.nb)
+                torch.cuda.synchronize()
+                out = y.cpu().numpy().astype(np.complex128)
+                assert max_rel_err(out, ref, prob) <= tol, (kind, T, L)
+                if kind in outs:
+                    assert np.array_equal(out, outs[kind]), (kind, T, L)
+                else:
+                    outs[kind] = out
+    assert set(outs) == {0, 1}
+    plan.close()
