@@ -173,6 +173,23 @@ int pwk_davidson_batched(pwk_plan* plan, int mode, void* psi, double* eig, int n
 int pwk_eigh_batched(int nprob, int n, int nev, const void* H, const void* S, double* eig,
                      void* vec, int* status, void* stream);
 
+/* pwk_eigh_batched_noalloc: pwk_eigh_batched without any device allocation, for callers that
+ * cannot call cudaMalloc where they solve: a latency-bound serving loop (cudaMalloc and
+ * cudaFree synchronise the whole device and stall its other streams) or a process whose
+ * device memory is entirely reserved by another allocator, so that a new cudaMalloc fails.
+ * The paper has no counterpart: this is a deployment variant of the same eigensolver.
+ * Same arguments, layouts and results as pwk_eigh_batched.  The workspace is a fixed array of
+ * 19.7 MB in the library's device memory, held on every device that loads the library until
+ * the process exits; it limits a call to nprob * n^2 <= 409600 (e.g. 16 problems of
+ * n = 160, 256 of n = 40); larger calls return PWK_ERR_UNSUPPORTED and do nothing.
+ * The first call on a device looks up the array's device address (once per device, with that
+ * device current); make that first call before any stream capture.  Every call shares the
+ * array (its previous contents are never read: the kernel writes each element before using
+ * it), so calls that overlap on the GPU, on any streams, race: serialise them.
+ * Asynchronous on `stream`: results are ready when the stream has synchronised. */
+int pwk_eigh_batched_noalloc(int nprob, int n, int nev, const void* H, const void* S,
+                             double* eig, void* vec, int* status, void* stream);
+
 /* ---------------------------------------------------------------------------- Sternheimer
  * pwk_sternheimer_cg_batched: for every k of plan_k and every occupied band n, solve the
  * DFPT linear system of Eq. linear_system with S = I and dS = 0,

@@ -22,7 +22,8 @@ PRECISIONS = {"fp64": PWK_FP64, "fp32": PWK_FP32, "fp32_c128": PWK_FP32_C128}
 EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
            "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_supported_grid",
            "pwk_hpsi_batched", "pwk_hpsi_items", "pwk_davidson_batched",
-           "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_strerror", "pwk_last_error_detail", "pwk_version")
+           "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_eigh_batched_noalloc",
+           "pwk_strerror", "pwk_last_error_detail", "pwk_version")
 
 _lib = None
 
@@ -54,6 +55,7 @@ def load(path: str = LIB_PATH):
         "pwk_sternheimer_cg_batched": (_I, [_P, _P, _I, _P, _P, _P, _I, _P, _P, _P, _D, _I, _P,
                                             _P, _P]),
         "pwk_eigh_batched": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
+        "pwk_eigh_batched_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
         "pwk_strerror": (ctypes.c_char_p, [_I]),
         "pwk_last_error_detail": (ctypes.c_char_p, []),
         "pwk_version": (ctypes.c_char_p, []),
@@ -247,6 +249,16 @@ def eigh_batched(H, S, nev: int, status=None, stream=None):
                                    _ptr(status) if status is not None else None,
                                    _stream(stream)), "pwk_eigh_batched")
     return eig, vec
+
+
+def eigh_batched_noalloc(H, S, nev: int, eig, vec, status=None, stream=None):
+    """pwk_eigh_batched_noalloc: the same solve with the library's built-in workspace; the
+    caller provides the outputs eig [nprob][nev] float64 and vec [nprob][n][nev] complex128.
+    Asynchronous: synchronise the stream before reading the results."""
+    nprob, n = int(H.shape[0]), int(H.shape[1])
+    _check(load().pwk_eigh_batched_noalloc(nprob, n, nev, _ptr(H), _ptr(S), _ptr(eig), _ptr(vec),
+                                           _ptr(status) if status is not None else None,
+                                           _stream(stream)), "pwk_eigh_batched_noalloc")
 
 
 def supported_grid(N: int) -> bool:
