@@ -92,7 +92,7 @@ size_t pwk_plan_device_bytes(const pwk_plan* plan);
 int pwk_plan_launch_shape(const pwk_plan* plan, int precision, int* kind, int* threads,
                           int* l3_chunk, size_t* smem_bytes);
 
-/* Override the launch shape of one precision: kind 0 or 1, threads 128, 192 or 256,
+/* Override the launch shape of one precision: kind 0 or 1, threads 96, 128, 192 or 256,
  * 1 <= l3_chunk <= N.  Returns PWK_ERR_UNSUPPORTED if the shape does not fit in shared
  * memory or the window kernel does not apply to the plan (the shape is then unchanged). */
 int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threads, int l3_chunk);

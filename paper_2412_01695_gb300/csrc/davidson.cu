@@ -16,9 +16,9 @@
 // A k-point whose reduced problem fails (S~ numerically singular in its leading block, or QL
 // not converging) drops the vectors of that step and restarts from its Ritz vectors; after
 // more than three failures it is given up and its bands are reported unconverged.
-// Mixed mode: FP32 H applications until the bands stop moving by more than
-// max(eth, 1e-4 Ry) (and ||r|| < max(res_tol, 1e-3)); then the Ritz vectors get FP64 H
-// applications and the iteration goes on in FP64 to eth.  Reduced matrices, eigensolve, norms and residuals are FP64 always.
+// Mixed mode: each k-point applies H in FP32 until its bands stop moving by more than
+// max(eth, 1e-4 Ry) (and ||r|| < max(res_tol, 1e-3)); then its Ritz vectors get FP64 H
+// applications and it goes on in FP64 to eth (per k-point, independently of the others).  Reduced matrices, eigensolve, norms and residuals are FP64 always.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -36,8 +36,9 @@ struct DavWork {
   double2 *Hr = nullptr, *Sr = nullptr, *W = nullptr, *ev = nullptr;
   double *eps = nullptr, *eps_new = nullptr, *hdiag = nullptr, *rnorm = nullptr;
   int *nbase = nullptr, *nnc = nullptr, *todo = nullptr, *active = nullptr, *moved = nullptr;
-  int *restart = nullptr, *items = nullptr, *counters = nullptr, *iters = nullptr,
-      *status = nullptr, *failcount = nullptr, *force = nullptr, *dbg = nullptr;
+  int *restart = nullptr, *items = nullptr, *iters = nullptr,
+      *status = nullptr, *failcount = nullptr, *force = nullptr, *dbg = nullptr,
+      *phase = nullptr, *switchk = nullptr, *iterk = nullptr, *counters = nullptr;
   std::vector<void*> ptrs;
 };
 
@@ -76,9 +77,11 @@ static int ensure_dav_work(pwk_plan* p, int nb, int MB) {
       (rc = dalloc(p, w, &w->nnc, nk)) || (rc = dalloc(p, w, &w->todo, nk * nb)) ||
       (rc = dalloc(p, w, &w->active, nk)) || (rc = dalloc(p, w, &w->moved, nk * nb)) ||
       (rc = dalloc(p, w, &w->restart, nk)) || (rc = dalloc(p, w, &w->items, nk * nb * 3)) ||
-      (rc = dalloc(p, w, &w->counters, 4)) || (rc = dalloc(p, w, &w->iters, nk)) ||
+      (rc = dalloc(p, w, &w->iters, nk)) ||
       (rc = dalloc(p, w, &w->status, nk)) || (rc = dalloc(p, w, &w->failcount, nk)) ||
-      (rc = dalloc(p, w, &w->force, nk)) || (rc = dalloc(p, w, &w->dbg, 4))) {
+      (rc = dalloc(p, w, &w->force, nk)) || (rc = dalloc(p, w, &w->dbg, 4)) ||
+      (rc = dalloc(p, w, &w->phase, nk)) || (rc = dalloc(p, w, &w->switchk, nk)) ||
+      (rc = dalloc(p, w, &w->iterk, nk)) || (rc = dalloc(p, w, &w->counters, 8))) {
     destroy_dav_work(p);
     return rc;
   }
@@ -140,15 +143,17 @@ __global__ void copy_vecs_kernel(int nk, int nv, int np, const double2* src, int
   for (int g = threadIdx.x; g < np; g += blockDim.x) d[g] = s[g];
 }
 
-// work list: (k, base[k] + t) for t < cnt[k] on active k, else empty slots (k = -1)
+// work list: (k, base[k] + t) for t < cnt[k] on k with mask[k] (and phase[k] == want_phase
+// when want_phase > 0), else empty slots (k = -1)
 __global__ void items_kernel(int nk, int nb, const int* active, const int* base, int base_const,
-                             const int* cnt, int cnt_const, int* items) {
+                             const int* cnt, int cnt_const, const int* phase, int want_phase,
+                             int* items) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nk * nb) return;
   const int k = i / nb, t = i % nb;
   const int b = base ? base[k] : base_const;
   const int c = cnt ? cnt[k] : cnt_const;
-  const bool on = active[k] && t < c;
+  const bool on = active[k] && t < c && (want_phase <= 0 || phase[k] == want_phase);
   items[3 * i] = on ? k : -1;
   items[3 * i + 1] = on ? b + t : 0;
   items[3 * i + 2] = on ? b + t : 0;
@@ -309,14 +314,20 @@ __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, cons
   if (threadIdx.x == 0) rnorm[k * nb + i] = sqrt(rr);
 }
 
-// Which bands still need a correction.  counters[0] += bands left; counters[1] |= a k-point
-// given up after repeated failures of its reduced problem (counters[2], [3]: its k and status).
-__global__ void select_kernel(int nk, int nb, int MB, double res_tol, int* active, const int* moved,
-                              const double* rnorm, const int* nbase, int* todo, int* nnc,
-                              int* restart, int* iters, const int* status, int* force,
-                              const int* failcount, int* counters) {
+// Which bands still need a correction, per k-point and its phase (1: FP32 H, 2: FP64 H).
+// counters[0] += bands to correct this step, counters[5] += those of phase-2 k-points,
+// counters[4] += k-points switching from phase 1 to phase 2 this step (their FP32 floor is
+// reached or their phase-1 iterations are used up), counters[1] += bands of k-points given up
+// after repeated reduced-problem failures (counters[2], [3]: the first such k and its status).
+__global__ void select_kernel(int nk, int nb, int MB, double rt1, double rt2, int cap1, int* active,
+                              const int* phase, const int* moved, const double* rnorm,
+                              const int* nbase, int* todo, int* nnc, int* restart, int* iters,
+                              const int* status, int* force, const int* failcount, int* switchk,
+                              int* iterk, int* counters) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nk) return;
+  switchk[k] = 0;
+  iterk[k] = 0;
   if (active[k] && failcount[k] > 3) {   // give this k-point up: its bands stay unconverged
     active[k] = 0;
     nnc[k] = nb;
@@ -330,17 +341,35 @@ __global__ void select_kernel(int nk, int nb, int MB, double res_tol, int* activ
     restart[k] = 0;
     return;
   }
+  const double rt = phase[k] == 1 ? rt1 : rt2;
   int c = 0;
   for (int i = 0; i < nb; ++i) {
-    const bool conv = !moved[k * nb + i] && (res_tol <= 0.0 || rnorm[k * nb + i] <= res_tol);
+    const bool conv = !moved[k * nb + i] && (rt <= 0.0 || rnorm[k * nb + i] <= rt);
     if (!conv) todo[k * nb + c++] = i;
+  }
+  if (phase[k] == 1 && (c == 0 || iters[k] >= cap1)) {
+    switchk[k] = 1;
+    nnc[k] = 0;
+    restart[k] = 0;
+    atomicAdd(&counters[4], 1);
+    return;
   }
   nnc[k] = c;
   restart[k] = (c > 0 && (nbase[k] + c > MB || force[k])) ? 1 : 0;
   force[k] = 0;
-  if (c == 0) active[k] = 0;
-  else iters[k] += 1;
+  if (c == 0) {
+    active[k] = 0;
+  } else {
+    iters[k] += 1;
+    iterk[k] = 1;
+  }
   atomicAdd(&counters[0], c);
+  if (phase[k] == 2) atomicAdd(&counters[5], c);
+}
+
+__global__ void set_value_kernel(int nk, const int* mask, int* a, int v) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nk && mask[k]) a[k] = v;
 }
 
 __global__ void append_kernel(int nb, int MB, int np, const int* active, const int* nbase,
@@ -364,13 +393,15 @@ __global__ void set_nbase_kernel(int nk, const int* only, int* nbase, int value,
 // this step (n_base -= added[k]), keeps its previous Ritz pairs, corrects every band again and
 // restarts from its Ritz vectors at the next step; after more than three failures it is
 // given up (reported as an error by the next select).
-__global__ void update_kernel(int nk, int nb, double eth, int* active, int force_all,
-                              const double* eps_new, double* eps, int* moved, const int* status,
-                              const int* added, int* nbase, int* force, int* failcount, int* dbg) {
+__global__ void update_kernel(int nk, int nb, double eth1, double eth2, const int* phase,
+                              const int* mask, int force_all, const double* eps_new, double* eps,
+                              int* moved, const int* status, const int* added, int* nbase,
+                              int* force, int* failcount, int* dbg) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nk * nb) return;
   const int k = i / nb;
-  if (!active[k]) return;
+  if (!mask[k]) return;
+  const double eth = phase[k] == 1 ? eth1 : eth2;
   if (status[k] != 0) {
     moved[i] = 1;
     if (i % nb == 0) {
@@ -470,7 +501,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   if (gram_smem > 48 * 1024)
     cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem);
   long long napply[2] = {0, 0};
-  int total = 0, given_up = 0, host_counters[4] = {0, 0, -1, 0}, host_dbg[4] = {0, 0, 0, 0};
+  int total = 0, given_up = 0, host_dbg[4] = {0, 0, 0, 0};
   bool dumped = false;
 
   hdiag_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>(nk, np, p->nkb, p->d_npw, p->d_g2, p->v_mean,
@@ -486,51 +517,56 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi, MB, 0, nullptr);
   KCHECK("davidson init");
 
-  // H on phi[0:nb] in precision prec, reduced matrices of that block, eigensolve
-  auto start_block = [&](int prec, const int* only) -> int {
-    items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, only ? only : w->active, nullptr, 0,
-                                                          nullptr, nb, w->items);
+  // Phase 1 (mixed mode) stops at the FP32 noise floor: eigenvalues of the reduced problem
+  // built from FP32 H applications move by ~1e-6 |H| between iterations and residuals bottom
+  // out near 1e-5, so a k-point leaves phase 1 when its bands stop moving by 1e-4 Ry with
+  // ||r|| < 1e-3, or after max_iter/2 correction steps; it then restarts from its Ritz
+  // vectors with FP64 H applications (phase 2) and goes on to eth and res_tol.  Each k-point
+  // switches on its own: the others keep iterating in their phase.
+  const double eth1 = mode == PWK_FP32_C128 ? std::max(eth, 1e-4) : eth;
+  const double rt1 = mode == PWK_FP32_C128 && res_tol > 0 ? std::max(res_tol, 1e-3) : res_tol;
+  const int cap1 = std::max(1, max_iter / 2);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->phase, mode == PWK_FP32_C128 ? 1 : 2);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->switchk, 0);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, 0);
+
+  // H on phi[0:nb] of the k-points in mask, their nb x nb reduced matrices and eigensolve
+  auto start_block = [&](int prec, int* mask, int count) -> int {
+    items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, mask, nullptr, 0, nullptr, nb,
+                                                          w->phase, 0, w->items);
     KCHECK("items_kernel");
     int r = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st);
     if (r) return r;
-    napply[prec == PWK_FP64 ? 0 : 1] += (long long)nk * nb;
-    gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->active, nullptr, 0, nullptr,
-                                                 nb, w->phi, w->hphi, w->Hr, w->Sr);
+    napply[prec == PWK_FP64 ? 0 : 1] += (long long)count * nb;
+    gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, mask, nullptr, 0, nullptr, nb,
+                                                 w->phi, w->hphi, w->Hr, w->Sr);
     KCHECK("gram_kernel");
-    set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, w->nbase, nb, nullptr);
-    r = launch_rr(nk, MB, nb, w->nbase, w->active, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st);
-    if (r) return r;
-    return PWK_OK;
+    set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, mask, w->nbase, nb, nullptr);
+    return launch_rr(nk, MB, nb, w->nbase, mask, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st);
   };
 
-  // Phase 1 (mixed mode) stops at the FP32 noise floor: eigenvalues of the reduced problem
-  // built from FP32 H applications move by ~1e-6 |H| between iterations, residuals bottom out
-  // near 1e-5, so phase 1 asks for |d eps| < 1e-4 Ry and ||r|| < 1e-3, and runs at most
-  // max_iter/2 iterations; phase 2 (FP64) reaches eth and res_tol.
-  int phase = (mode == PWK_FP32_C128) ? 1 : 2;
-  int prec = phase == 1 ? PWK_FP32_C128 : PWK_FP64;
-  double eth_cur = phase == 1 ? std::max(eth, 1e-4) : eth;
-  double rt_cur = phase == 1 && res_tol > 0 ? std::max(res_tol, 1e-3) : res_tol;
-  const int phase1_cap = std::max(1, max_iter / 2);
-  if ((rc = start_block(prec, nullptr))) return rc;
-  update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth_cur, w->active, 1, w->eps_new,
-                                                         w->eps, w->moved, w->status, nullptr,
-                                                         w->nbase, w->force, w->failcount, w->dbg);
+  if ((rc = start_block(mode == PWK_FP64 ? PWK_FP64 : PWK_FP32_C128, w->active, nk))) return rc;
+  update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->active, 1,
+                                                         w->eps_new, w->eps, w->moved, w->status,
+                                                         nullptr, w->nbase, w->force, w->failcount,
+                                                         w->dbg);
   KCHECK("update_kernel");
 
   int it = 0;
+  int hc[8];
   for (;;) {
     resid_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved,
-                                          rt_cur > 0 ? 1 : 0, w->ev, w->eps, w->phi, w->hphi,
-                                          w->hdiag, w->corr, w->rnorm);
+                                          (rt1 > 0 || res_tol > 0) ? 1 : 0, w->ev, w->eps, w->phi,
+                                          w->hphi, w->hdiag, w->corr, w->rnorm);
     KCHECK("resid_kernel");
-    cudaMemsetAsync(w->counters, 0, 2 * sizeof(int), st);
+    cudaMemsetAsync(w->counters, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(w->counters + 2, 0xff, sizeof(int), st);
-    select_kernel<<<blocks(nk), 256, 0, st>>>(nk, nb, MB, rt_cur, w->active, w->moved, w->rnorm,
-                                              w->nbase, w->todo, w->nnc, w->restart, w->iters,
-                                              w->status, w->force, w->failcount, w->counters);
+    select_kernel<<<blocks(nk), 256, 0, st>>>(nk, nb, MB, rt1, res_tol, cap1, w->active, w->phase,
+                                              w->moved, w->rnorm, w->nbase, w->todo, w->nnc,
+                                              w->restart, w->iters, w->status, w->force,
+                                              w->failcount, w->switchk, w->iterk, w->counters);
     KCHECK("select_kernel");
-    cudaError_t ce = cudaMemcpyAsync(host_counters, w->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaError_t ce = cudaMemcpyAsync(hc, w->counters, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(host_dbg, w->dbg, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return cuda_fail(ce, "davidson counters");
@@ -538,68 +574,68 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       dump_reduced(w, host_dbg[1], host_dbg[2]);
       dumped = true;
     }
-    if (host_counters[1]) {
-      given_up += host_counters[1];
-      int nbk = -1;
-      cudaMemcpy(&nbk, w->nbase + host_counters[2], sizeof(int), cudaMemcpyDeviceToHost);
+    if (hc[1]) {
+      given_up += hc[1];
       char buf[200];
       std::snprintf(buf, sizeof(buf),
-                    "k=%d given up after repeated reduced-problem failures (status %d: %s), "
-                    "iteration %d, phase %d, n_base %d",
-                    host_counters[2], host_counters[3],
-                    host_counters[3] == PWK_ERR_NUMERIC ? "QL did not converge" : "S~ not positive definite",
-                    it, phase, nbk);
+                    "k=%d given up after repeated reduced-problem failures (status %d: %s), iteration %d",
+                    hc[2], hc[3], hc[3] == PWK_ERR_NUMERIC ? "QL did not converge" : "S~ not positive definite",
+                    it);
       set_error(buf);
     }
-    total = host_counters[0];
-    if (total == 0 || (phase == 1 && it >= phase1_cap)) {
-      if (phase == 1) {
-        // FP64 refinement: restart every k from its Ritz vectors with FP64 H applications
-        phase = 2;
-        prec = PWK_FP64;
-        eth_cur = eth;
-        rt_cur = res_tol;
-        reactivate_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, w->failcount);
-        rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi, w->tmp1, nb);
-        copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, nullptr);
-        KCHECK("refinement restart");
-        if ((rc = start_block(prec, nullptr))) return rc;
-        update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth_cur, w->active, 0,
-                                                               w->eps_new, w->eps, w->moved,
-                                                               w->status, nullptr, w->nbase,
-                                                               w->force, w->failcount, w->dbg);
-        KCHECK("update_kernel");
-        continue;
-      }
-      break;
-    }
+    total = hc[0];
+    const int nswitch = hc[4], n64 = hc[5];
+    if (total == 0 && nswitch == 0) break;
     if (++it > max_iter) break;
-    // restart the k-points whose basis would overflow
-    rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->phi, w->tmp1, nb);
-    rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->hphi, w->tmp2, nb);
-    copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, w->restart);
-    copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp2, nb, 0, w->hphi, MB, 0, w->restart);
-    gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->restart, nullptr, 0, nullptr,
-                                                 nb, w->phi, w->hphi, w->Hr, w->Sr);
-    set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, w->nbase, nb, nullptr);
-    KCHECK("davidson restart");
-    // append the corrections, apply H to them, extend H~ and S~
-    append_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->active, w->nbase, w->nnc, w->todo, w->corr, w->phi);
-    items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, w->active, w->nbase, 0, w->nnc, 0, w->items);
-    KCHECK("davidson append");
-    if ((rc = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st))) return rc;
-    napply[prec == PWK_FP64 ? 0 : 1] += total;
-    gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->active, w->nbase, 0, w->nnc, 0,
-                                                 w->phi, w->hphi, w->Hr, w->Sr);
-    set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, w->nbase, 0, w->nnc);
-    KCHECK("davidson gram");
-    if ((rc = launch_rr(nk, MB, nb, w->nbase, w->active, w->Hr, w->Sr, w->W, w->ev, w->eps_new,
-                        w->status, st)))
-      return rc;
-    update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth_cur, w->active, 0, w->eps_new,
-                                                           w->eps, w->moved, w->status, w->nnc,
-                                                           w->nbase, w->force, w->failcount, w->dbg);
-    KCHECK("update_kernel");
+    if (nswitch > 0) {
+      // FP64 refinement start of the k-points leaving phase 1: Ritz vectors, FP64 H on them
+      rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->switchk, w->ev, w->phi, w->tmp1, nb);
+      copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, w->switchk);
+      set_value_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->switchk, w->phase, 2);
+      KCHECK("phase switch");
+      if ((rc = start_block(PWK_FP64, w->switchk, nswitch))) return rc;
+      update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->switchk, 0,
+                                                             w->eps_new, w->eps, w->moved, w->status,
+                                                             nullptr, w->nbase, w->force, w->failcount,
+                                                             w->dbg);
+      KCHECK("update_kernel");
+    }
+    if (total > 0) {
+      // restart the k-points whose basis would overflow
+      rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->phi, w->tmp1, nb);
+      rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->hphi, w->tmp2, nb);
+      copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, w->restart);
+      copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp2, nb, 0, w->hphi, MB, 0, w->restart);
+      gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->restart, nullptr, 0, nullptr,
+                                                   nb, w->phi, w->hphi, w->Hr, w->Sr);
+      set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, w->nbase, nb, nullptr);
+      KCHECK("davidson restart");
+      // append the corrections, apply H to them (FP32 for phase-1 k, FP64 for phase-2 k)
+      append_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->iterk, w->nbase, w->nnc, w->todo, w->corr, w->phi);
+      KCHECK("davidson append");
+      for (int ph = 1; ph <= 2; ++ph) {
+        const int cnt = ph == 2 ? n64 : total - n64;
+        if (cnt == 0) continue;
+        items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, w->iterk, w->nbase, 0, w->nnc, 0,
+                                                              w->phase, ph, w->items);
+        KCHECK("items_kernel");
+        const int prec = ph == 2 ? PWK_FP64 : PWK_FP32_C128;
+        if ((rc = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st))) return rc;
+        napply[ph == 2 ? 0 : 1] += cnt;
+      }
+      gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->iterk, w->nbase, 0, w->nnc,
+                                                   0, w->phi, w->hphi, w->Hr, w->Sr);
+      set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, w->nbase, 0, w->nnc);
+      KCHECK("davidson gram");
+      if ((rc = launch_rr(nk, MB, nb, w->nbase, w->iterk, w->Hr, w->Sr, w->W, w->ev, w->eps_new,
+                          w->status, st)))
+        return rc;
+      update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->iterk, 0,
+                                                             w->eps_new, w->eps, w->moved, w->status,
+                                                             w->nnc, w->nbase, w->force, w->failcount,
+                                                             w->dbg);
+      KCHECK("update_kernel");
+    }
   }
   // eigenvectors out: psi = phi v; eigenvalues out
   rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi, psi, nb);

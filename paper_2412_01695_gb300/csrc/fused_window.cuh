@@ -54,11 +54,11 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
   const int tid = threadIdx.x, nth = blockDim.x;
   const int np = a.npw_in[k];
   const int ns = a.nstick[k];
-  const int zs = a.zs, L = a.L;
+  const int zs = a.zs, L = a.L, yps = a.yps;
 
   V* Z = reinterpret_cast<V*>(smem_raw);               // [NW*NW][zs]
-  V* Y = Z + (size_t)NW * NW * zs;                      // [NW][N][L]
-  V* psis = Y + (size_t)NW * N * L;                     // [npw_max]
+  V* Y = Z + (size_t)NW * NW * zs;                      // [NW][yps] (N x L used per plane)
+  V* psis = Y + (size_t)NW * yps;                       // [npw_max]
   V* lam = psis + a.npw_in_max;
   V* gam = lam + a.nkb;
   short* rows = reinterpret_cast<short*>(gam + a.nkb);  // [nstick_max]
@@ -132,12 +132,12 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
     const int lc = min(L, N - l0);
     // 3a: inverse y transforms, inputs on the m2 window of plane p
     for (int t = tid; t < NW * lc; t += nth) {
-      const int p = t / lc, c = t - p * lc;
+      const int c = t / NW, p = t - c * NW;   // plane fastest: conflict-free (see window_strides)
       V x[N];
       const V* zp = Z + (size_t)p * NW * zs + l0 + c;
       PWK_SFOR(N, j, x[j] = Wn::in(j) ? zp[Wn::idx(j) * zs] : V{T(0), T(0)});
       LineFFT<T, N, +1>::run(x);
-      V* yp = Y + (size_t)p * N * L + c;
+      V* yp = Y + (size_t)p * yps + c;
       PWK_SFOR(N, l2, yp[l2 * L] = x[OutSlot<N, l2>::value]);
     }
     __syncthreads();
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
       const int l2 = t / lc, c = t - l2 * lc;
       V x[N];
       const V* yl = Y + (size_t)l2 * L + c;
-      PWK_SFOR(N, i, x[i] = Wn::in(i) ? yl[(size_t)Wn::idx(i) * N * L] : V{T(0), T(0)});
+      PWK_SFOR(N, i, x[i] = Wn::in(i) ? yl[(size_t)Wn::idx(i) * yps] : V{T(0), T(0)});
       LineFFT<T, N, +1>::run(x);
       T w[N];
       load_vline<T, N>(static_cast<const T*>(a.V) + ((size_t)l2 * N + l0 + c) * N, w);
@@ -158,15 +158,15 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
       LineFFT<T, N, -1>::run(y);
       V* yo = Y + (size_t)l2 * L + c;
       PWK_SFOR(N, i, {
-        if constexpr (Wn::in(i)) yo[(size_t)Wn::idx(i) * N * L] = y[OutSlot<N, i>::value];
+        if constexpr (Wn::in(i)) yo[(size_t)Wn::idx(i) * yps] = y[OutSlot<N, i>::value];
       });
     }
     __syncthreads();
     // 3c: forward y transforms, window outputs written back to the stick square
     for (int t = tid; t < NW * lc; t += nth) {
-      const int p = t / lc, c = t - p * lc;
+      const int c = t / NW, p = t - c * NW;
       V x[N];
-      const V* yp = Y + (size_t)p * N * L + c;
+      const V* yp = Y + (size_t)p * yps + c;
       PWK_SFOR(N, l2, x[l2] = yp[l2 * L]);
       LineFFT<T, N, -1>::run(x);
       V* zp = Z + (size_t)p * NW * zs + l0 + c;

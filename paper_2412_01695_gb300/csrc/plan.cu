@@ -78,10 +78,31 @@ size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int
   return elems * elem_bytes + (size_t)P * N * sizeof(short) + 16;
 }
 
+// The y pass maps thread t to (plane p = t % NW, column c = t / NW) and touches element
+// p * (NW * zs) + c of the stick square and p * yps + c of the chunk buffer; the x pass maps t to
+// (l2 = t / L, c = t % L) and touches p * yps + l2 * L + c.  With u = NW^-1 (mod 16) (NW is
+// odd), NW * zs = yps = u (mod 16) makes every y-pass address u * t plus a constant (mod 16), and
+// x-pass addresses are consecutive in t: the 16 eight-byte accesses of a half-warp fall on 32
+// different banks in both passes.  zs = u^2 (mod 16) is odd, so the z pass (one stick row per
+// thread) stays conflict-free for consecutive sticks as well.
+void window_strides(int N, int L, int* zs, int* yps) {
+  const int W = N / 4, NW = 2 * W + 1;
+  int u = 1;
+  while ((NW * u) % 16 != 1) ++u;
+  const int z_res = (u * u) % 16;
+  int z = N;
+  while (z % 16 != z_res) ++z;
+  *zs = z;
+  int y = N * L;
+  while (y % 16 != u) ++y;
+  *yps = y;
+}
+
 size_t window_smem_bytes(int N, int elem_bytes, int L, int npw_max, int nkb, int nstick_max) {
   const int W = N / 4, NW = 2 * W + 1;
-  const int zs = (N % 2 == 0) ? N + 1 : N;
-  size_t elems = (size_t)NW * NW * zs + (size_t)NW * N * L + npw_max + 2 * (size_t)nkb;
+  int zs, yps;
+  window_strides(N, L, &zs, &yps);
+  size_t elems = (size_t)NW * NW * zs + (size_t)NW * yps + npw_max + 2 * (size_t)nkb;
   return elems * elem_bytes + (size_t)nstick_max * sizeof(short) + 16;
 }
 
@@ -305,10 +326,13 @@ static void use_kind(const pwk_plan* p, FusedArgs& a, int kind) {
   if (kind == 1) {
     a.gin = a.gout = p->d_wgmap;
     a.sid = p->d_wrows;
+    window_strides(p->N, a.L, &a.zs, &a.yps);
   } else {
     a.gin = p->self.d_gin;
     a.gout = p->self.d_gout;
     a.sid = p->self.d_sid;
+    a.zs = (p->N % 2 == 0) ? p->N + 1 : p->N;
+    a.yps = p->N * a.L;
   }
 }
 
@@ -321,10 +345,10 @@ int autotune_shape(pwk_plan* p, int precision) {
   const int elem = precision == PWK_FP64 ? 16 : 8;
   const int io_elem = precision == PWK_FP32 ? 8 : 16;
   std::vector<LaunchShape> cands;
-  const int Ls[3] = {N, (N + 1) / 2, (N + 2) / 3};
+  const int Ls[4] = {N, (N + 1) / 2, (N + 2) / 3, (N + 3) / 4};
   for (int kind = 0; kind < (p->window_ok ? 2 : 1); ++kind)
-    for (int T : {128, 192, 256})
-      for (int li = 0; li < 3; ++li) {
+    for (int T : {96, 128, 192, 256})
+      for (int li = 0; li < 4; ++li) {
         const int L = Ls[li];
         if (li > 0 && L == Ls[li - 1]) continue;
         LaunchShape c;
@@ -458,8 +482,9 @@ size_t pwk_plan_device_bytes(const pwk_plan* p) { return p ? p->bytes : 0; }
 
 int pwk_plan_set_launch_shape(pwk_plan* p, int precision, int kind, int threads, int l3_chunk) {
   if (p == nullptr || precision < 0 || precision > 2 || kind < 0 || kind > 1 ||
-      (threads != 128 && threads != 192 && threads != 256) || l3_chunk < 1 || l3_chunk > p->N) {
-    set_error("bad plan, precision, kind (0/1), threads (128/192/256) or l3 chunk (1..N)");
+      (threads != 96 && threads != 128 && threads != 192 && threads != 256) || l3_chunk < 1 ||
+      l3_chunk > p->N) {
+    set_error("bad plan, precision, kind (0/1), threads (96/128/192/256) or l3 chunk (1..N)");
     return PWK_ERR_INVALID;
   }
   if (kind == 1 && !p->window_ok) {

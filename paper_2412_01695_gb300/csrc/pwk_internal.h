@@ -103,6 +103,7 @@ struct FusedArgs {
   const int* gout = nullptr;
   const short* sid = nullptr;
   int nstick_max = 0, m1lo = 0, P = 0, L = 0, zs = 0;
+  int yps = 0;                     // plane stride of the y/x chunk buffer (window kernel)
   const double* g2 = nullptr;      // kinetic table [nk][npw_out_max] or null
   const void* beta = nullptr;      // [nk][nkb][npw_out_max] complex of the arithmetic type
   const void* D = nullptr;         // [nkb][nkb] real of the arithmetic type
@@ -126,6 +127,8 @@ int launch_window_f32(int N, const FusedArgs& a, int nblocks, const LaunchShape&
 int launch_window_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchShape& s,
                           cudaStream_t st);
 size_t window_smem_bytes(int N, int elem_bytes, int L, int npw_max, int nkb, int nstick_max);
+// strides of the window kernel's shared buffers for chunk L (bank-conflict-free y/x passes)
+void window_strides(int N, int L, int* zs, int* yps);
 
 // fill FusedArgs for H|psi> with this plan
 FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out);

@@ -7,14 +7,14 @@
 //   2. C = L^-1 H~ L^-H by two triangular solves (one thread per right-hand side);
 //   3. Householder reduction of C to a real symmetric tridiagonal T = Q^H C Q
 //      (reflectors H = I - tau v v^H, beta real, two-sided rank-2 updates);
-//   4. implicit QL iteration with Wilkinson shifts on T; thread 0 chases the bulge and
-//      records the Givens rotations of one sweep, every thread then applies them to one row
-//      of the eigenvector matrix Z (column-major, so a column is a coalesced access);
-//   5. the nb lowest eigenvalues are selected; their vectors are mapped back,
-//      x = L^-H Q z (reflectors applied in reverse order, then back substitution).
+//   4. the nb lowest eigenvalues of T by bisection on Sturm counts and their eigenvectors by
+//      inverse iteration on T (one thread per eigenpair, threads of a warp in lockstep;
+//      near-equal eigenvalues orthogonalised by modified Gram-Schmidt);
+//   5. back-transform x = L^-H Q z (reflectors applied in reverse order, then back
+//      substitution).
 // All matrices live in a per-k global workspace (L2-resident while the CTA works on it).
-// A non-positive pivot in step 1 marks the k-point with status PWK_ERR_NOT_POSDEF; an
-// eigenvalue that does not converge in 60 QL sweeps marks it PWK_ERR_NUMERIC.
+// A dependent vector among the first nb (pivot below 1e-9 of its diagonal) marks the k-point
+// with status PWK_ERR_NOT_POSDEF; a non-finite eigenvector marks it PWK_ERR_NUMERIC.
 #include <cmath>
 
 #include "solvers.h"
@@ -60,8 +60,7 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   __shared__ double red[32];
   __shared__ double d[kMaxBasis], e[kMaxBasis], rc[kMaxBasis], rs[kMaxBasis];
   __shared__ double2 tau[kMaxBasis];
-  __shared__ int rank[kMaxBasis];
-  __shared__ int flag, nrot, rot_lo, qstate;
+  __shared__ int flag;
   __shared__ unsigned char dropped[kMaxBasis];
   const size_t ldsq = (size_t)ld * ld;
   const double2* H = Hr + k * ldsq;
@@ -249,102 +248,124 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     d[n - 1] = C[(n - 1) * ld + (n - 1)].x;
     e[n - 1] = 0.0;
   }
-  // ---- 4. implicit QL on (d, e); Z = I (real, column-major in X)
-  double* Z = reinterpret_cast<double*>(X);
-  for (int i = tid; i < n * n; i += nth) Z[i] = (i / n == i % n) ? 1.0 : 0.0;
   __syncthreads();
-  for (int l = 0; l < n; ++l) {
-    int iter = 0;
-    while (true) {
-      if (tid == 0) {
-        int m = l;
-        for (; m < n - 1; ++m) {
-          const double dd = fabs(d[m]) + fabs(d[m + 1]);
-          if (fabs(e[m]) + dd == dd) break;
-        }
-        nrot = 0;
-        rot_lo = m - 1;
-        if (m == l) {
-          qstate = 0;                       // d[l] is an eigenvalue
-        } else if (++iter > 60) {
-          qstate = 2;
-          flag = 2;
-        } else {
-          qstate = 1;
-          // shift from the leading 2x2 block of the unreduced part (Wilkinson)
-          double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-          double r = hypot(g, 1.0);
-          g = d[m] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
-          double s = 1.0, c = 1.0, p = 0.0;
-          bool early = false;
-          for (int i = m - 1; i >= l; --i) {
-            const double f = s * e[i], b = c * e[i];
-            r = hypot(f, g);
-            e[i + 1] = r;
-            if (r == 0.0) {   // exact split inside the chase
-              d[i + 1] -= p;
-              e[m] = 0.0;
-              early = true;
-              break;
-            }
-            s = f / r;
-            c = g / r;
-            g = d[i + 1] - p;
-            r = (d[i] - g) * s + 2.0 * c * b;
-            p = s * r;
-            d[i + 1] = g + p;
-            g = c * r - b;
-            rc[nrot] = c;          // rotation nrot acts on columns (m-1-nrot, m-nrot)
-            rs[nrot] = s;
-            ++nrot;
-          }
-          if (!early) {
-            d[l] -= p;
-            e[l] = g;
-            e[m] = 0.0;
-          }
-        }
+  // ---- 4. the nb lowest eigenpairs of the real tridiagonal T = (d, e): bisection on Sturm
+  //      counts for the eigenvalues, then inverse iteration for the eigenvectors, one thread per
+  //      eigenpair (the threads of a warp work in lockstep, so every FP64 instruction serves up
+  //      to 32 eigenpairs).  Near-equal eigenvalues are orthogonalised (modified Gram-Schmidt).
+  double* lam = rc;
+  double* e2 = rs;
+  __shared__ double glo, ghi, pivmin, tiny;
+  if (tid == 0) {
+    double lo = 1e300, hi = -1e300, emax = 0.0, dmax = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const double r = (i > 0 ? fabs(e[i - 1]) : 0.0) + (i + 1 < n ? fabs(e[i]) : 0.0);
+      lo = fmin(lo, d[i] - r);
+      hi = fmax(hi, d[i] + r);
+      dmax = fmax(dmax, fabs(d[i]));
+      if (i + 1 < n) {
+        e2[i] = e[i] * e[i];
+        emax = fmax(emax, e2[i]);
       }
-      __syncthreads();
-      const int st = qstate, nr = nrot, top = rot_lo;
-      // every thread has read the shared step state before thread 0 may write the next one
-      __syncthreads();
-      if (st != 1) break;
-      for (int row = tid; row < n; row += nth) {
-        for (int q = 0; q < nr; ++q) {
-          const int i = top - q;
-          const double c = rc[q], s = rs[q];
-          const double zi = Z[(size_t)i * n + row], zi1 = Z[(size_t)(i + 1) * n + row];
-          Z[(size_t)(i + 1) * n + row] = s * zi + c * zi1;
-          Z[(size_t)i * n + row] = c * zi - s * zi1;
-        }
-      }
-      __syncthreads();
     }
-    if (flag == 2) break;
+    const double span = fmax(fabs(lo), fabs(hi));
+    glo = lo - 1e-14 * span - 1e-300;
+    ghi = hi + 1e-14 * span + 1e-300;
+    pivmin = 1e-290 * fmax(1.0, emax);
+    tiny = 2.2e-16 * fmax(1.0, fmax(dmax, sqrt(emax)));
+  }
+  __syncthreads();
+  for (int j = tid; j < nb; j += nth) {
+    // the j-th smallest eigenvalue: count(x) = number of eigenvalues below x (Sturm sequence
+    // of the LDL^T factorisation of T - x)
+    double a = glo, b = ghi;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (mid <= a || mid >= b || b - a <= 4.4e-16 * fmax(fabs(a), fabs(b)) + 2.0 * pivmin) break;
+      double q = d[0] - mid;
+      int cnt = q < 0.0;
+      for (int i = 1; i < n; ++i) {
+        if (fabs(q) < pivmin) q = -pivmin;
+        q = d[i] - mid - e2[i - 1] / q;
+        cnt += q < 0.0;
+      }
+      if (cnt > j) b = mid;
+      else a = mid;
+    }
+    lam[j] = 0.5 * (a + b);
+  }
+  __syncthreads();
+  double* XS = reinterpret_cast<double*>(X);   // x_j at XS + j n, pivots of T - lam_j at XS + (nb + j) n
+  for (int j = tid; j < nb; j += nth) {
+    double* x = XS + (size_t)j * n;
+    double* Dv = XS + (size_t)(nb + j) * n;
+    const double lj = lam[j];
+    double D = d[0] - lj;
+    if (fabs(D) < tiny) D = D < 0.0 ? -tiny : tiny;
+    Dv[0] = D;
+    for (int i = 1; i < n; ++i) {
+      D = d[i] - lj - e2[i - 1] / Dv[i - 1];
+      if (fabs(D) < tiny) D = D < 0.0 ? -tiny : tiny;
+      Dv[i] = D;
+    }
+    for (int i = 0; i < n; ++i) {   // start vector: a fixed pseudo-random pattern per (i, j)
+      const unsigned h = (unsigned)(i + 1) * 2654435761u ^ (unsigned)(j + 1) * 2246822519u;
+      x[i] = 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
+    }
+    for (int iter = 0; iter < 3; ++iter) {
+      for (int i = 1; i < n; ++i) x[i] -= (e[i - 1] / Dv[i - 1]) * x[i - 1];   // L y = b
+      x[n - 1] /= Dv[n - 1];                                                   // D z = y, L^T x = z
+      for (int i = n - 2; i >= 0; --i) x[i] = x[i] / Dv[i] - (e[i] / Dv[i]) * x[i + 1];
+      double nn = 0.0;
+      for (int i = 0; i < n; ++i) nn += x[i] * x[i];
+      if (!(nn > 0.0) || !isfinite(nn)) {
+        flag = 2;   // non-finite eigenvector: report, do not use
+        break;
+      }
+      const double inv = 1.0 / sqrt(nn);
+      for (int i = 0; i < n; ++i) x[i] *= inv;
+    }
   }
   __syncthreads();
   if (flag == 2) {
     if (tid == 0 && status != nullptr) status[k] = PWK_ERR_NUMERIC;
     return;
   }
-  // ---- 5. select the nb lowest; back-transform x = L^-H Q z
-  for (int i = tid; i < n; i += nth) {
-    int r = 0;
-    for (int j = 0; j < n; ++j) r += (d[j] < d[i]) || (d[j] == d[i] && j < i);
-    rank[i] = r;
+  // clusters of near-equal eigenvalues: orthogonalise in order (warp 0)
+  if (tid < 32) {
+    const double scale = fmax(1.0, fmax(fabs(lam[0]), fabs(lam[nb - 1])));
+    int c0 = 0;
+    for (int j = 1; j < nb; ++j) {
+      if (lam[j] - lam[j - 1] > 1e-9 * scale) {
+        c0 = j;
+        continue;
+      }
+      double* xj = XS + (size_t)j * n;
+      for (int q = c0; q < j; ++q) {
+        const double* xq = XS + (size_t)q * n;
+        double s = 0.0;
+        for (int i = tid; i < n; i += 32) s += xq[i] * xj[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        for (int i = tid; i < n; i += 32) xj[i] -= s * xq[i];
+        __syncwarp();
+      }
+      double nn = 0.0;
+      for (int i = tid; i < n; i += 32) nn += xj[i] * xj[i];
+      for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
+      const double inv = 1.0 / sqrt(nn);
+      for (int i = tid; i < n; i += 32) xj[i] *= inv;
+      __syncwarp();
+    }
   }
   __syncthreads();
-  for (int i = tid; i < n; i += nth)
-    if (rank[i] < nb) eps[k * nb + rank[i]] = d[i];
+  // ---- 5. back-transform x = L^-H Q z of the selected vectors
+  for (int j = tid; j < nb; j += nth) eps[k * nb + j] = lam[j];
   double2* E = ev + (size_t)k * ld * nb;
   // one warp per selected vector
   const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
-  for (int i = 0; i < n; ++i) {
-    const int j = rank[i];
-    if (j >= nb || (i % nw) != warp) continue;
+  for (int j = warp; j < nb; j += nw) {
     // y = z (real) in E[:, j]
-    for (int r = lane; r < n; r += 32) E[r * nb + j] = make_double2(Z[(size_t)i * n + r], 0.0);
+    for (int r = lane; r < n; r += 32) E[r * nb + j] = make_double2(XS[(size_t)j * n + r], 0.0);
     __syncwarp();
     // y = H_0 H_1 ... H_{n-2} y : apply H_{n-2} first
     for (int h = n - 2; h >= 0; --h) {

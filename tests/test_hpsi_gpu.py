@@ -178,8 +178,8 @@ def test_every_launch_shape_gives_identical_results(precision):
     tol = TOL64 if precision == "fp64" else TOL32
     outs = {}
     for kind in (0, 1):
-        for T in (128, 192, 256):
-            for L in (24, 12, 8, 5):
+        for T in (96, 128, 192, 256):
+            for L in (24, 12, 8, 6, 5):
                 try:
                     plan.set_launch_shape(prec, kind, T, L)
                 except pwk.PwkError as e:
