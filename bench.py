@@ -116,6 +116,12 @@ def algorithmic_flops_per_band(prob, nstick_mean: float, P: int) -> float:
     return fft + 2.0 * N ** 3 + 16.0 * prob.nkb * npw + 2.0 * npw
 
 
+def kernel_name(N: int, shape) -> str:
+    """Name of the H|psi> kernel the plan launches for a (kind, threads, L, smem) shape."""
+    return (f"fused_window_kernel<float,float,{N},{N // 4}>" if shape[0] == 1
+            else f"fused_kernel<float,float,{N},false>")
+
+
 def stick_stats(prob):
     ns = []
     m1 = []
@@ -212,6 +218,7 @@ def run_ours(args, rank, world, local_rank):
 
     nstick_mean, P = stick_stats(prob)
     flops = algorithmic_flops_per_band(prob, nstick_mean, P) * nbk
+    shape32 = plan.launch_shape(pwk.PWK_FP32)
     pk = peaks()
     achieved_tf = flops / kern_s / 1e12
     res = {
@@ -237,7 +244,8 @@ def run_ours(args, rank, world, local_rank):
         "p99_ms_per_step": float(np.percentile(np.array(t32) * 1e3, 99)),
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": pk["fp32_tflops"],
                      "unit": "TFLOP/s", "frac": achieved_tf / pk["fp32_tflops"], "traffic": None,
-                     "kernel": "fused_kernel<float,float,24> (FP32 CUDA-core FMA)",
+                     "kernel": kernel_name(prob.N, shape32) + " (FP32 CUDA-core FMA)",
+                     "launch_shape": {"threads": shape32[1], "l3_chunk": shape32[2], "smem": shape32[3]},
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz",
                      "hbm_gbs_achieved": algorithmic_bytes_per_band(prob, 8) * nbk / kern_s / 1e9,
                      "hbm_peak_gbs": pk["hbm_gbs"]},
@@ -338,6 +346,31 @@ def run_solvers(dev, stream, quick=False):
     return out
 
 
+def run_serving(n_jobs=40, rate_hz=200.0):
+    """Serving: a seeded Poisson stream of mixed jobs (60% H|psi>, 25% Davidson, 15%
+    Sternheimer) on fcc / simple-cubic cells, admitted by HBM footprint into 4 overlapping
+    slots with H|psi> coalescing, against the same jobs run one at a time in FP64
+    (one slot, no coalescing, FP64 Davidson / Sternheimer)."""
+    from paper_2412_01695_gb300 import serve
+    jobs = serve.random_mix(n_jobs, rate_hz=rate_hz, seed=2024, max_nk=27, max_nb=16,
+                            ecut_range=(25.0, 40.0))
+    copy = lambda js: [serve.Job(j.jid, j.kind, j.cell, j.nb, arrival=j.arrival) for j in js]  # noqa: E731
+    ex = serve.GpuExecutor(slots=4)
+    ex.prepare(jobs)
+    srv = serve.Server(ex, hbm_budget=32 << 30, slots=4, estimate=serve.estimate_for)
+    done = srv.run(copy(jobs), realtime=True)
+    st = serve.latency_stats(done)
+    ex1 = serve.GpuExecutor(slots=1)
+    ex1.prepare(jobs)
+    one = serve.Server(ex1, hbm_budget=32 << 30, slots=1, estimate=serve.estimate_for,
+                       coalesce=False).run(copy(jobs), realtime=True)
+    st1 = serve.latency_stats(one)
+    return {"jobs": n_jobs, "rate_hz": rate_hz,
+            "mix": {k: sum(j.kind == k for j in jobs) for k in ("hpsi", "davidson", "sternheimer")},
+            "continuous": st, "one_at_a_time": st1,
+            "p99_speedup": st1.get("p99_s", float("nan")) / st.get("p99_s", float("nan"))}
+
+
 def cpu_baseline(prob, gpu_out, budget_s=20.0):
     """The FP64 oracle (dense H per k) on the host cores, on a seeded sample of k-points."""
     from oracle import hamiltonian as ham
@@ -404,6 +437,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solvers", action="store_true", help="skip the solver time-to-solution section")
     ap.add_argument("--quick", action="store_true", help="smaller solver samples")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop section")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -423,6 +457,8 @@ def main():
                           quick=args.quick)
         eig_mixed = sol.pop("_eig_mixed", None)
         res.update(sol)
+        if not args.no_serving:
+            res["serving"] = run_serving(n_jobs=20 if args.quick else 40)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gpu_out = out32.cpu().numpy().astype(np.complex128)
         # the oracle runs on the same (FP32-rounded) input the GPU path saw

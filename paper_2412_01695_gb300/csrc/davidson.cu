@@ -498,8 +498,8 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
     set_error("npw_max too large for the Gram kernel (2 vectors in shared memory)");
     return PWK_ERR_UNSUPPORTED;
   }
-  if (gram_smem > 48 * 1024)
-    cudaFuncSetAttribute(gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gram_smem);
+  if (cudaError_t e = allow_full_smem(gram_kernel); e != cudaSuccess)
+    return cuda_fail(e, "cudaFuncSetAttribute(gram)");
   long long napply[2] = {0, 0};
   int total = 0, given_up = 0, host_dbg[4] = {0, 0, 0, 0};
   bool dumped = false;

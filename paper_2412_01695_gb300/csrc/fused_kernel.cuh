@@ -277,8 +277,7 @@ int launch_fused(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, c
 #define PWK_CASE(n)                                                                             \
   case n: {                                                                                     \
     auto kern = fused_kernel<T, TI, n, CPLXV>;                                                  \
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                         (int)s.smem);                                          \
+    cudaError_t e = allow_full_smem(kern);                                                      \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");                   \
     kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \
     e = cudaGetLastError();                                                                     \

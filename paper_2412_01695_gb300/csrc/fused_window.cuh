@@ -222,8 +222,7 @@ int launch_window(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, 
 #define PWK_WCASE(n)                                                                            \
   case n: {                                                                                     \
     auto kern = fused_window_kernel<T, TI, n, window_of(n)>;                                    \
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
-                                         (int)s.smem);                                          \
+    cudaError_t e = allow_full_smem(kern);                                                     \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(window)");                  \
     kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \
     e = cudaGetLastError();                                                                     \

@@ -658,9 +658,9 @@ int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int
     goto fail;
   }
   TRY(build_window_tables(p));
-  TRYC(cudaDeviceSynchronize(), "plan setup");
+  TRYC(cudaStreamSynchronize(cudaStreamLegacy), "plan setup");
   for (int prec = 0; prec < 3; ++prec) TRY(autotune_shape(p, prec));
-  TRYC(cudaDeviceSynchronize(), "plan setup");
+  TRYC(cudaStreamSynchronize(cudaStreamLegacy), "plan setup");
   cudaFree(d_miller);
   cudaFree(d_B);
   cudaFree(d_vsum);

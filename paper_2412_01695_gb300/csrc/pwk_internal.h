@@ -16,6 +16,18 @@ namespace pwk {
 void set_error(const std::string& msg);  // thread-local detail for pwk_last_error_detail()
 int cuda_fail(cudaError_t e, const char* what);
 
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum.  The value
+// set never depends on the launch, so host threads that launch the same kernel at the same
+// time (one per stream in a serving loop) cannot lower the limit under one another's launch.
+template <typename K>
+inline cudaError_t allow_full_smem(K kern) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  return e;
+}
+
 // Device tables that place the coefficients of one sphere (input) on the FFT sticks and
 // gather the coefficients of another (output) back: for H|psi> the two are the same
 // sphere; for the DFPT right-hand side the input is the k sphere and the output the k+q one.
