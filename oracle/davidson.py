@@ -1,14 +1,15 @@
 """Oracle: block Davidson diagonalisation of one k (TEST INFRASTRUCTURE ONLY).
 
-Follows the steps of paper Sec. 2.1 in order, with S = I (norm-conserving projectors, no
-q_mn), in FP64, for one k at a time.  The reduced generalized problem (H~ - eps S~) v = 0
+Follows the steps of paper Sec. 2.1 in order, in FP64, for one k at a time, with S = I
+(norm-conserving projectors) unless an overlap operator S is passed (ultrasoft/PAW q_mn,
+Sec. 2.2; oracle/overlap.py builds it).  The reduced generalized problem (H~ - eps S~) v = 0
 is solved with LAPACK (scipy.linalg.eigh), which the paper also uses for this step
 (Sec. 6, ZHEGV/ZHEGVX).  ``lowest_eigenpairs`` is the exact result the iteration reaches.
 
 Readings of points the paper leaves open (listed with the design notes):
-  * the preconditioner denominator x = H_GG - eps_i is clamped to sign(x) max(|x|, 1e-2 Ry);
+  * the preconditioner denominator x = H_GG - eps_i S_GG is clamped to sign(x) max(|x|, 1e-2 Ry);
   * a band is converged when |eps_i^(n+1) - eps_i^(n)| < eps_th; an optional residual
-    bound ||H phi - eps phi|| < res_tol may be required as well;
+    bound ||H phi - eps S phi|| < res_tol may be required as well;
   * a restart keeps the current Ritz vectors (the "restart with {phi^(n+1), eps^(n+1)}" step);
   * when the preconditioned residual is numerically parallel to its Ritz vector
     (|cos| > 1 - 1e-6, which happens when H is diagonal in the plane-wave basis and the
@@ -50,10 +51,10 @@ def _reduced_eig(Hr, Sr, nb, drop_tol=1e-9):
     return w[:nb], full
 
 
-def _reduced(basis, hbasis):
-    # H~_ij = <phi_i|H|phi_j>, S~_ij = <phi_i|S|phi_j> with S = I (Sec. 2.1)
+def _reduced(basis, hbasis, sbasis):
+    # H~_ij = <phi_i|H|phi_j>, S~_ij = <phi_i|S|phi_j> (Sec. 2.1)
     Hr = basis.conj() @ hbasis.T
-    Sr = basis.conj() @ basis.T
+    Sr = basis.conj() @ sbasis.T
     return 0.5 * (Hr + Hr.conj().T), 0.5 * (Sr + Sr.conj().T)
 
 
@@ -63,30 +64,37 @@ def _precondition_denominator(x: np.ndarray, floor: float = 1e-2) -> np.ndarray:
 
 
 def davidson(apply_h, h_diag: np.ndarray, psi0: np.ndarray, eth: float = 1e-10,
-             max_iter: int = 100, max_basis: int = None, res_tol: float = None):
+             max_iter: int = 100, max_basis: int = None, res_tol: float = None,
+             apply_s=None, s_diag: np.ndarray = None):
     """Block Davidson (Sec. 2.1) for one k.
 
     apply_h(X) -> H X for rows X (n, npw); h_diag (npw,) the diagonal of H in the plane-wave
-    basis; psi0 (nb, npw) trial vectors.  Returns (eps (nb,), psi (nb, npw), iterations,
-    number of H applications, converged flags)."""
+    basis; psi0 (nb, npw) trial vectors; apply_s / s_diag the overlap S and its diagonal
+    (None: S = I).  Returns (eps (nb,), psi (nb, npw) S-orthonormal, iterations, number of
+    H applications, converged flags)."""
     nb = psi0.shape[0]
     if max_basis is None:
         max_basis = 4 * nb
+    if apply_s is None:
+        apply_s = lambda X: X  # noqa: E731
+        s_diag = np.ones_like(h_diag)
     basis = psi0.astype(np.complex128).copy()
     hbasis = apply_h(basis)
+    sbasis = apply_s(basis)
     napply = nb
     # 1. reduced problem on the trial vectors, eigenpairs {phi^(n), eps^(n)}
-    Hr, Sr = _reduced(basis, hbasis)
+    Hr, Sr = _reduced(basis, hbasis, sbasis)
     eps, vecs = _reduced_eig(Hr, Sr, nb)
     todo = np.arange(nb)                    # the first step corrects every band
     conv = np.zeros(nb, bool)
     it = 0
     for it in range(1, max_iter + 1):
-        # 2. correction vectors (H_diag - eps_i S_diag)^-1 (H - eps_i S)|phi_i>, S_diag = 1
+        # 2. correction vectors (H_diag - eps_i S_diag)^-1 (H - eps_i S)|phi_i>
         ritz = vecs[:, todo].T @ basis
         hritz = vecs[:, todo].T @ hbasis
-        resid = hritz - eps[todo, None] * ritz
-        corr = resid / _precondition_denominator(h_diag[None, :] - eps[todo, None])
+        sritz = vecs[:, todo].T @ sbasis
+        resid = hritz - eps[todo, None] * sritz
+        corr = resid / _precondition_denominator(h_diag[None, :] - eps[todo, None] * s_diag[None, :])
         cos = np.abs(np.sum(ritz.conj() * corr, axis=1)) / (
             np.linalg.norm(ritz, axis=1) * np.linalg.norm(corr, axis=1))
         parallel = cos > 1.0 - 1e-6
@@ -97,18 +105,20 @@ def davidson(apply_h, h_diag: np.ndarray, psi0: np.ndarray, eth: float = 1e-10,
         if basis.shape[0] + len(todo) > max_basis:
             basis = vecs.T @ basis
             hbasis = vecs.T @ hbasis
+            sbasis = vecs.T @ sbasis
         # 4. extended reduced Hamiltonian and overlap
         basis = np.vstack([basis, corr])
         hbasis = np.vstack([hbasis, apply_h(corr)])
+        sbasis = np.vstack([sbasis, apply_s(corr)])
         napply += len(todo)
-        Hr, Sr = _reduced(basis, hbasis)
+        Hr, Sr = _reduced(basis, hbasis, sbasis)
         # 5. diagonalise the N_base x N_base reduced problem
         eps_new, vecs = _reduced_eig(Hr, Sr, nb)
         # 6. bands whose eigenvalue moved by more than eps_th still need a correction
         moved = np.abs(eps_new - eps) > eth
         if res_tol is not None:
-            ritz = vecs.T @ basis
-            rn = np.linalg.norm(vecs.T @ hbasis - eps_new[:, None] * ritz, axis=1)
+            sritz = vecs.T @ sbasis
+            rn = np.linalg.norm(vecs.T @ hbasis - eps_new[:, None] * sritz, axis=1)
             moved |= rn > res_tol
         eps = eps_new
         todo = np.nonzero(moved)[0]

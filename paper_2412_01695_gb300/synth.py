@@ -31,7 +31,7 @@ from typing import Optional, Sequence
 import numpy as np
 
 SEED_BASE = 2412016950
-STREAMS = {"V": 0, "beta": 1, "D": 2, "psi": 3, "dv": 4, "tau": 5}
+STREAMS = {"V": 0, "beta": 1, "D": 2, "psi": 3, "dv": 4, "tau": 5, "q": 6}
 
 
 def rng_for(cfg_id: int, stream: str) -> np.random.Generator:
@@ -131,6 +131,26 @@ def random_D(rng: np.random.Generator, nat: int, lset: Sequence[int]) -> np.ndar
         blk = np.triu(blk) + np.triu(blk, 1).T
         D[ia * npa:(ia + 1) * npa, ia * npa:(ia + 1) * npa] = blk
     return D
+
+
+def random_q(rng: np.random.Generator, nat: int, lset: Sequence[int], scale: float = 20.0) -> np.ndarray:
+    """Block-diagonal real symmetric positive semi-definite q (ultrasoft/PAW augmentation
+    coefficients): one block scale * R R^T / n per atom, R with U(-1,1) entries.  With the
+    Gaussian projectors of this generator S = 1 + sum beta q beta^* then has eigenvalues in
+    about [1, 3]; positive semi-definite q keeps S positive definite for any projector set."""
+    npa = sum(2 * l + 1 for l in lset)
+    q = np.zeros((nat * npa, nat * npa))
+    for ia in range(nat):
+        R = rng.uniform(-1.0, 1.0, size=(npa, npa))
+        q[ia * npa:(ia + 1) * npa, ia * npa:(ia + 1) * npa] = scale * (R @ R.T) / npa
+    return q
+
+
+def q_for(cfg: int) -> np.ndarray:
+    """The augmentation coefficients q of a synthetic cell (ultrasoft/PAW variant)."""
+    c = CONFIGS[cfg]
+    _, tau = cell_for(cfg)
+    return random_q(rng_for(cfg, "q"), len(tau), c["lset"])
 
 
 # ----------------------------------------------------------------------------- fields on the grid
