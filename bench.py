@@ -105,15 +105,34 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------- work
-def algorithmic_flops_per_band(prob, nstick_mean: float, P: int) -> float:
-    """5 n log2 n per 1D transform of the pruned pair (z on the sticks, y on the carried
-    m1 planes, x on every line; inverse and forward), 2 N_r for V(r) u(r), 16 nkb npw for
-    the two projector contractions (Eqs. lambdah and finalnl), 2 npw kinetic."""
+def local_flops_per_band(prob, nstick_mean: float, P: int) -> float:
+    """Fused local kernel: 5 n log2 n per 1D transform of the pruned pair (z on the sticks,
+    y on the carried m1 planes, x on every line; inverse and forward), 2 N_r for V(r) u(r),
+    2 npw for the kinetic term."""
     N = prob.N
     f1 = 5.0 * N * math.log2(N)
     fft = f1 * 2.0 * (nstick_mean + P * N + N * N)
     npw = float(np.mean(prob.npw))
-    return fft + 2.0 * N ** 3 + 16.0 * prob.nkb * npw + 2.0 * npw
+    return fft + 2.0 * N ** 3 + 2.0 * npw
+
+
+def algorithmic_flops_per_band(prob, nstick_mean: float, P: int) -> float:
+    """Whole H application: the local kernel plus 16 nkb npw for the two projector
+    contractions (Eqs. lambdah and finalnl)."""
+    npw = float(np.mean(prob.npw))
+    return local_flops_per_band(prob, nstick_mean, P) + 16.0 * prob.nkb * npw
+
+
+def nonlocal_bytes_per_band(prob, elem_bytes: int) -> float:
+    """Projector kernels: read C (projection), read and write H C (add-back), and beta(k)
+    twice per k-point (once per kernel) shared by its bands."""
+    npw = float(np.mean(prob.npw))
+    return 3.0 * npw * elem_bytes + 2.0 * prob.nkb * npw * elem_bytes / prob.nb
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the kernel, from the ncu
+# capture summarised in profiles/ (None once the kernel has changed since the capture)
+TRAFFIC = {}
 
 
 def kernel_name(N: int, shape) -> str:
@@ -217,10 +236,25 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = float(np.mean(te2e))
 
     nstick_mean, P = stick_stats(prob)
-    flops = algorithmic_flops_per_band(prob, nstick_mean, P) * nbk
     shape32 = plan.launch_shape(pwk.PWK_FP32)
     pk = peaks()
-    achieved_tf = flops / kern_s / 1e12
+    # the fused local kernel alone: the same cell with the projector set emptied, same launch
+    # shape (one launch per step); the projector kernels take the rest of the step
+    import copy
+    prob_loc = copy.copy(prob)
+    prob_loc.beta = np.ascontiguousarray(prob.beta[:, :0, :])
+    prob_loc.D = np.zeros((0, 0))
+    plan_loc = pwk.plan_from_problem(prob_loc, device=dev)
+    plan_loc.set_launch_shape(pwk.PWK_FP32, *shape32[:3])
+    t_loc = timed(lambda: pwk.hpsi_batched(plan_loc, pwk.PWK_FP32, psi32, out32, nb, stream),
+                  min(200, max(3, args.steps // 4)), 5)
+    plan_loc.close()
+    loc_s = float(np.mean(t_loc))
+    nl_s = max(kern_s - loc_s, 1e-12)
+    loc_flops = local_flops_per_band(prob, nstick_mean, P) * nbk
+    achieved_tf = loc_flops / loc_s / 1e12
+    flops = algorithmic_flops_per_band(prob, nstick_mean, P) * nbk
+    nl_gbs = nonlocal_bytes_per_band(prob, 8) * nbk / nl_s / 1e9
     res = {
         "metric": METRIC,
         "value": total_units / step_s,
@@ -243,16 +277,22 @@ def run_ours(args, rank, world, local_rank):
         "speedup_vs_per_k_fp64": float(np.mean(tpk)) / kern_s,
         "p99_ms_per_step": float(np.percentile(np.array(t32) * 1e3, 99)),
         "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": pk["fp32_tflops"],
-                     "unit": "TFLOP/s", "frac": achieved_tf / pk["fp32_tflops"], "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved_tf / pk["fp32_tflops"],
+                     "traffic": TRAFFIC.get(kernel_name(prob.N, shape32)),
                      "kernel": kernel_name(prob.N, shape32) + " (FP32 CUDA-core FMA)",
+                     "kernel_ms": loc_s * 1e3,
                      "launch_shape": {"threads": shape32[1], "l3_chunk": shape32[2], "smem": shape32[3]},
                      "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz",
+                     "step_tflops": flops / kern_s / 1e12,
                      "hbm_gbs_achieved": algorithmic_bytes_per_band(prob, 8) * nbk / kern_s / 1e9,
                      "hbm_peak_gbs": pk["hbm_gbs"]},
+        "roofline_nonlocal": {"bound": "hbm", "achieved": nl_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                              "frac": nl_gbs / pk["hbm_gbs"], "ms": nl_s * 1e3,
+                              "kernels": "nl_project_kernel + nl_addback_kernel (step time minus the local kernel)"},
         "e2e": {"value": nbk / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
                 "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size())},
-        "gpu_launches": args.steps,
+        "gpu_launches": 3 * args.steps,   # projections, local kernel, add-back per step
         "clocks": clocks,
     }
     plan.close()

@@ -106,12 +106,15 @@ int pwk_supported_grid(int N);
  *   kinetic |k+G|^2 C (Sec. 2.2.1), local V_eff by scatter G->r, inverse 3D transform,
  *   V(r) u(r), forward 3D transform with 1/N_r and gather r->G (Sec. 2.2.2, Sec. 5),
  *   nonlocal lambda = sum_G beta* C (Eq. lambdah), gamma = D lambda (Eq. gamma),
- *   add-back sum gamma beta (Eq. finalnl).  S = I (norm-conserving; no q_mn).
+ *   add-back sum gamma beta (Eq. finalnl).  S is not applied (pwk_hspsi_batched does).
  *   precision  PWK_FP64, PWK_FP32 or PWK_FP32_C128
  *   psi        device [nk][nb][npw_max] complex128 (complex64 for PWK_FP32)
  *   hpsi       device, same shape and type; may be the same pointer as psi (in place),
  *              must not otherwise overlap it
- * Asynchronous on `stream`. */
+ * Three launches on `stream` (projections, local and kinetic terms, nonlocal add-back); the
+ * projector coefficients between them (2 nkb complex per band-k) take scratch for the call
+ * from a stream-ordered memory pool the library keeps per device (memory returned to the
+ * pool stays mapped for later calls).  Asynchronous on `stream`. */
 int pwk_hpsi_batched(pwk_plan* plan, int precision, const void* psi, void* hpsi, int nb,
                      void* stream);
 
@@ -128,11 +131,35 @@ int pwk_hpsi_batched(pwk_plan* plan, int precision, const void* psi, void* hpsi,
 int pwk_hpsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, const int* items,
                    int nitems, int nvec_per_k, void* stream);
 
+/* ---------------------------------------------------------------------------- overlap S
+ * Ultrasoft / PAW overlap (paper Sec. 2.2):
+ *   S C = C + sum_{I,mn} q^I_mn beta^I_m <beta^I_n|C>  (Eqs. lambdah, delta_eq, finals),
+ * computed from the same projections lambda as the nonlocal term of H.
+ *
+ * pwk_plan_set_overlap: give the plan the coefficients q (host float64 [nkb][nkb], real
+ * symmetric; block diagonal per atom like D, not enforced) or remove them (q = NULL: S = 1).
+ * Copies q to the device (the caller keeps ownership of its array); synchronises the device.
+ * Returns PWK_ERR_INVALID for a non-finite or non-symmetric q.  A plan with q makes
+ * pwk_davidson_batched solve H x = eps S x and pwk_sternheimer_cg_batched use S (see there). */
+int pwk_plan_set_overlap(pwk_plan* plan, const double* q);
+/* 1 if the plan holds overlap coefficients q, else 0. */
+int pwk_plan_has_overlap(const pwk_plan* plan);
+
+/* pwk_hspsi_batched / pwk_hspsi_items: H C and S C together (one projection serves both),
+ * same arguments as pwk_hpsi_batched / pwk_hpsi_items plus
+ *   spsi   device, same shape and type as psi: S psi out (padding written as zero).
+ * psi, hpsi and spsi must be three distinct, non-overlapping buffers (PWK_ERR_INVALID if two
+ * pointers are equal).  Without q, S = 1 and spsi = psi.  Asynchronous on `stream`. */
+int pwk_hspsi_batched(pwk_plan* plan, int precision, const void* psi, void* hpsi, void* spsi,
+                      int nb, void* stream);
+int pwk_hspsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, void* spsi,
+                    const int* items, int nitems, int nvec_per_k, void* stream);
+
 /* ---------------------------------------------------------------------------- Davidson
  * pwk_davidson_batched: lowest nb eigenpairs of H(k) for every k of the plan by the block
  * Davidson iteration of Sec. 2.1, run for all k at once (Algorithm 2):
- *   Rayleigh-Ritz on the basis (H~ = <phi|H|phi>, S~ = <phi|phi>, FP64 Cholesky of S~ and
- *   Hermitian eigensolve, Sec. 6), correction vectors (H_diag - eps)^-1 (H - eps) phi,
+ *   Rayleigh-Ritz on the basis (H~ = <phi|H|phi>, S~ = <phi|S|phi>, FP64 Cholesky of S~ and
+ *   Hermitian eigensolve, Sec. 6), correction vectors (H_diag - eps S_diag)^-1 (H - eps S) phi,
  *   normalisation, basis expansion, restart with the Ritz vectors when the basis would
  *   exceed max_basis, per-band test |eps^(n+1) - eps^(n)| > eth.
  *   mode     PWK_FP64: every H application in FP64.
@@ -142,7 +169,7 @@ int pwk_hpsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, c
  *            iterations; then the Ritz vectors get FP64 H applications and the iteration
  *            continues in FP64 to eth and res_tol (FP64 refinement).
  *            Reduced matrices, the eigensolve, norms and residuals are FP64 in both modes.
- *   psi      device [nk][nb][npw_max] complex128: trial vectors in, eigenvectors out
+ *   psi      device [nk][nb][npw_max] complex128: trial vectors in, eigenvectors out (S-orthonormal)
  *   eig      device [nk][nb] float64: eigenvalues out (Ry), ascending per k
  *   eth      eigenvalue threshold (Ry), > 0
  *   res_tol  if > 0, a band also needs ||H phi - eps phi|| < res_tol to be converged
@@ -159,14 +186,14 @@ int pwk_davidson_batched(pwk_plan* plan, int mode, void* psi, double* eig, int n
 /* pwk_eigh_batched: the batched generalized Hermitian eigensolver of the Davidson reduced
  * problem as a stand-alone call (paper Sec. 6: ZHEGV for many k-points at once).  For each
  * problem p < nprob: H_p v = eps S_p v, the nev lowest eigenpairs, FP64, one CTA per problem
- * (Cholesky of S, reduction to standard form, Householder tridiagonalisation, implicit QL).
+ * (Cholesky of S, reduction to standard form, Householder tridiagonalisation, bisection and inverse iteration).
  *   H, S    device complex128 [nprob][n][n], row-major, full Hermitian; S positive definite
  *   eig     device float64 [nprob][nev], ascending
  *   vec     device complex128 [nprob][n][nev]: column j is the eigenvector of eig[p][j],
  *           S-orthonormal
  *   status  device int [nprob] or NULL: 0, PWK_ERR_NOT_POSDEF (one of the first nev rows of
- *           S is dependent on the earlier ones) or PWK_ERR_NUMERIC (QL did not converge)
- * A row j >= nev whose Cholesky pivot falls below 1e-9 S_jj is treated as dependent and left
+ *           S is dependent on the earlier ones) or PWK_ERR_NUMERIC (non-finite eigenvector)
+ * A row j >= nev whose Cholesky pivot falls below 1e-6 S_jj is treated as dependent and left
  * out of the problem (its eigenvector entries are zero).  1 <= nev <= n <= 160.
  * Allocates a workspace of 3 n^2 complex128 per problem for the call and synchronises
  * `stream` before returning. */
@@ -192,10 +219,12 @@ int pwk_eigh_batched_noalloc(int nprob, int n, int nev, const void* H, const voi
 
 /* ---------------------------------------------------------------------------- Sternheimer
  * pwk_sternheimer_cg_batched: for every k of plan_k and every occupied band n, solve the
- * DFPT linear system of Eq. linear_system with S = I and dS = 0,
- *   [H_{k+q} + alpha_k P_v - eps_{k,n}] dpsi_{k,n} = - P_c dV psi_{k,n},
- * P_v = sum_{v < nocc} |psi_{k+q,v}><psi_{k+q,v}| (Eq. projector, Eqs. compute_mu,
- * use_mu with S = I), P_c = 1 - P_v, dV = e^{iq.r} dv(r), by the preconditioned CG of
+ * DFPT linear system of Eq. linear_system with dS = 0 (a local perturbation dv),
+ *   [H_{k+q} + alpha_k Q - eps_{k,n} S] dpsi_{k,n} = -(1 - S P_v) dV psi_{k,n},
+ * Q = sum_{v < nocc} S|psi_{k+q,v}><psi_{k+q,v}|S (Eq. projector, Eqs. compute_mu, use_mu,
+ * apply_s_ch), P_v = sum_v |psi_{k+q,v}><psi_{k+q,v}|, dV = e^{iq.r} dv(r); S is the
+ * overlap of plan_kq (S = 1 without q: [H + alpha P_v - eps] dpsi = -P_c dV psi; with q the
+ * psi_{k+q,v} must be S-orthonormal), by the preconditioned CG of
  * Sec. 2.4 (Eqs. ax1 .. updatedold) for all (k, n) at once (Algorithm 4), with the
  * preconditioner M_GG = max(1, |k+q+G|^2 / <psi_{k+q,n}|T|psi_{k+q,n}>).
  *   plan_kq   plan of the k+q points (the operator); plan_k  plan of the k points; both

@@ -16,7 +16,8 @@ Readings of points the paper leaves open (listed with the design notes):
     diagonal preconditioner is exact) the unpreconditioned residual is used instead, so the
     correction always brings a new direction;
   * basis vectors that are numerically dependent on the earlier ones (the Cholesky pivot of
-    S~ below 1e-9 of its diagonal) are left out of the reduced problem.
+    S~ below 1e-6 of its diagonal, a new direction below 1e-3 of the vector's norm) are
+    left out of the reduced problem.
 """
 from __future__ import annotations
 
@@ -30,7 +31,7 @@ def lowest_eigenpairs(H: np.ndarray, nb: int):
     return w[:nb], v[:, :nb].T
 
 
-def _reduced_eig(Hr, Sr, nb, drop_tol=1e-9):
+def _reduced_eig(Hr, Sr, nb, drop_tol=1e-6):
     """Lowest nb eigenpairs of (H~ - eps S~) v = 0 on the basis vectors that are independent:
     a vector whose Cholesky pivot falls below drop_tol of its S~ diagonal is left out (its
     coefficients are zero)."""

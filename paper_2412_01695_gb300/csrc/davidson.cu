@@ -13,8 +13,8 @@
 //   gram    : new rows/columns of H~ and S~ (FP64 dot products)
 //   rr      : batched FP64 generalized eigensolve (rr.cu)
 // The host only reads one counter per iteration (bands left) to decide whether to stop.
-// A k-point whose reduced problem fails (S~ numerically singular in its leading block, or QL
-// not converging) drops the vectors of that step and restarts from its Ritz vectors; after
+// A k-point whose reduced problem fails (S~ numerically singular in its leading block, or a
+// non-finite eigenvector) drops the vectors of that step and restarts from its Ritz vectors; after
 // more than three failures it is given up and its bands are reported unconverged.
 // Mixed mode: each k-point applies H in FP32 until its bands stop moving by more than
 // max(eth, 1e-4 Ry) (and ||r|| < max(res_tol, 1e-3)); then its Ritz vectors get FP64 H
@@ -32,7 +32,10 @@ namespace pwk {
 
 struct DavWork {
   int nk = 0, nb = 0, MB = 0, npw_max = 0;
+  bool with_s = false;   // overlap S (plan with q): S phi kept beside H phi
   double2 *phi = nullptr, *hphi = nullptr, *corr = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;
+  double2 *sphi = nullptr, *tmp3 = nullptr;
+  double* sdiag = nullptr;
   double2 *Hr = nullptr, *Sr = nullptr, *W = nullptr, *ev = nullptr;
   double *eps = nullptr, *eps_new = nullptr, *hdiag = nullptr, *rnorm = nullptr;
   int *nbase = nullptr, *nnc = nullptr, *todo = nullptr, *active = nullptr, *moved = nullptr;
@@ -57,7 +60,8 @@ static int dalloc(pwk_plan* p, DavWork* w, T** ptr, size_t n) {
 }
 
 static int ensure_dav_work(pwk_plan* p, int nb, int MB) {
-  if (p->dav && p->dav->nb == nb && p->dav->MB == MB) return PWK_OK;
+  const bool with_s = p->d_q != nullptr;
+  if (p->dav && p->dav->nb == nb && p->dav->MB == MB && p->dav->with_s == with_s) return PWK_OK;
   destroy_dav_work(p);
   DavWork* w = new DavWork();
   p->dav = w;
@@ -65,8 +69,14 @@ static int ensure_dav_work(pwk_plan* p, int nb, int MB) {
   w->nb = nb;
   w->MB = MB;
   w->npw_max = p->npw_max;
+  w->with_s = with_s;
   const size_t nk = p->nk, np = p->npw_max;
   int rc;
+  if (with_s && ((rc = dalloc(p, w, &w->sphi, nk * MB * np)) || (rc = dalloc(p, w, &w->tmp3, nk * nb * np)) ||
+                 (rc = dalloc(p, w, &w->sdiag, nk * np)))) {
+    destroy_dav_work(p);
+    return rc;
+  }
   if ((rc = dalloc(p, w, &w->phi, nk * MB * np)) || (rc = dalloc(p, w, &w->hphi, nk * MB * np)) ||
       (rc = dalloc(p, w, &w->corr, nk * nb * np)) || (rc = dalloc(p, w, &w->tmp1, nk * nb * np)) ||
       (rc = dalloc(p, w, &w->tmp2, nk * nb * np)) || (rc = dalloc(p, w, &w->Hr, nk * MB * MB)) ||
@@ -109,27 +119,34 @@ __device__ double bsum(double v, double* red) {
 }
 
 // H_diag(G) = |k+G|^2 + <V> + sum_mn beta_m(G) D_mn conj(beta_n(G))   (diagonal of H in PWs)
+// S_diag(G) = 1 + sum_mn beta_m(G) q_mn conj(beta_n(G))   (when q is given; Sec. 2.1)
 __global__ void hdiag_kernel(int nk, int np, int nkb, const int* npw, const double* g2,
-                             double vmean, const double2* beta, const double* D, double* hd) {
+                             double vmean, const double2* beta, const double* D, double* hd,
+                             const double* q, double* sd) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= (size_t)nk * np) return;
   const int k = (int)(i / np), g = (int)(i % np);
   if (g >= npw[k]) {
     hd[i] = 0.0;
+    if (sd != nullptr) sd[i] = 1.0;
     return;
   }
-  double s = g2[i] + vmean;
+  double s = g2[i] + vmean, so = 1.0;
   const double2* b = beta + (size_t)k * nkb * np + g;
   for (int m = 0; m < nkb; ++m) {
     const double2 bm = b[(size_t)m * np];
     for (int n = 0; n < nkb; ++n) {
       const double dmn = D[m * nkb + n];
-      if (dmn == 0.0) continue;
+      const double qmn = q != nullptr ? q[m * nkb + n] : 0.0;
+      if (dmn == 0.0 && qmn == 0.0) continue;
       const double2 bn = b[(size_t)n * np];
-      s += dmn * (bm.x * bn.x + bm.y * bn.y);   // Re(beta_m conj(beta_n))
+      const double re = bm.x * bn.x + bm.y * bn.y;   // Re(beta_m conj(beta_n))
+      s += dmn * re;
+      so += qmn * re;
     }
   }
   hd[i] = s;
+  if (sd != nullptr) sd[i] = so;
 }
 
 // copy nv vectors per k between arrays with different per-k strides
@@ -161,11 +178,12 @@ __global__ void items_kernel(int nk, int nb, const int* active, const int* base,
 
 // New columns b = base + t (t < cnt) of H~ and S~: rows a < base + cnt.  Each (a, b) is
 // written by one CTA (rows a >= base only for a <= b) together with its mirror (b, a).
+// S~_ab = <phi_a|S phi_b> with sphi = S phi (sphi = phi when S = 1).
 __global__ void __launch_bounds__(256) gram_kernel(int nb, int MB, int np, const int* npw,
                                                    const int* active, const int* base,
                                                    int base_const, const int* cnt, int cnt_const,
                                                    const double2* phi, const double2* hphi,
-                                                   double2* Hr, double2* Sr) {
+                                                   const double2* sphi, double2* Hr, double2* Sr) {
   const int k = blockIdx.x / nb, t = blockIdx.x % nb;
   if (!active[k]) return;
   const int b0 = base ? base[k] : base_const, c = cnt ? cnt[k] : cnt_const;
@@ -176,8 +194,9 @@ __global__ void __launch_bounds__(256) gram_kernel(int nb, int MB, int np, const
   double2* hb = sh + np;
   const double2* P = phi + (size_t)k * MB * np;
   const double2* HP = hphi + (size_t)k * MB * np;
+  const double2* SP = sphi + (size_t)k * MB * np;
   for (int g = threadIdx.x; g < n; g += blockDim.x) {
-    pb[g] = P[(size_t)b * np + g];
+    pb[g] = SP[(size_t)b * np + g];
     hb[g] = HP[(size_t)b * np + g];
   }
   __syncthreads();
@@ -241,16 +260,18 @@ __global__ void __launch_bounds__(256) rotate_kernel(int nb, int MB, int np, con
   }
 }
 
-// Correction vector of band i (Sec. 2.1): r = sum_j v_ji (H phi_j - eps_i phi_j),
-// c = r / clamp(H_diag - eps_i), c /= ||c||.  ||r|| is stored for the residual test.  When c
-// is numerically parallel to the Ritz vector (|cos| > 1 - 1e-6: H diagonal in plane waves,
-// exact preconditioner) the unpreconditioned r is used, so the correction is a new direction.
+// Correction vector of band i (Sec. 2.1): r = sum_j v_ji (H phi_j - eps_i S phi_j),
+// c = r / clamp(H_diag - eps_i S_diag), c /= ||c||.  ||r|| is stored for the residual test.
+// When c is numerically parallel to the Ritz vector (|cos| > 1 - 1e-6: H diagonal in plane
+// waves, exact preconditioner) the unpreconditioned r is used, so the correction is a new
+// direction.  sphi = phi and sdiag = null when S = 1.
 __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, const int* npw,
                                                     const int* nbase, const int* active,
                                                     const int* moved, int all_bands,
                                                     const double2* ev, const double* eps,
                                                     const double2* phi, const double2* hphi,
-                                                    const double* hdiag, double2* corr,
+                                                    const double2* sphi, const double* hdiag,
+                                                    const double* sdiag, double2* corr,
                                                     double* rnorm) {
   const int k = blockIdx.x / nb, i = blockIdx.x % nb;
   if (!active[k]) return;
@@ -263,14 +284,16 @@ __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, cons
   const double e = eps[k * nb + i];
   const double2* P = phi + (size_t)k * MB * np;
   const double2* HP = hphi + (size_t)k * MB * np;
+  const double2* SP = sphi + (size_t)k * MB * np;
   double2* out = corr + ((size_t)k * nb + i) * np;
   const double* hd = hdiag + (size_t)k * np;
+  const double* sdk = sdiag != nullptr ? sdiag + (size_t)k * np : nullptr;
   double rr = 0.0, cc = 0.0, zz = 0.0, zcx = 0.0, zcy = 0.0;
   for (int g = threadIdx.x; g < npk; g += blockDim.x) {
     double rx = 0, ry = 0, zx = 0, zy = 0;
     for (int j = 0; j < n; ++j) {
-      const double2 hp = HP[(size_t)j * np + g], p = P[(size_t)j * np + g];
-      const double2 d = make_double2(hp.x - e * p.x, hp.y - e * p.y);
+      const double2 hp = HP[(size_t)j * np + g], p = P[(size_t)j * np + g], sp = SP[(size_t)j * np + g];
+      const double2 d = make_double2(hp.x - e * sp.x, hp.y - e * sp.y);
       const double2 t = cmul_(c[j], d);
       const double2 z = cmul_(c[j], p);
       rx += t.x;
@@ -279,7 +302,7 @@ __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, cons
       zy += z.y;
     }
     rr += rx * rx + ry * ry;
-    double x = hd[g] - e;
+    double x = hd[g] - e * (sdk != nullptr ? sdk[g] : 1.0);
     const double s = x >= 0.0 ? 1.0 : -1.0;
     x = s * fmax(fabs(x), 1e-2);
     const double2 v = make_double2(rx / x, ry / x);
@@ -302,7 +325,7 @@ __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, cons
       const double2 r = out[g];
       double sc = inv;
       if (!parallel) {
-        double x = hd[g] - e;
+        double x = hd[g] - e * (sdk != nullptr ? sdk[g] : 1.0);
         const double s = x >= 0.0 ? 1.0 : -1.0;
         sc = inv / (s * fmax(fabs(x), 1e-2));
       }
@@ -455,6 +478,39 @@ static void dump_reduced(const DavWork* w, int k, int n) {
   }
 }
 
+// Diagnostic: when PWK_TRACE_RR names a directory, the reduced H~, S~ of k-point 0 at every
+// eigensolve of a call are written there as trace_<step>_H.bin / trace_<step>_S.bin, with the
+// eigenvalues the solver returned (trace_<step>_eps.bin, nb float64) and its status.
+static void trace_reduced(const DavWork* w, int step) {
+  const char* dir = std::getenv("PWK_TRACE_RR");
+  if (dir == nullptr) return;
+  int n = 0, status = 0;
+  if (cudaMemcpy(&n, w->nbase, sizeof(int), cudaMemcpyDeviceToHost) ||
+      cudaMemcpy(&status, w->status, sizeof(int), cudaMemcpyDeviceToHost) || n <= 0 || n > w->MB)
+    return;
+  std::vector<double2> h((size_t)w->MB * w->MB), s((size_t)w->MB * w->MB);
+  std::vector<double> e(w->nb);
+  if (cudaMemcpy(h.data(), w->Hr, h.size() * sizeof(double2), cudaMemcpyDeviceToHost) ||
+      cudaMemcpy(s.data(), w->Sr, s.size() * sizeof(double2), cudaMemcpyDeviceToHost) ||
+      cudaMemcpy(e.data(), w->eps_new, e.size() * sizeof(double), cudaMemcpyDeviceToHost))
+    return;
+  char path[512];
+  for (int which = 0; which < 2; ++which) {
+    std::snprintf(path, sizeof(path), "%s/trace_%03d_%s.bin", dir, step, which ? "S" : "H");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) continue;
+    const std::vector<double2>& m = which ? s : h;
+    for (int r = 0; r < n; ++r) std::fwrite(m.data() + (size_t)r * w->MB, sizeof(double2), n, f);
+    std::fclose(f);
+  }
+  std::snprintf(path, sizeof(path), "%s/trace_%03d_eps.bin", dir, step);
+  if (FILE* f = std::fopen(path, "wb")) {
+    std::fwrite(e.data(), sizeof(double), e.size(), f);
+    std::fwrite(&status, sizeof(int), 1, f);
+    std::fclose(f);
+  }
+}
+
 #define KCHECK(what)                                 \
   do {                                               \
     cudaError_t e_ = cudaGetLastError();             \
@@ -504,8 +560,10 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   int total = 0, given_up = 0, host_dbg[4] = {0, 0, 0, 0};
   bool dumped = false;
 
+  double2* const sphi = w->with_s ? w->sphi : w->phi;   // S phi (S = 1: phi itself)
   hdiag_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>(nk, np, p->nkb, p->d_npw, p->d_g2, p->v_mean,
-                                                        p->d_beta, p->d_D, w->hdiag);
+                                                        p->d_beta, p->d_D, w->hdiag, p->d_q,
+                                                        w->with_s ? w->sdiag : nullptr);
   KCHECK("hdiag_kernel");
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, 1);
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iters, 0);
@@ -535,11 +593,12 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
     items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, mask, nullptr, 0, nullptr, nb,
                                                           w->phase, 0, w->items);
     KCHECK("items_kernel");
-    int r = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st);
+    int r = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st,
+                     w->with_s ? w->sphi : nullptr);
     if (r) return r;
     napply[prec == PWK_FP64 ? 0 : 1] += (long long)count * nb;
     gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, mask, nullptr, 0, nullptr, nb,
-                                                 w->phi, w->hphi, w->Hr, w->Sr);
+                                                 w->phi, w->hphi, sphi, w->Hr, w->Sr);
     KCHECK("gram_kernel");
     set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, mask, w->nbase, nb, nullptr);
     return launch_rr(nk, MB, nb, w->nbase, mask, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st);
@@ -557,7 +616,8 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   for (;;) {
     resid_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved,
                                           (rt1 > 0 || res_tol > 0) ? 1 : 0, w->ev, w->eps, w->phi,
-                                          w->hphi, w->hdiag, w->corr, w->rnorm);
+                                          w->hphi, sphi, w->hdiag, w->with_s ? w->sdiag : nullptr,
+                                          w->corr, w->rnorm);
     KCHECK("resid_kernel");
     cudaMemsetAsync(w->counters, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(w->counters + 2, 0xff, sizeof(int), st);
@@ -579,7 +639,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       char buf[200];
       std::snprintf(buf, sizeof(buf),
                     "k=%d given up after repeated reduced-problem failures (status %d: %s), iteration %d",
-                    hc[2], hc[3], hc[3] == PWK_ERR_NUMERIC ? "QL did not converge" : "S~ not positive definite",
+                    hc[2], hc[3], hc[3] == PWK_ERR_NUMERIC ? "non-finite eigenvector" : "S~ not positive definite",
                     it);
       set_error(buf);
     }
@@ -606,8 +666,12 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->hphi, w->tmp2, nb);
       copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, w->restart);
       copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp2, nb, 0, w->hphi, MB, 0, w->restart);
+      if (w->with_s) {
+        rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->sphi, w->tmp3, nb);
+        copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp3, nb, 0, w->sphi, MB, 0, w->restart);
+      }
       gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->restart, nullptr, 0, nullptr,
-                                                   nb, w->phi, w->hphi, w->Hr, w->Sr);
+                                                   nb, w->phi, w->hphi, sphi, w->Hr, w->Sr);
       set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, w->nbase, nb, nullptr);
       KCHECK("davidson restart");
       // append the corrections, apply H to them (FP32 for phase-1 k, FP64 for phase-2 k)
@@ -620,16 +684,19 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
                                                               w->phase, ph, w->items);
         KCHECK("items_kernel");
         const int prec = ph == 2 ? PWK_FP64 : PWK_FP32_C128;
-        if ((rc = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st))) return rc;
+        if ((rc = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st,
+                           w->with_s ? w->sphi : nullptr)))
+          return rc;
         napply[ph == 2 ? 0 : 1] += cnt;
       }
       gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->iterk, w->nbase, 0, w->nnc,
-                                                   0, w->phi, w->hphi, w->Hr, w->Sr);
+                                                   0, w->phi, w->hphi, sphi, w->Hr, w->Sr);
       set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, w->nbase, 0, w->nnc);
       KCHECK("davidson gram");
       if ((rc = launch_rr(nk, MB, nb, w->nbase, w->iterk, w->Hr, w->Sr, w->W, w->ev, w->eps_new,
                           w->status, st)))
         return rc;
+      trace_reduced(w, it);
       update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->iterk, 0,
                                                              w->eps_new, w->eps, w->moved, w->status,
                                                              w->nnc, w->nbase, w->force, w->failcount,

@@ -1,24 +1,24 @@
-// Fused H|psi> kernel: one CTA applies the Hamiltonian to one band of one k-point with a
-// single round trip to HBM (read C, write H C).
+// Fused local-potential kernel: one CTA applies the kinetic and local terms of H to one
+// band of one k-point with a single round trip to HBM (read C, write the local part of H C).
+// The nonlocal projector terms run as separate kernels around it (nonlocal.cu): their
+// projections over all bands of a k-point share one staged copy of beta(k).
 //
 // Per work item (paper Sec. 2.2 and Sec. 5, Fig. 2 flow, here fused into one kernel):
 //   1. load C(G) and scatter it onto the z-sticks held in shared memory (Sec. 4 "sets the
-//      non zero elements of this grid"); in the same pass lambda_n = sum_G beta_n* C
-//      (Eq. lambdah), one warp per projector;
+//      non zero elements of this grid");
 //   2. inverse z transforms, only on the sticks (m1, m2) that carry coefficients (Eq. zfft);
-//      gamma = D lambda (Eq. gamma);
 //   3. for each chunk of L planes l3: inverse y transforms on the m1 planes that carry
 //      sticks (Eq. yfft); for every x line (l2, l3): inverse x transform (Eq. xfft),
 //      u'(r) = V(r) u(r) (Sec. 2.2.2), forward x transform keeping only the m1 planes that
 //      are carried back; forward y transforms written back onto the sticks;
 //   4. forward z transforms on the sticks (Eq. fwFFT);
-//   5. gather r -> G with the 1/N_r of Eq. fwFFT, add the kinetic term |k+G|^2 C
-//      (Sec. 2.2.1, Ry) and the nonlocal add-back sum_m gamma_m beta_m (Eq. finalnl).
+//   5. gather r -> G with the 1/N_r of Eq. fwFFT and add the kinetic term |k+G|^2 C
+//      (Sec. 2.2.1, Ry).
 // The pruning skips transforms of lines that are identically zero or whose results are
 // discarded; the result equals the full 3D transform pair exactly (up to rounding).
 //
 // Template parameters: T arithmetic type, TI io type (complex of TI in memory), N grid
-// size, CPLXV: V is a complex128 field and the kinetic/nonlocal terms are absent (the
+// size, CPLXV: V is a complex128 field and the kinetic term is absent (the
 // lattice-periodic dV psi product of the DFPT right-hand side, Eq. linear_system).
 // The real V(r) is read from a transposed copy [l2][l3][l1] (one x-line contiguous); the
 // complex dv(r) keeps the caller's [l1][l2][l3] layout.
@@ -93,9 +93,7 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
   V* Z = reinterpret_cast<V*>(smem_raw);
   V* Y = Z + (size_t)a.nstick_max * zs;
   V* psis = Y + (size_t)P * N * L;
-  V* lam = psis + a.npw_in_max;
-  V* gam = lam + a.nkb;
-  short* sid = reinterpret_cast<short*>(gam + a.nkb);
+  short* sid = reinterpret_cast<short*>(psis + a.npw_in_max);
 
   const VI* pin = static_cast<const VI*>(a.in) + ((size_t)k * a.nvec_in + vin) * a.npw_in_max;
   VI* pout = static_cast<VI*>(a.out) + ((size_t)k * a.nvec_out + vout) * a.npw_out_max;
@@ -112,7 +110,7 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
   }
   __syncthreads();
 
-  // ---- 1: scatter onto the sticks; projections lambda (Eq. lambdah)
+  // ---- 1: scatter onto the sticks
   {
     const int* gin = a.gin + (size_t)k * a.npw_in_max;
     for (int g = tid; g < npi; g += nth) {
@@ -120,48 +118,15 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
       Z[(m >> 8) * zs + (m & 255)] = psis[g];
     }
   }
-  if constexpr (!CPLXV) {
-    if (a.nkb > 0) {
-      const V* bk = static_cast<const V*>(a.beta) + (size_t)k * a.nkb * a.npw_out_max;
-      const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
-      for (int i = warp; i < a.nkb; i += nw) {
-        T sr = T(0), si = T(0);
-        const V* bi = bk + (size_t)i * a.npw_out_max;
-        for (int g = lane; g < npi; g += 32) {
-          const V b = bi[g], c = psis[g];
-          sr += b.x * c.x + b.y * c.y;   // conj(beta) * C
-          si += b.x * c.y - b.y * c.x;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          sr += __shfl_xor_sync(0xffffffffu, sr, o);
-          si += __shfl_xor_sync(0xffffffffu, si, o);
-        }
-        if (lane == 0) lam[i] = V{sr, si};
-      }
-    }
-  }
   __syncthreads();
 
-  // ---- 2: inverse z transforms on the sticks; gamma = D lambda (Eq. gamma)
+  // ---- 2: inverse z transforms on the sticks
   for (int s = tid; s < ns; s += nth) {
     V x[N];
     V* zr = Z + s * zs;
     PWK_SFOR(N, j, x[j] = zr[j]);
     LineFFT<T, N, +1>::run(x);
     PWK_SFOR(N, j, zr[j] = x[OutSlot<N, j>::value]);
-  }
-  if constexpr (!CPLXV) {
-    for (int i = tid; i < a.nkb; i += nth) {
-      const T* Dm = static_cast<const T*>(a.D) + (size_t)i * a.nkb;
-      T gr = T(0), gi = T(0);
-      for (int j = 0; j < a.nkb; ++j) {
-        const T d = Dm[j];
-        gr += d * lam[j].x;
-        gi += d * lam[j].y;
-      }
-      gam[i] = V{gr, gi};
-    }
   }
   __syncthreads();
 
@@ -240,13 +205,11 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
   }
   __syncthreads();
 
-  // ---- 5: gather with 1/N_r; kinetic and nonlocal add-back (Eq. finalnl)
+  // ---- 5: gather with 1/N_r; kinetic term
   {
     const int* gout = a.gout + (size_t)k * a.npw_out_max;
     const T sc = T(a.scale);
     const double* g2k = a.g2 != nullptr ? a.g2 + (size_t)k * a.npw_out_max : nullptr;
-    const V* bk = nullptr;
-    if constexpr (!CPLXV) bk = static_cast<const V*>(a.beta) + (size_t)k * a.nkb * a.npw_out_max;
     for (int g = tid; g < npo; g += nth) {
       const int m = gout[g];
       const V z = Z[(m >> 8) * zs + (m & 255)];
@@ -256,12 +219,6 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
           const T t2 = T(g2k[g]);
           acc.x += t2 * psis[g].x;
           acc.y += t2 * psis[g].y;
-        }
-        for (int i = 0; i < a.nkb; ++i) {
-          const V b = bk[(size_t)i * a.npw_out_max + g];
-          const V c = gam[i];
-          acc.x += c.x * b.x - c.y * b.y;
-          acc.y += c.x * b.y + c.y * b.x;
         }
       }
       pout[g] = VI{TI(acc.x), TI(acc.y)};

@@ -1,7 +1,7 @@
 // Window-specialised fused H|psi> kernel.
 //
-// Same operator and the same one-HBM-round-trip structure as fused_kernel (paper Sec. 2.2 and
-// Sec. 5; see fused_kernel.cuh), for spheres whose Miller indices all satisfy |m_i| <= W with
+// Same operator (kinetic and local terms) and the same one-HBM-round-trip structure as
+// fused_kernel (paper Sec. 2.2 and Sec. 5; see fused_kernel.cuh), for spheres whose Miller indices all satisfy |m_i| <= W with
 // W = N/4: a grid chosen to hold the differences G - G' of the basis (Sec. 5: "N_i large
 // enough"), N >= 4 max|m|, always satisfies it.  With the window known at compile time:
 //   * the z-sticks live in a dense (2W+1) x (2W+1) square of rows [m1][m2] (rows without a
@@ -58,51 +58,28 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
 
   V* Z = reinterpret_cast<V*>(smem_raw);               // [NW*NW][zs]
   V* Y = Z + (size_t)NW * NW * zs;                      // [NW][yps] (N x L used per plane)
-  V* psis = Y + (size_t)NW * yps;                       // [npw_max]
-  V* lam = psis + a.npw_in_max;
-  V* gam = lam + a.nkb;
-  short* rows = reinterpret_cast<short*>(gam + a.nkb);  // [nstick_max]
+  short* rows = reinterpret_cast<short*>(Y + (size_t)NW * yps);  // [nstick_max]
 
   const VI* pin = static_cast<const VI*>(a.in) + ((size_t)k * a.nvec_in + vin) * a.npw_in_max;
   VI* pout = static_cast<VI*>(a.out) + ((size_t)k * a.nvec_out + vout) * a.npw_out_max;
 
-  // ---- 0: zero the stick square, stage the stick rows and C(G)
+  // C(G) is read from global memory by the two stages that need it (scatter, kinetic term):
+  // the second read hits L1/L2, and the shared memory a staged copy would take buys occupancy.
+  // ---- 0: zero the stick square, stage the stick rows
   for (int i = tid; i < NW * NW * zs; i += nth) Z[i] = V{T(0), T(0)};
   {
     const short* rk = a.sid + (size_t)k * a.nstick_max;
     for (int i = tid; i < ns; i += nth) rows[i] = rk[i];
   }
-  for (int g = tid; g < np; g += nth) {
-    VI v = pin[g];
-    psis[g] = V{T(v.x), T(v.y)};
-  }
   __syncthreads();
 
-  // ---- 1: scatter; projections lambda (Eq. lambdah)
+  // ---- 1: scatter
   {
     const int* gin = a.gin + (size_t)k * a.npw_in_max;
     for (int g = tid; g < np; g += nth) {
       const int m = gin[g];
-      Z[(m >> 8) * zs + (m & 255)] = psis[g];
-    }
-  }
-  if (a.nkb > 0) {
-    const V* bk = static_cast<const V*>(a.beta) + (size_t)k * a.nkb * a.npw_out_max;
-    const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
-    for (int i = warp; i < a.nkb; i += nw) {
-      T sr = T(0), si = T(0);
-      const V* bi = bk + (size_t)i * a.npw_out_max;
-      for (int g = lane; g < np; g += 32) {
-        const V b = bi[g], c = psis[g];
-        sr += b.x * c.x + b.y * c.y;
-        si += b.x * c.y - b.y * c.x;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        sr += __shfl_xor_sync(0xffffffffu, sr, o);
-        si += __shfl_xor_sync(0xffffffffu, si, o);
-      }
-      if (lane == 0) lam[i] = V{sr, si};
+      const VI v = pin[g];
+      Z[(m >> 8) * zs + (m & 255)] = V{T(v.x), T(v.y)};
     }
   }
   __syncthreads();
@@ -114,16 +91,6 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
     PWK_SFOR(N, j, x[j] = Wn::in(j) ? zr[j] : V{T(0), T(0)});
     LineFFT<T, N, +1>::run(x);
     PWK_SFOR(N, j, zr[j] = x[OutSlot<N, j>::value]);
-  }
-  for (int i = tid; i < a.nkb; i += nth) {
-    const T* Dm = static_cast<const T*>(a.D) + (size_t)i * a.nkb;
-    T gr = T(0), gi = T(0);
-    for (int j = 0; j < a.nkb; ++j) {
-      const T d = Dm[j];
-      gr += d * lam[j].x;
-      gi += d * lam[j].y;
-    }
-    gam[i] = V{gr, gi};
   }
   __syncthreads();
 
@@ -144,12 +111,13 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
     // 3b: x lines: inverse x, V(r) product, forward x (window outputs only)
     for (int t = tid; t < N * lc; t += nth) {
       const int l2 = t / lc, c = t - l2 * lc;
+      // V(r) of the line is requested first: its latency hides behind the inverse transform
+      T w[N];
+      load_vline<T, N>(static_cast<const T*>(a.V) + ((size_t)l2 * N + l0 + c) * N, w);
       V x[N];
       const V* yl = Y + (size_t)l2 * L + c;
       PWK_SFOR(N, i, x[i] = Wn::in(i) ? yl[(size_t)Wn::idx(i) * yps] : V{T(0), T(0)});
       LineFFT<T, N, +1>::run(x);
-      T w[N];
-      load_vline<T, N>(static_cast<const T*>(a.V) + ((size_t)l2 * N + l0 + c) * N, w);
       V y[N];
       PWK_SFOR(N, l1, {
         const V u = x[OutSlot<N, l1>::value];
@@ -189,23 +157,17 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
   }
   __syncthreads();
 
-  // ---- 5: gather with 1/N_r; kinetic and nonlocal add-back (Eq. finalnl)
+  // ---- 5: gather with 1/N_r; kinetic term
   {
     const int* gout = a.gout + (size_t)k * a.npw_out_max;
     const T sc = T(a.scale);
     const double* g2k = a.g2 + (size_t)k * a.npw_out_max;
-    const V* bk = static_cast<const V*>(a.beta) + (size_t)k * a.nkb * a.npw_out_max;
     for (int g = tid; g < np; g += nth) {
       const int m = gout[g];
       const V z = Z[(m >> 8) * zs + (m & 255)];
       const T t2 = T(g2k[g]);
-      V acc = V{z.x * sc + t2 * psis[g].x, z.y * sc + t2 * psis[g].y};
-      for (int i = 0; i < a.nkb; ++i) {
-        const V b = bk[(size_t)i * a.npw_out_max + g];
-        const V c = gam[i];
-        acc.x += c.x * b.x - c.y * b.y;
-        acc.y += c.x * b.y + c.y * b.x;
-      }
+      const VI cv = pin[g];
+      V acc = V{z.x * sc + t2 * T(cv.x), z.y * sc + t2 * T(cv.y)};
       pout[g] = VI{TI(acc.x), TI(acc.y)};
     }
     for (int g = np + tid; g < a.npw_out_max; g += nth) pout[g] = VI{TI(0), TI(0)};
@@ -222,7 +184,7 @@ int launch_window(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, 
 #define PWK_WCASE(n)                                                                            \
   case n: {                                                                                     \
     auto kern = fused_window_kernel<T, TI, n, window_of(n)>;                                    \
-    cudaError_t e = allow_full_smem(kern);                                                     \
+    cudaError_t e = allow_full_smem(kern);                                                      \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(window)");                  \
     kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \
     e = cudaGetLastError();                                                                     \

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -71,10 +72,9 @@ bool grid_supported(int N) {
   }
 }
 
-size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int npw_in_max,
-                        int nkb) {
+size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int npw_in_max) {
   const int zs = (N % 2 == 0) ? N + 1 : N;
-  size_t elems = (size_t)nstick_max * zs + (size_t)P * N * L + npw_in_max + 2 * (size_t)nkb;
+  size_t elems = (size_t)nstick_max * zs + (size_t)P * N * L + npw_in_max;
   return elems * elem_bytes + (size_t)P * N * sizeof(short) + 16;
 }
 
@@ -98,11 +98,11 @@ void window_strides(int N, int L, int* zs, int* yps) {
   *yps = y;
 }
 
-size_t window_smem_bytes(int N, int elem_bytes, int L, int npw_max, int nkb, int nstick_max) {
+size_t window_smem_bytes(int N, int elem_bytes, int L, int nstick_max) {
   const int W = N / 4, NW = 2 * W + 1;
   int zs, yps;
   window_strides(N, L, &zs, &yps);
-  size_t elems = (size_t)NW * NW * zs + (size_t)NW * yps + npw_max + 2 * (size_t)nkb;
+  size_t elems = (size_t)NW * NW * zs + (size_t)NW * yps;
   return elems * elem_bytes + (size_t)nstick_max * sizeof(short) + 16;
 }
 
@@ -288,20 +288,20 @@ int build_window_tables(pwk_plan* p) {
 
 // Launch shape: the largest l3 chunk that keeps two CTAs per SM (FP64: one) within the
 // 227 KB of shared memory per CTA, threads 256.
-LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int nkb, int ctas_per_sm) {
+LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int ctas_per_sm) {
   LaunchShape s;
   s.threads = 256;
   const size_t sm_total = 228 * 1024, per_cta_max = 227 * 1024;
   const size_t target = std::min(per_cta_max, sm_total / ctas_per_sm - 1024);
   int best = 1;
   for (int L = N; L >= 1; --L) {
-    if (fused_smem_bytes(N, elem_bytes, sm.nstick_max, sm.P, L, sm.npw_in_max, nkb) <= target) {
+    if (fused_smem_bytes(N, elem_bytes, sm.nstick_max, sm.P, L, sm.npw_in_max) <= target) {
       best = L;
       break;
     }
   }
   s.L = best;
-  s.smem = fused_smem_bytes(N, elem_bytes, sm.nstick_max, sm.P, best, sm.npw_in_max, nkb);
+  s.smem = fused_smem_bytes(N, elem_bytes, sm.nstick_max, sm.P, best, sm.npw_in_max);
   return s;
 }
 
@@ -355,8 +355,8 @@ int autotune_shape(pwk_plan* p, int precision) {
         c.kind = kind;
         c.threads = T;
         c.L = L;
-        c.smem = kind == 1 ? window_smem_bytes(N, elem, L, p->npw_max, p->nkb, p->self.nstick_max)
-                           : fused_smem_bytes(N, elem, p->self.nstick_max, p->self.P, L, p->npw_max, p->nkb);
+        c.smem = kind == 1 ? window_smem_bytes(N, elem, L, p->self.nstick_max)
+                           : fused_smem_bytes(N, elem, p->self.nstick_max, p->self.P, L, p->npw_max);
         if (c.smem <= 227 * 1024) cands.push_back(c);
       }
   if (cands.empty()) return PWK_OK;   // the default shape stands (plan creation checked it)
@@ -422,34 +422,100 @@ FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out)
   a.L = p->shape[precision].L;
   a.zs = (p->N % 2 == 0) ? p->N + 1 : p->N;
   a.g2 = p->d_g2;
-  a.nkb = p->nkb;
-  if (precision == PWK_FP64) {
-    a.beta = p->d_beta;
-    a.D = p->d_D;
-    a.V = p->d_Vt64;
-  } else {
-    a.beta = p->d_beta32;
-    a.D = p->d_D32;
-    a.V = p->d_V32;
-  }
+  a.V = precision == PWK_FP64 ? static_cast<const void*>(p->d_Vt64) : static_cast<const void*>(p->d_V32);
   a.scale = 1.0 / (double)p->Nr;
   a.err = p->d_err;
   return a;
 }
 
+// Stream-ordered pool for per-call scratch (one per device, kept for the life of the
+// process).  Its release threshold is unbounded, so memory freed at the end of a call stays
+// mapped and the next call's allocation is a pool hit instead of a new mapping.
+static cudaError_t scratch_pool(cudaMemPool_t* pool) {
+  static std::mutex mu;
+  static std::map<int, cudaMemPool_t> pools;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = pools.find(dev);
+  if (it != pools.end()) {
+    *pool = it->second;
+    return cudaSuccess;
+  }
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  e = cudaMemPoolCreate(pool, &props);
+  if (e != cudaSuccess) return e;
+  unsigned long long keep = ~0ull;
+  e = cudaMemPoolSetAttribute(*pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  if (e != cudaSuccess) return e;
+  pools[dev] = *pool;
+  return cudaSuccess;
+}
+
 int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* items,
-             const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st) {
+             const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st,
+             void* sout) {
+  if (precision < 0 || precision > 2) {
+    set_error("unknown precision");
+    return PWK_ERR_INVALID;
+  }
+  if (nblocks <= 0) return PWK_OK;
+  // projector coefficients gamma, delta of every item: scratch from a stream-ordered pool,
+  // so concurrent calls on other streams never share it
+  NlArgs n;
+  const bool nl = p->nkb > 0 || sout != nullptr;   // with no projectors S C = C (phase 1 copies)
+  if (nl) {
+    n.in = in;
+    n.out = out;
+    n.sout = sout;
+    n.items = items;
+    n.d_count = d_count;
+    n.nitems = nblocks;
+    n.nvec_in = nvec_in;
+    n.nvec_out = nvec_out;
+    n.nk = p->nk;
+    n.npw_max = p->npw_max;
+    n.npw = p->d_npw;
+    n.nkb = p->nkb;
+    const bool f64 = precision == PWK_FP64;
+    n.beta = f64 ? static_cast<const void*>(p->d_beta) : static_cast<const void*>(p->d_beta32);
+    n.D = f64 ? static_cast<const void*>(p->d_D) : static_cast<const void*>(p->d_D32);
+    n.q = f64 ? static_cast<const void*>(p->d_q) : static_cast<const void*>(p->d_q32);
+    const size_t cbytes = (size_t)nblocks * 2 * p->nkb * (f64 ? 16 : 8);
+    if (cbytes > 0) {
+      cudaMemPool_t pool;
+      cudaError_t e = scratch_pool(&pool);
+      if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&n.coef, cbytes, pool, st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(projector coefficients)");
+    }
+    n.phase = 0;
+    if (int r = launch_nl(precision, n, st)) {
+      if (n.coef) cudaFreeAsync(n.coef, st);
+      return r;
+    }
+  }
   FusedArgs a = hpsi_args(p, precision, in, out);
   a.items = items;
   a.d_count = d_count;
   a.nvec_in = nvec_in;
   a.nvec_out = nvec_out;
-  if (precision < 0 || precision > 2) {
-    set_error("unknown precision");
-    return PWK_ERR_INVALID;
-  }
   use_kind(p, a, p->shape[precision].kind);
-  return launch_variant(precision, p->N, a, nblocks, p->shape[precision], st);
+  int r = launch_variant(precision, p->N, a, nblocks, p->shape[precision], st);
+  if (nl) {
+    if (r == PWK_OK) {
+      n.phase = 1;
+      r = launch_nl(precision, n, st);
+    }
+    if (n.coef) {
+      cudaError_t e = cudaFreeAsync(n.coef, st);
+      if (r == PWK_OK && e != cudaSuccess) r = cuda_fail(e, "cudaFreeAsync(projector coefficients)");
+    }
+  }
+  return r;
 }
 
 }  // namespace pwk
@@ -496,9 +562,8 @@ int pwk_plan_set_launch_shape(pwk_plan* p, int precision, int kind, int threads,
   c.kind = kind;
   c.threads = threads;
   c.L = l3_chunk;
-  c.smem = kind == 1 ? window_smem_bytes(p->N, elem, l3_chunk, p->npw_max, p->nkb, p->self.nstick_max)
-                     : fused_smem_bytes(p->N, elem, p->self.nstick_max, p->self.P, l3_chunk, p->npw_max,
-                                        p->nkb);
+  c.smem = kind == 1 ? window_smem_bytes(p->N, elem, l3_chunk, p->self.nstick_max)
+                     : fused_smem_bytes(p->N, elem, p->self.nstick_max, p->self.P, l3_chunk, p->npw_max);
   if (c.smem > 227 * 1024) {
     set_error("shape needs more than 227 KB of shared memory");
     return PWK_ERR_UNSUPPORTED;
@@ -649,8 +714,8 @@ int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int
   TRYC(cudaMemcpy(&p->v_mean, d_vsum, sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy(vsum)");
   p->v_mean /= (double)p->Nr;
   TRY(build_sphere_map(p, p->self, nk, npw, npw_max, miller, npw, npw_max, miller, p->d_npw, p->d_npw));
-  p->shape[PWK_FP64] = choose_shape(p->N, 16, p->self, nkb, 1);
-  p->shape[PWK_FP32] = choose_shape(p->N, 8, p->self, nkb, 2);
+  p->shape[PWK_FP64] = choose_shape(p->N, 16, p->self, 1);
+  p->shape[PWK_FP32] = choose_shape(p->N, 8, p->self, 2);
   p->shape[PWK_FP32_C128] = p->shape[PWK_FP32];
   if (p->shape[PWK_FP64].smem > 227 * 1024) {
     set_error("the z-sticks and one plane of the carried m1 window do not fit in shared memory");
@@ -692,6 +757,85 @@ int pwk_hpsi_batched(pwk_plan* p, int precision, const void* psi, void* hpsi, in
   }
   return run_hpsi(p, precision, psi, hpsi, nullptr, nullptr, (int)nblocks, nb, nb,
                   static_cast<cudaStream_t>(stream));
+}
+
+int pwk_plan_set_overlap(pwk_plan* p, const double* q) {
+  if (p == nullptr) {
+    set_error("null plan");
+    return PWK_ERR_INVALID;
+  }
+  if (cudaError_t e = cudaSetDevice(p->device); e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  if (cudaError_t e = cudaDeviceSynchronize(); e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+  plan_free(p, p->d_q);
+  plan_free(p, p->d_q32);
+  p->d_q = nullptr;
+  p->d_q32 = nullptr;
+  if (q == nullptr || p->nkb == 0) return PWK_OK;
+  const size_t n2 = (size_t)p->nkb * p->nkb;
+  for (size_t i = 0; i < n2; ++i) {
+    const size_t r = i / p->nkb, c = i % p->nkb;
+    if (!std::isfinite(q[i]) || q[i] != q[c * p->nkb + r]) {
+      set_error("q must be finite and symmetric");
+      return PWK_ERR_INVALID;
+    }
+  }
+  std::vector<float> q32(q, q + n2);
+  int r = plan_alloc(p, (void**)&p->d_q, sizeof(double) * n2);
+  if (r == PWK_OK) r = plan_alloc(p, (void**)&p->d_q32, sizeof(float) * n2);
+  if (r != PWK_OK) {
+    plan_free(p, p->d_q);
+    p->d_q = nullptr;
+    return r;
+  }
+  cudaError_t e = cudaMemcpy(p->d_q, q, sizeof(double) * n2, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_q32, q32.data(), sizeof(float) * n2, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(q)");
+  return PWK_OK;
+}
+
+int pwk_plan_has_overlap(const pwk_plan* p) { return p != nullptr && p->d_q != nullptr ? 1 : 0; }
+
+static int check_hs(pwk_plan* p, int precision, const void* psi, const void* hpsi, const void* spsi) {
+  if (p == nullptr || psi == nullptr || hpsi == nullptr || spsi == nullptr) {
+    set_error("null pointer");
+    return PWK_ERR_INVALID;
+  }
+  if (precision < 0 || precision > 2) {
+    set_error("unknown precision");
+    return PWK_ERR_INVALID;
+  }
+  if (spsi == psi || spsi == hpsi || hpsi == psi) {
+    set_error("psi, hpsi and spsi must be three different buffers");
+    return PWK_ERR_INVALID;
+  }
+  return PWK_OK;
+}
+
+int pwk_hspsi_batched(pwk_plan* p, int precision, const void* psi, void* hpsi, void* spsi, int nb,
+                      void* stream) {
+  if (int r = check_hs(p, precision, psi, hpsi, spsi)) return r;
+  if (nb < 1) {
+    set_error("nb < 1");
+    return PWK_ERR_INVALID;
+  }
+  const long long nblocks = (long long)p->nk * nb;
+  if (nblocks > 0x7fffffffLL) {
+    set_error("nk * nb too large for one launch");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  return run_hpsi(p, precision, psi, hpsi, nullptr, nullptr, (int)nblocks, nb, nb,
+                  static_cast<cudaStream_t>(stream), spsi);
+}
+
+int pwk_hspsi_items(pwk_plan* p, int precision, const void* psi, void* hpsi, void* spsi,
+                    const int* items, int nitems, int nvec_per_k, void* stream) {
+  if (int r = check_hs(p, precision, psi, hpsi, spsi)) return r;
+  if ((nitems > 0 && items == nullptr) || nitems < 0 || nvec_per_k < 1) {
+    set_error("null pointer or bad size");
+    return PWK_ERR_INVALID;
+  }
+  return run_hpsi(p, precision, psi, hpsi, items, nullptr, nitems, nvec_per_k, nvec_per_k,
+                  static_cast<cudaStream_t>(stream), spsi);
 }
 
 int pwk_hpsi_items(pwk_plan* p, int precision, const void* psi, void* hpsi, const int* items,

@@ -16,15 +16,19 @@ namespace pwk {
 void set_error(const std::string& msg);  // thread-local detail for pwk_last_error_detail()
 int cuda_fail(cudaError_t e, const char* what);
 
-// Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum.  The value
-// set never depends on the launch, so host threads that launch the same kernel at the same
-// time (one per stream in a serving loop) cannot lower the limit under one another's launch.
+// Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum (less the
+// kernel's static shared memory).  The value set never depends on the launch, so host threads
+// that launch the same kernel at the same time (one per stream in a serving loop) cannot lower
+// the limit under one another's launch.
 template <typename K>
 inline cudaError_t allow_full_smem(K kern) {
   int dev = 0, optin = 0;
+  cudaFuncAttributes fa;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
   return e;
 }
 
@@ -73,6 +77,8 @@ struct pwk_plan {
   float2* d_beta32 = nullptr;
   double* d_D = nullptr;
   float* d_D32 = nullptr;
+  double* d_q = nullptr;          // overlap coefficients q_mn (null: S = 1), pwk_plan_set_overlap
+  float* d_q32 = nullptr;
   const double* d_V = nullptr;   // caller-owned
   float* d_V32 = nullptr;         // transposed [l2][l3][l1]
   double* d_Vt64 = nullptr;       // transposed [l2][l3][l1]
@@ -117,16 +123,33 @@ struct FusedArgs {
   int nstick_max = 0, m1lo = 0, P = 0, L = 0, zs = 0;
   int yps = 0;                     // plane stride of the y/x chunk buffer (window kernel)
   const double* g2 = nullptr;      // kinetic table [nk][npw_out_max] or null
-  const void* beta = nullptr;      // [nk][nkb][npw_out_max] complex of the arithmetic type
-  const void* D = nullptr;         // [nkb][nkb] real of the arithmetic type
-  int nkb = 0;
   const void* V = nullptr;         // real [N^3] of the arithmetic type, or complex128 dv
   double scale = 1.0;              // 1/N_r
   int* err = nullptr;
 };
 
-size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int npw_in_max,
-                        int nkb);
+size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int npw_in_max);
+
+// Arguments of the nonlocal projector kernels (nonlocal.cu): phase 0 computes gamma = D lambda
+// and delta = q lambda of every item into coef; phase 1 adds sum gamma beta to out and, if
+// sout is set, writes sout = in + sum delta beta.
+struct NlArgs {
+  int phase = 0;
+  const void* in = nullptr;   // input vectors (complex of the io type)
+  void* out = nullptr;        // H output (phase 1 adds to it)
+  void* sout = nullptr;       // S output or null
+  const int* items = nullptr; // [n][3] (k, in_slot, out_slot) or null: item = k * nvec + band
+  const int* d_count = nullptr;
+  int nitems = 0, nvec_in = 0, nvec_out = 0, nk = 0, npw_max = 0;
+  const int* npw = nullptr;
+  const void* beta = nullptr;  // [nk][nkb][npw_max] complex of the arithmetic type
+  const void* D = nullptr;     // [nkb][nkb] real of the arithmetic type
+  const void* q = nullptr;     // [nkb][nkb] or null
+  int nkb = 0;
+  void* coef = nullptr;        // [nitems][2][nkb] complex of the arithmetic type
+};
+int launch_nl(int precision, const NlArgs& a, cudaStream_t st);
+size_t nl_shared_bytes(int nkb, int precision);
 
 // launchers (one per arithmetic/io variant), defined in hpsi_*.cu
 int launch_fused_f64(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
@@ -138,18 +161,21 @@ int launch_window_f64(int N, const FusedArgs& a, int nblocks, const LaunchShape&
 int launch_window_f32(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
 int launch_window_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchShape& s,
                           cudaStream_t st);
-size_t window_smem_bytes(int N, int elem_bytes, int L, int npw_max, int nkb, int nstick_max);
+size_t window_smem_bytes(int N, int elem_bytes, int L, int nstick_max);
 // strides of the window kernel's shared buffers for chunk L (bank-conflict-free y/x passes)
 void window_strides(int N, int L, int* zs, int* yps);
 
 // fill FusedArgs for H|psi> with this plan
 FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out);
+// H (and, with sout set, S) on nblocks work items: projections, local + kinetic term,
+// nonlocal add-back (three launches on st).  sout must not alias in.
 int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* items,
-             const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st);
+             const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st,
+             void* sout = nullptr);
 
 bool grid_supported(int N);
 int build_sphere_map(pwk_plan* p, SphereMap& sm, int nk, const int* npw_in, int npw_in_max,
                      const int* miller_in, const int* npw_out, int npw_out_max,
                      const int* miller_out, const int* d_npw_in, const int* d_npw_out);
-LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int nkb, int ctas_per_sm);
+LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int ctas_per_sm);
 }  // namespace pwk

@@ -8,13 +8,14 @@
 //   3. Householder reduction of C to a real symmetric tridiagonal T = Q^H C Q
 //      (reflectors H = I - tau v v^H, beta real, two-sided rank-2 updates);
 //   4. the nb lowest eigenvalues of T by bisection on Sturm counts and their eigenvectors by
-//      inverse iteration on T (one thread per eigenpair, threads of a warp in lockstep;
-//      near-equal eigenvalues orthogonalised by modified Gram-Schmidt);
+//      inverse iteration on T (one thread per cluster of close eigenvalues, clusters in
+//      parallel; the members of a cluster reorthogonalised inside the iteration);
 //   5. back-transform x = L^-H Q z (reflectors applied in reverse order, then back
 //      substitution).
 // All matrices live in a per-k global workspace (L2-resident while the CTA works on it).
-// A dependent vector among the first nb (pivot below 1e-9 of its diagonal) marks the k-point
-// with status PWK_ERR_NOT_POSDEF; a non-finite eigenvector marks it PWK_ERR_NUMERIC.
+// A dependent vector among the first nb (pivot below 1e-6 of its diagonal) marks the k-point
+// with status PWK_ERR_NOT_POSDEF; a non-finite eigenvector, or eigenvectors of T that are not
+// orthonormal to 1e-8, mark it PWK_ERR_NUMERIC.
 #include <cmath>
 
 #include "solvers.h"
@@ -69,9 +70,13 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   double2* X = Lm + ldsq;             // L^-1 H, then Z (real, column-major)
   double2* C = X + ldsq;              // L^-1 H L^-H, then Householder vectors
   if (tid == 0) flag = 0;
-  // ---- 1. Cholesky of S (lower).  A basis vector whose pivot falls below 1e-9 of its S~
-  //      diagonal is numerically dependent on the earlier ones: it is dropped (its row and
-  //      column of L become e_j and it is decoupled from the reduced problem below).
+  // ---- 1. Cholesky of S (lower).  A basis vector whose pivot falls below 1e-6 of its S~
+  //      diagonal (new direction below 1e-3 of its norm) is numerically dependent on the
+  //      earlier ones: it is dropped (its row and column of L become e_j and it is decoupled
+  //      from the reduced problem below).  The bound sits far above the rounding noise of the
+  //      Schur complement of an exactly dependent vector (seen up to 4e-8 when the earlier
+  //      basis is itself ill-conditioned), which a smaller bound can mistake for a new
+  //      direction and turn into a spurious Ritz value.
   for (int i = tid; i < n * n; i += nth) {
     const int r = i / n, c = i - r * n;
     Lm[r * ld + c] = S[r * ld + c];
@@ -81,7 +86,7 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   for (int j = 0; j < n; ++j) {
     if (tid == 0) {
       const double p = Lm[j * ld + j].x;
-      const bool drop = !(p > 1e-9 * S[j * ld + j].x);
+      const bool drop = !(p > 1e-6 * S[j * ld + j].x);
       dropped[j] = drop ? 1 : 0;
       if (drop && j < nb) flag = 1;   // the leading nb vectors must be independent
       Lm[j * ld + j] = make_double2(drop ? 1.0 : sqrt(p), 0.0);
@@ -250,9 +255,9 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   }
   __syncthreads();
   // ---- 4. the nb lowest eigenpairs of the real tridiagonal T = (d, e): bisection on Sturm
-  //      counts for the eigenvalues, then inverse iteration for the eigenvectors, one thread per
-  //      eigenpair (the threads of a warp work in lockstep, so every FP64 instruction serves up
-  //      to 32 eigenpairs).  Near-equal eigenvalues are orthogonalised (modified Gram-Schmidt).
+  //      counts for the eigenvalues (one thread per eigenvalue: the threads of a warp work in
+  //      lockstep, so every FP64 instruction serves up to 32 eigenvalues), then inverse
+  //      iteration for the eigenvectors.
   double* lam = rc;
   double* e2 = rs;
   __shared__ double glo, ghi, pivmin, tiny;
@@ -296,68 +301,83 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   }
   __syncthreads();
   double* XS = reinterpret_cast<double*>(X);   // x_j at XS + j n, pivots of T - lam_j at XS + (nb + j) n
-  for (int j = tid; j < nb; j += nth) {
-    double* x = XS + (size_t)j * n;
-    double* Dv = XS + (size_t)(nb + j) * n;
-    const double lj = lam[j];
-    double D = d[0] - lj;
-    if (fabs(D) < tiny) D = D < 0.0 ? -tiny : tiny;
-    Dv[0] = D;
-    for (int i = 1; i < n; ++i) {
-      D = d[i] - lj - e2[i - 1] / Dv[i - 1];
+  // Clusters: consecutive eigenvalues closer than ortol = 1e-3 max(1, |lam|) (the reorthogonalisation
+  // criterion of inverse iteration, relative to the spectrum the nb eigenpairs span).  Each
+  // cluster is handled by one thread in order: every iterate of a member is orthogonalised
+  // against the members before it, inside the iteration; eigenvalues of a cluster closer than
+  // eps3 are separated by eps3 before the LDL^T factorisation.  Clusters run in parallel.
+  __shared__ int ncl, cl_start[kMaxBasis + 1];
+  __shared__ double ortol, eps3;
+  if (tid == 0) {
+    const double scale = fmax(1.0, fmax(fabs(lam[0]), fabs(lam[nb - 1])));
+    ortol = 1e-3 * scale;
+    eps3 = 16.0 * 2.2e-16 * scale;
+    int c = 0;
+    cl_start[c++] = 0;
+    for (int j = 1; j < nb; ++j)
+      if (lam[j] - lam[j - 1] > ortol) cl_start[c++] = j;
+    cl_start[c] = nb;
+    ncl = c;
+  }
+  __syncthreads();
+  for (int c = tid; c < ncl; c += nth) {
+    double lprev = -1e300;
+    for (int j = cl_start[c]; j < cl_start[c + 1]; ++j) {
+      double* x = XS + (size_t)j * n;
+      double* Dv = XS + (size_t)(nb + j) * n;
+      double lj = lam[j];
+      if (j > cl_start[c] && lj < lprev + eps3) lj = lprev + eps3;
+      lprev = lj;
+      double D = d[0] - lj;
       if (fabs(D) < tiny) D = D < 0.0 ? -tiny : tiny;
-      Dv[i] = D;
-    }
-    for (int i = 0; i < n; ++i) {   // start vector: a fixed pseudo-random pattern per (i, j)
-      const unsigned h = (unsigned)(i + 1) * 2654435761u ^ (unsigned)(j + 1) * 2246822519u;
-      x[i] = 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
-    }
-    for (int iter = 0; iter < 3; ++iter) {
-      for (int i = 1; i < n; ++i) x[i] -= (e[i - 1] / Dv[i - 1]) * x[i - 1];   // L y = b
-      x[n - 1] /= Dv[n - 1];                                                   // D z = y, L^T x = z
-      for (int i = n - 2; i >= 0; --i) x[i] = x[i] / Dv[i] - (e[i] / Dv[i]) * x[i + 1];
-      double nn = 0.0;
-      for (int i = 0; i < n; ++i) nn += x[i] * x[i];
-      if (!(nn > 0.0) || !isfinite(nn)) {
-        flag = 2;   // non-finite eigenvector: report, do not use
-        break;
+      Dv[0] = D;
+      for (int i = 1; i < n; ++i) {
+        D = d[i] - lj - e2[i - 1] / Dv[i - 1];
+        if (fabs(D) < tiny) D = D < 0.0 ? -tiny : tiny;
+        Dv[i] = D;
       }
-      const double inv = 1.0 / sqrt(nn);
-      for (int i = 0; i < n; ++i) x[i] *= inv;
+      for (int i = 0; i < n; ++i) {   // start vector: a fixed pseudo-random pattern per (i, j)
+        const unsigned h = (unsigned)(i + 1) * 2654435761u ^ (unsigned)(j + 1) * 2246822519u;
+        x[i] = 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
+      }
+      for (int iter = 0; iter < 5; ++iter) {
+        for (int i = 1; i < n; ++i) x[i] -= (e[i - 1] / Dv[i - 1]) * x[i - 1];   // L y = b
+        x[n - 1] /= Dv[n - 1];                                                   // D z = y, L^T x = z
+        for (int i = n - 2; i >= 0; --i) x[i] = x[i] / Dv[i] - (e[i] / Dv[i]) * x[i + 1];
+        for (int q = cl_start[c]; q < j; ++q) {   // modified Gram-Schmidt against the cluster
+          const double* xq = XS + (size_t)q * n;
+          double s2 = 0.0;
+          for (int i = 0; i < n; ++i) s2 += xq[i] * x[i];
+          for (int i = 0; i < n; ++i) x[i] -= s2 * xq[i];
+        }
+        double nn = 0.0;
+        for (int i = 0; i < n; ++i) nn += x[i] * x[i];
+        if (!(nn > 0.0) || !isfinite(nn)) {
+          flag = 2;   // non-finite eigenvector: report, do not use
+          break;
+        }
+        const double inv = 1.0 / sqrt(nn);
+        for (int i = 0; i < n; ++i) x[i] *= inv;
+      }
     }
+  }
+  __syncthreads();
+  // guard: the nb vectors must be orthonormal; a loss (a cluster missed by the criterion)
+  // is reported like a non-finite vector and the caller drops the step
+  for (int pq = tid; pq < nb * nb && flag == 0; pq += nth) {
+    const int a = pq / nb, b = pq - a * nb;
+    if (b > a) continue;
+    const double* xa = XS + (size_t)a * n;
+    const double* xb = XS + (size_t)b * n;
+    double s2 = 0.0;
+    for (int i = 0; i < n; ++i) s2 += xa[i] * xb[i];
+    if (!(fabs(s2 - (a == b ? 1.0 : 0.0)) < 1e-8)) flag = 2;
   }
   __syncthreads();
   if (flag == 2) {
     if (tid == 0 && status != nullptr) status[k] = PWK_ERR_NUMERIC;
     return;
   }
-  // clusters of near-equal eigenvalues: orthogonalise in order (warp 0)
-  if (tid < 32) {
-    const double scale = fmax(1.0, fmax(fabs(lam[0]), fabs(lam[nb - 1])));
-    int c0 = 0;
-    for (int j = 1; j < nb; ++j) {
-      if (lam[j] - lam[j - 1] > 1e-9 * scale) {
-        c0 = j;
-        continue;
-      }
-      double* xj = XS + (size_t)j * n;
-      for (int q = c0; q < j; ++q) {
-        const double* xq = XS + (size_t)q * n;
-        double s = 0.0;
-        for (int i = tid; i < n; i += 32) s += xq[i] * xj[i];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        for (int i = tid; i < n; i += 32) xj[i] -= s * xq[i];
-        __syncwarp();
-      }
-      double nn = 0.0;
-      for (int i = tid; i < n; i += 32) nn += xj[i] * xj[i];
-      for (int o = 16; o > 0; o >>= 1) nn += __shfl_xor_sync(0xffffffffu, nn, o);
-      const double inv = 1.0 / sqrt(nn);
-      for (int i = tid; i < n; i += 32) xj[i] *= inv;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
   // ---- 5. back-transform x = L^-H Q z of the selected vectors
   for (int j = tid; j < nb; j += nth) eps[k * nb + j] = lam[j];
   double2* E = ev + (size_t)k * ld * nb;

@@ -1,8 +1,12 @@
 // Batched DFPT Sternheimer solver (paper Sec. 2.3-2.4, Algorithm 4): for every k of the
 // block and every occupied band n
-//   [H_{k+q} + alpha_k P_v - eps_{k,n}] x_{k,n} = b_{k,n} = -P_c dV psi_{k,n}
-// (Eq. linear_system with S = I, dS = 0; Eqs. projector, compute_mu, use_mu with S = I),
-// solved by the preconditioned CG of Eqs. ax1 .. updatedold for all (k, n) at once.
+//   [H_{k+q} + alpha_k Q - eps_{k,n} S] x_{k,n} = b_{k,n} = -(1 - S P_v) dV psi_{k,n}
+// (Eq. linear_system with dS = 0 for a local perturbation dv; Q = sum_v S|u_v><u_v|S,
+// Eqs. projector, compute_mu, use_mu, apply_s_ch; S = 1 without q, where this is
+// [H + alpha P_v - eps] x = -P_c dV psi), solved by the preconditioned CG of Eqs. ax1 ..
+// updatedold for all (k, n) at once.  With S, S u_v is computed once per call and
+// alpha Q d = sum_v (S u_v) alpha <S u_v|d>, so S is applied to each CG direction once
+// (together with H, from the same projections).
 //
 // Kernels (one CTA per (k, n) unless noted):
 //   rhs     : fused transfer kernel (inverse transform of psi_k on the k sphere, dv(r) u(r),
@@ -28,7 +32,9 @@ namespace pwk {
 
 struct CgWork {
   int nk = 0, nocc = 0, np = 0;
+  bool with_s = false;    // overlap S (plan with q): S u_v and S d kept
   double2 *b = nullptr, *r = nullptr, *d = nullptr, *dold = nullptr, *t = nullptr;
+  double2 *su = nullptr, *sx = nullptr;
   double *rho = nullptr, *rho_old = nullptr, *bnorm = nullptr, *thr = nullptr, *tkin = nullptr;
   double *rnorm = nullptr;
   int *active = nullptr, *first = nullptr, *iters = nullptr, *items = nullptr, *counters = nullptr;
@@ -50,15 +56,21 @@ static int calloc_(pwk_plan* p, CgWork* w, T** ptr, size_t n) {
 }
 
 static int ensure_cg_work(pwk_plan* p, int nocc) {
-  if (p->cg && p->cg->nocc == nocc) return PWK_OK;
+  const bool with_s = p->d_q != nullptr;
+  if (p->cg && p->cg->nocc == nocc && p->cg->with_s == with_s) return PWK_OK;
   destroy_cg_work(p);
   CgWork* w = new CgWork();
   p->cg = w;
   w->nk = p->nk;
   w->nocc = nocc;
   w->np = p->npw_max;
+  w->with_s = with_s;
   const size_t nv = (size_t)p->nk * nocc, nv2 = nv * p->npw_max;
   int rc;
+  if (with_s && ((rc = calloc_(p, w, &w->su, nv2)) || (rc = calloc_(p, w, &w->sx, nv2)))) {
+    destroy_cg_work(p);
+    return rc;
+  }
   if ((rc = calloc_(p, w, &w->b, nv2)) || (rc = calloc_(p, w, &w->r, nv2)) ||
       (rc = calloc_(p, w, &w->d, nv2)) || (rc = calloc_(p, w, &w->dold, nv2)) ||
       (rc = calloc_(p, w, &w->t, nv2)) || (rc = calloc_(p, w, &w->rho, nv)) ||
@@ -90,13 +102,16 @@ __device__ double bsum2(double v, double* red) {
   return s;
 }
 
-// out = a_u u + a_w w + a_p sum_v psi_v <psi_v|w>  for (k, n) with active (or all if null).
-// a_w = wmode ? -eps[k][n] : -1;  a_p = pmode ? alpha[k] : 1;  u may be null (a_u = 0).
-// The norm of out is written to onorm (if non-null).
+// out = u + a_w ws + a_p sum_v py_v <pm_v|w>  for (k, n) with active (or all if null).
+// a_w = wmode ? -eps[k][n] : -1;  a_p = pmode ? alpha[k] : 1;  u may be null (a_u = 0);
+// ws null means ws = w.  With S = 1: pm = py = psi_{k+q,v}, ws = w.  With S (Eq. projector):
+// pm = py = S psi_{k+q,v} and ws = S w for the operator (alpha Q w - eps S w), and pm = psi,
+// py = S psi for the right-hand side -(1 - S P_v) w.  The norm of out goes to onorm.
 __global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, const int* npw,
                                                            const int* active,
-                                                           const double2* psi_kq,
+                                                           const double2* pm, const double2* py,
                                                            const double2* u, const double2* w,
+                                                           const double2* ws,
                                                            int wmode, const double* eps,
                                                            int pmode, const double* alpha,
                                                            double2* out, double* onorm) {
@@ -106,7 +121,9 @@ __global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, con
   __shared__ double2 mu[64];
   __shared__ double red[32];
   const double2* W = w + (size_t)blockIdx.x * np;
-  const double2* Pk = psi_kq + (size_t)k * nocc * np;
+  const double2* WS = ws != nullptr ? ws + (size_t)blockIdx.x * np : W;
+  const double2* Pk = pm + (size_t)k * nocc * np;
+  const double2* Yk = py + (size_t)k * nocc * np;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int v = warp; v < nocc; v += nw) {
     double sx = 0, sy = 0;
@@ -135,11 +152,11 @@ __global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, con
     }
     double2 y = make_double2(0.0, 0.0);
     for (int v = 0; v < nocc; ++v) {
-      const double2 p = Pk[(size_t)v * np + g], m = mu[v];
+      const double2 p = Yk[(size_t)v * np + g], m = mu[v];
       y.x += p.x * m.x - p.y * m.y;
       y.y += p.x * m.y + p.y * m.x;
     }
-    const double2 wg = W[g];
+    const double2 wg = WS[g];
     double2 o = make_double2(aw * wg.x + ap * y.x, aw * wg.y + ap * y.y);
     if (U) {
       o.x += U[g].x;
@@ -358,7 +375,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     rc = build_sphere_map(pq, pq->xfer, pq->nk, pk->h_npw.data(), pk->npw_max, pk->h_miller.data(),
                           pq->h_npw.data(), pq->npw_max, pq->h_miller.data(), pk->d_npw, pq->d_npw);
     if (rc) return rc;
-    pq->xshape = choose_shape(pq->N, 16, pq->xfer, 0, 1);
+    pq->xshape = choose_shape(pq->N, 16, pq->xfer, 1);
     if (pq->xshape.smem > 227 * 1024) {
       set_error("transfer kernel does not fit in shared memory");
       return PWK_ERR_UNSUPPORTED;
@@ -402,8 +419,17 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     a.err = pq->d_err;
     if ((rc = launch_fused_xfer(pq->N, a, npairs, pq->xshape, st))) return rc;
   }
-  proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, nullptr, w->t, 0,
-                                              nullptr, 0, nullptr, w->b, w->bnorm);
+  // S psi_{k+q,v} (FP64) when the plan has q; the H output of that call is not used
+  const double2* su = psi_kq;
+  if (w->with_s) {
+    cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
+    if ((rc = run_hpsi(pq, PWK_FP64, psi_kq, w->r, w->items, nullptr, npairs, nocc, nocc, st, w->su)))
+      return rc;
+    su = w->su;
+  }
+  double2* const sx = w->with_s ? w->sx : nullptr;   // S applied to the operand of A
+  proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, su, nullptr, w->t,
+                                              nullptr, 0, nullptr, 0, nullptr, w->b, w->bnorm);
   tkin_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, psi_kq, w->tkin);
   cudaMemsetAsync(w->iters, 0, sizeof(int) * npairs, st);
   cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)npairs * np, st);
@@ -420,8 +446,8 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     } else {
       // t = H x (FP64) on every pair, then t = t - eps x + alpha P_v x, r = t - b
       cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
-      if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st))) return rc;
-      proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, w->t, x, 1,
+      if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
+      proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1,
                                                   eps_k, 1, alpha, w->t, nullptr);
       residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, eta,
                                               w->r, w->rnorm, w->thr, w->active, w->first, w->counters);
@@ -438,9 +464,10 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
       if ((rc = read_counters())) return rc;
       if (hc[0] == 0) break;
       cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->items);
-      if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, npairs, nocc, nocc, st))) return rc;
-      proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, psi_kq, w->t, w->d, 1,
-                                                  eps_k, 1, alpha, w->t, nullptr);
+      if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx)))
+        return rc;
+      proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t, w->d, sx,
+                                                  1, eps_k, 1, alpha, w->t, nullptr);
       cg_step_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, w->d, w->t, x, w->r, w->dold,
                                              w->rho, w->rho_old, w->iters, w->counters);
       KCK("cg_step_kernel");
@@ -450,8 +477,8 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
   cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
   {
     cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
-    if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st))) return rc;
-    proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, w->t, x, 1, eps_k,
+    if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
+    proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1, eps_k,
                                                 1, alpha, w->t, nullptr);
     residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, 0.0, w->r,
                                             w->rnorm, w->thr, w->active, w->first, w->counters);

@@ -21,7 +21,8 @@ PRECISIONS = {"fp64": PWK_FP64, "fp32": PWK_FP32, "fp32_c128": PWK_FP32_C128}
 # every symbol declared in include/pwk.h
 EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
            "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_supported_grid",
-           "pwk_hpsi_batched", "pwk_hpsi_items", "pwk_davidson_batched",
+           "pwk_hpsi_batched", "pwk_hpsi_items", "pwk_plan_set_overlap", "pwk_plan_has_overlap",
+           "pwk_hspsi_batched", "pwk_hspsi_items", "pwk_davidson_batched",
            "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_eigh_batched_noalloc",
            "pwk_strerror", "pwk_last_error_detail", "pwk_version")
 
@@ -51,6 +52,10 @@ def load(path: str = LIB_PATH):
         "pwk_supported_grid": (_I, [_I]),
         "pwk_hpsi_batched": (_I, [_P, _I, _P, _P, _I, _P]),
         "pwk_hpsi_items": (_I, [_P, _I, _P, _P, _P, _I, _I, _P]),
+        "pwk_plan_set_overlap": (_I, [_P, _P]),
+        "pwk_plan_has_overlap": (_I, [_P]),
+        "pwk_hspsi_batched": (_I, [_P, _I, _P, _P, _P, _I, _P]),
+        "pwk_hspsi_items": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P]),
         "pwk_davidson_batched": (_I, [_P, _I, _P, _P, _I, _D, _D, _I, _I, _P, _P, _P, _P]),
         "pwk_sternheimer_cg_batched": (_I, [_P, _P, _I, _P, _P, _P, _I, _P, _P, _P, _D, _I, _P,
                                             _P, _P]),
@@ -126,6 +131,18 @@ class Plan:
         _check(load().pwk_plan_set_launch_shape(self.handle, precision, kind, threads, l3_chunk),
                "pwk_plan_set_launch_shape")
 
+    def set_overlap(self, q) -> None:
+        """pwk_plan_set_overlap: q host float64 [nkb][nkb] symmetric, or None (S = 1)."""
+        if q is None:
+            _check(load().pwk_plan_set_overlap(self.handle, None), "pwk_plan_set_overlap")
+            return
+        q = np.ascontiguousarray(q, np.float64)
+        _check(load().pwk_plan_set_overlap(self.handle, _np_ptr(q)), "pwk_plan_set_overlap")
+
+    @property
+    def has_overlap(self) -> bool:
+        return bool(load().pwk_plan_has_overlap(self.handle))
+
     def close(self):
         if self.handle:
             load().pwk_plan_destroy(self.handle)
@@ -196,6 +213,30 @@ def hpsi_items(plan: Plan, precision: int, psi, hpsi, items, nvec_per_k: int, st
     _check(load().pwk_hpsi_items(plan.handle, precision, _ptr(psi), _ptr(hpsi),
                                  _ptr(items) if n else None, n, nvec_per_k, _stream(stream)),
            "pwk_hpsi_items")
+
+
+def hspsi_batched(plan: Plan, precision: int, psi, hpsi, spsi, nb: int, stream=None) -> None:
+    import torch
+    dt = torch.complex64 if precision == PWK_FP32 else torch.complex128
+    shape = (plan.nk, nb, plan.npw_max)
+    for t, name in ((psi, "psi"), (hpsi, "hpsi"), (spsi, "spsi")):
+        _need(t, shape, dt, name)
+    _check(load().pwk_hspsi_batched(plan.handle, precision, _ptr(psi), _ptr(hpsi), _ptr(spsi), nb,
+                                    _stream(stream)), "pwk_hspsi_batched")
+
+
+def hspsi_items(plan: Plan, precision: int, psi, hpsi, spsi, items, nvec_per_k: int, stream=None):
+    import torch
+    dt = torch.complex64 if precision == PWK_FP32 else torch.complex128
+    shape = (plan.nk, nvec_per_k, plan.npw_max)
+    for t, name in ((psi, "psi"), (hpsi, "hpsi"), (spsi, "spsi")):
+        _need(t, shape, dt, name)
+    n = 0 if items is None else int(items.shape[0])
+    if n:
+        _need(items, (n, 3), torch.int32, "items")
+    _check(load().pwk_hspsi_items(plan.handle, precision, _ptr(psi), _ptr(hpsi), _ptr(spsi),
+                                  _ptr(items) if n else None, n, nvec_per_k, _stream(stream)),
+           "pwk_hspsi_items")
 
 
 def davidson_batched(plan: Plan, mode: int, psi, eig, nb: int, eth: float, res_tol: float = 0.0,

@@ -63,6 +63,35 @@ def test_dependent_row_is_left_out():
     assert np.max(np.abs(vec.cpu().numpy()[0][20])) < 1e-12
 
 
+def test_nearly_dependent_chain_matches_oracle():
+    """Vectors that add less than 1e-3 of a new direction (pivot below 1e-6 of the diagonal),
+    one of them built on another such vector, and an exact linear combination: all are left
+    out, the Ritz values equal the oracle's and no spurious value appears below the spectrum."""
+    torch = torch_cuda()
+    from paper_2412_01695_gb300 import pwk
+    rng = np.random.default_rng(11)
+    n, nev, m = 32, 8, 80
+    B = rng.standard_normal((n, m)) + 1j * rng.standard_normal((n, m))
+    B /= np.linalg.norm(B, axis=1, keepdims=True)
+    noise = lambda: 1e-4 * (rng.standard_normal(m) + 1j * rng.standard_normal(m)) / np.sqrt(2 * m)  # noqa: E731
+    B[20] = B[3] + noise()
+    B[21] = B[20] + noise()
+    B[25] = 3.0 * B[7] - 2.0 * B[11]
+    B[28] = B[25] + noise()
+    A = rng.standard_normal((m, m)) + 1j * rng.standard_normal((m, m))
+    A = A + A.conj().T
+    S = np.ascontiguousarray((B.conj() @ B.T)[None])
+    H = np.ascontiguousarray((B.conj() @ A @ B.T)[None])
+    eig, vec = pwk.eigh_batched(torch.from_numpy(H).cuda(), torch.from_numpy(S).cuda(), nev)
+    w, v = dav._reduced_eig(H[0], S[0], nev)
+    np.testing.assert_allclose(eig.cpu().numpy()[0], w, atol=1e-9 * np.max(np.abs(w)))
+    V = vec.cpu().numpy()[0]
+    for r in (20, 21, 25, 28):
+        assert np.max(np.abs(V[r])) < 1e-12
+    # lower bound: no Ritz value below the smallest eigenvalue of A
+    assert eig.cpu().numpy()[0].min() >= np.linalg.eigvalsh(A)[0] - 1e-9
+
+
 def test_indefinite_leading_block_reports_status():
     torch = torch_cuda()
     from paper_2412_01695_gb300 import pwk
