@@ -183,6 +183,31 @@ int pwk_davidson_batched(pwk_plan* plan, int mode, void* psi, double* eig, int n
                          double res_tol, int max_iter, int max_basis, int* iters_out,
                          int* notconv_out, long long* napply_out, void* stream);
 
+/* ---------------------------------------------------------------------------- induced density
+ * pwk_drho_batched: the charge density induced by the perturbation (Eq. drho, Sec. 2.3),
+ *   drho(r) = 4 sum_k w_k sum_{nu < nocc} conj(u_{k,nu}(r)) [P_c du_{k,nu}](r),
+ * without the augmentation term (which the paper did not accelerate).  u(r) is the inverse
+ * transform without normalisation of Sec. 2.2.2 (u on the k sphere of plan_k, du on the k+q
+ * sphere of plan_kq); P_c du = du - sum_v psi_{k+q,v} <S psi_{k+q,v}|du> with the overlap of
+ * plan_kq (S = 1 without q).
+ *   plan_kq, plan_k  as for pwk_sternheimer_cg_batched (same nk, cell and grid)
+ *   precision  PWK_FP64, or PWK_FP32_C128 (FP32 transforms, FP64 products and sums)
+ *   psi_k      device [nk][nocc][npw_max(k)] complex128
+ *   psi_kq     device [nk][nocc][npw_max(k+q)] complex128: valence states of k+q
+ *              (S-orthonormal)
+ *   dpsi       device [nk][nocc][npw_max(k+q)] complex128: du_{k,nu} (e.g. the output of
+ *              pwk_sternheimer_cg_batched)
+ *   weights    device float64 [nk]: w_k (1/N_k for a full unreduced grid)
+ *   drho       device complex128 [N][N][N] (l3 fastest): overwritten with the result, per grid
+ *              point (the 1/Omega of a density per volume is left out)
+ * Each (k, nu) pair is transformed by one CTA and its product added to one of 256 partial
+ * grids; the partial grids are summed in a fixed order, so the result is reproducible bit for
+ * bit.  Scratch (P_c du, the partial grids) comes from the library's stream-ordered pool.
+ * Asynchronous on `stream`. */
+int pwk_drho_batched(pwk_plan* plan_kq, pwk_plan* plan_k, int precision, const void* psi_k,
+                     const void* psi_kq, const void* dpsi, int nocc, const double* weights,
+                     void* drho, void* stream);
+
 /* pwk_eigh_batched: the batched generalized Hermitian eigensolver of the Davidson reduced
  * problem as a stand-alone call (paper Sec. 6: ZHEGV for many k-points at once).  For each
  * problem p < nprob: H_p v = eps S_p v, the nev lowest eigenpairs, FP64, one CTA per problem

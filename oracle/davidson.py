@@ -13,8 +13,9 @@ Readings of points the paper leaves open (listed with the design notes):
   * a restart keeps the current Ritz vectors (the "restart with {phi^(n+1), eps^(n+1)}" step);
   * when the preconditioned residual is numerically parallel to its Ritz vector
     (|cos| > 1 - 1e-6, which happens when H is diagonal in the plane-wave basis and the
-    diagonal preconditioner is exact) the unpreconditioned residual is used instead, so the
-    correction always brings a new direction;
+    diagonal preconditioner is exact), or when the band's previous correction was left out
+    of the reduced problem as dependent on the basis, the unpreconditioned residual is used
+    instead (Galerkin-orthogonal to the basis), so the correction brings a new direction;
   * basis vectors that are numerically dependent on the earlier ones (the Cholesky pivot of
     S~ below 1e-6 of its diagonal, a new direction below 1e-3 of the vector's norm) are
     left out of the reduced problem.
@@ -35,6 +36,12 @@ def _reduced_eig(Hr, Sr, nb, drop_tol=1e-6):
     """Lowest nb eigenpairs of (H~ - eps S~) v = 0 on the basis vectors that are independent:
     a vector whose Cholesky pivot falls below drop_tol of its S~ diagonal is left out (its
     coefficients are zero)."""
+    w, full, _ = _reduced_eig_keep(Hr, Sr, nb, drop_tol)
+    return w, full
+
+
+def _reduced_eig_keep(Hr, Sr, nb, drop_tol=1e-6):
+    """_reduced_eig, also returning the indices of the basis vectors kept."""
     n = len(Sr)
     keep = []
     for j in range(n):
@@ -49,7 +56,7 @@ def _reduced_eig(Hr, Sr, nb, drop_tol=1e-6):
     w, v = scipy.linalg.eigh(Hr[np.ix_(keep, keep)], Sr[np.ix_(keep, keep)])
     full = np.zeros((n, nb), np.complex128)
     full[keep] = v[:, :nb]
-    return w[:nb], full
+    return w[:nb], full, keep
 
 
 def _reduced(basis, hbasis, sbasis):
@@ -85,7 +92,8 @@ def davidson(apply_h, h_diag: np.ndarray, psi0: np.ndarray, eth: float = 1e-10,
     napply = nb
     # 1. reduced problem on the trial vectors, eigenpairs {phi^(n), eps^(n)}
     Hr, Sr = _reduced(basis, hbasis, sbasis)
-    eps, vecs = _reduced_eig(Hr, Sr, nb)
+    eps, vecs, keep = _reduced_eig_keep(Hr, Sr, nb)
+    last = np.full(nb, -1)                  # basis row of each band's latest correction
     todo = np.arange(nb)                    # the first step corrects every band
     conv = np.zeros(nb, bool)
     it = 0
@@ -98,7 +106,8 @@ def davidson(apply_h, h_diag: np.ndarray, psi0: np.ndarray, eth: float = 1e-10,
         corr = resid / _precondition_denominator(h_diag[None, :] - eps[todo, None] * s_diag[None, :])
         cos = np.abs(np.sum(ritz.conj() * corr, axis=1)) / (
             np.linalg.norm(ritz, axis=1) * np.linalg.norm(corr, axis=1))
-        parallel = cos > 1.0 - 1e-6
+        dropped = np.array([last[i] >= 0 and last[i] not in keep for i in todo], bool)
+        parallel = (cos > 1.0 - 1e-6) | dropped
         corr[parallel] = resid[parallel]
         # 3. normalisation
         corr /= np.linalg.norm(corr, axis=1, keepdims=True)
@@ -107,14 +116,16 @@ def davidson(apply_h, h_diag: np.ndarray, psi0: np.ndarray, eth: float = 1e-10,
             basis = vecs.T @ basis
             hbasis = vecs.T @ hbasis
             sbasis = vecs.T @ sbasis
+            last[:] = -1
         # 4. extended reduced Hamiltonian and overlap
+        last[todo] = basis.shape[0] + np.arange(len(todo))
         basis = np.vstack([basis, corr])
         hbasis = np.vstack([hbasis, apply_h(corr)])
         sbasis = np.vstack([sbasis, apply_s(corr)])
         napply += len(todo)
         Hr, Sr = _reduced(basis, hbasis, sbasis)
         # 5. diagonalise the N_base x N_base reduced problem
-        eps_new, vecs = _reduced_eig(Hr, Sr, nb)
+        eps_new, vecs, keep = _reduced_eig_keep(Hr, Sr, nb)
         # 6. bands whose eigenvalue moved by more than eps_th still need a correction
         moved = np.abs(eps_new - eps) > eth
         if res_tol is not None:

@@ -36,6 +36,8 @@ struct DavWork {
   double2 *phi = nullptr, *hphi = nullptr, *corr = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;
   double2 *sphi = nullptr, *tmp3 = nullptr;
   double* sdiag = nullptr;
+  unsigned char* drop = nullptr;   // [nk][MB] basis vectors the last eigensolve left out
+  int* lastrow = nullptr;          // [nk][nb] basis row of each band's latest correction
   double2 *Hr = nullptr, *Sr = nullptr, *W = nullptr, *ev = nullptr;
   double *eps = nullptr, *eps_new = nullptr, *hdiag = nullptr, *rnorm = nullptr;
   int *nbase = nullptr, *nnc = nullptr, *todo = nullptr, *active = nullptr, *moved = nullptr;
@@ -91,7 +93,8 @@ static int ensure_dav_work(pwk_plan* p, int nb, int MB) {
       (rc = dalloc(p, w, &w->status, nk)) || (rc = dalloc(p, w, &w->failcount, nk)) ||
       (rc = dalloc(p, w, &w->force, nk)) || (rc = dalloc(p, w, &w->dbg, 4)) ||
       (rc = dalloc(p, w, &w->phase, nk)) || (rc = dalloc(p, w, &w->switchk, nk)) ||
-      (rc = dalloc(p, w, &w->iterk, nk)) || (rc = dalloc(p, w, &w->counters, 8))) {
+      (rc = dalloc(p, w, &w->iterk, nk)) || (rc = dalloc(p, w, &w->counters, 8)) ||
+      (rc = dalloc(p, w, &w->drop, nk * MB)) || (rc = dalloc(p, w, &w->lastrow, nk * nb))) {
     destroy_dav_work(p);
     return rc;
   }
@@ -262,16 +265,19 @@ __global__ void __launch_bounds__(256) rotate_kernel(int nb, int MB, int np, con
 
 // Correction vector of band i (Sec. 2.1): r = sum_j v_ji (H phi_j - eps_i S phi_j),
 // c = r / clamp(H_diag - eps_i S_diag), c /= ||c||.  ||r|| is stored for the residual test.
-// When c is numerically parallel to the Ritz vector (|cos| > 1 - 1e-6: H diagonal in plane
-// waves, exact preconditioner) the unpreconditioned r is used, so the correction is a new
-// direction.  sphi = phi and sdiag = null when S = 1.
+// The unpreconditioned r (orthogonal to the whole basis by the Galerkin condition, so a new
+// direction whenever it is not zero) is used instead when c is numerically parallel to the
+// Ritz vector (|cos| > 1 - 1e-6: H diagonal in plane waves, exact preconditioner) or when the
+// band's previous correction was left out of the reduced problem as dependent on the basis.
+// sphi = phi and sdiag = null when S = 1.
 __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, const int* npw,
                                                     const int* nbase, const int* active,
                                                     const int* moved, int all_bands,
                                                     const double2* ev, const double* eps,
                                                     const double2* phi, const double2* hphi,
                                                     const double2* sphi, const double* hdiag,
-                                                    const double* sdiag, double2* corr,
+                                                    const double* sdiag, const unsigned char* drop,
+                                                    const int* lastrow, double2* corr,
                                                     double* rnorm) {
   const int k = blockIdx.x / nb, i = blockIdx.x % nb;
   if (!active[k]) return;
@@ -317,7 +323,9 @@ __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, cons
   zz = bsum(zz, red);
   zcx = bsum(zcx, red);
   zcy = bsum(zcy, red);
-  const bool parallel = (zcx * zcx + zcy * zcy) > (1.0 - 1e-6) * (1.0 - 1e-6) * zz * cc;
+  const int lr = lastrow[k * nb + i];
+  const bool was_dropped = lr >= 0 && lr < n && drop[(size_t)k * MB + lr] != 0;
+  const bool parallel = was_dropped || (zcx * zcx + zcy * zcy) > (1.0 - 1e-6) * (1.0 - 1e-6) * zz * cc;
   const double nrm2 = parallel ? rr : cc;
   const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
   for (int g = threadIdx.x; g < np; g += blockDim.x) {
@@ -396,10 +404,12 @@ __global__ void set_value_kernel(int nk, const int* mask, int* a, int v) {
 }
 
 __global__ void append_kernel(int nb, int MB, int np, const int* active, const int* nbase,
-                              const int* nnc, const int* todo, const double2* corr, double2* phi) {
+                              const int* nnc, const int* todo, const double2* corr, double2* phi,
+                              int* lastrow) {
   const int k = blockIdx.x / nb, t = blockIdx.x % nb;
   if (!active[k] || t >= nnc[k]) return;
   const int i = todo[k * nb + t];
+  if (threadIdx.x == 0) lastrow[k * nb + i] = nbase[k] + t;
   const double2* s = corr + ((size_t)k * nb + i) * np;
   double2* d = phi + ((size_t)k * MB + nbase[k] + t) * np;
   for (int g = threadIdx.x; g < np; g += blockDim.x) d[g] = s[g];
@@ -572,6 +582,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->force, 0);
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->failcount, 0);
   fill_int_kernel<<<1, 32, 0, st>>>(4, w->dbg, 0);
+  fill_int_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk * nb, w->lastrow, -1);
   copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi, MB, 0, nullptr);
   KCHECK("davidson init");
 
@@ -601,7 +612,8 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
                                                  w->phi, w->hphi, sphi, w->Hr, w->Sr);
     KCHECK("gram_kernel");
     set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, mask, w->nbase, nb, nullptr);
-    return launch_rr(nk, MB, nb, w->nbase, mask, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st);
+    return launch_rr(nk, MB, nb, w->nbase, mask, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st,
+                     w->drop);
   };
 
   if ((rc = start_block(mode == PWK_FP64 ? PWK_FP64 : PWK_FP32_C128, w->active, nk))) return rc;
@@ -617,7 +629,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
     resid_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved,
                                           (rt1 > 0 || res_tol > 0) ? 1 : 0, w->ev, w->eps, w->phi,
                                           w->hphi, sphi, w->hdiag, w->with_s ? w->sdiag : nullptr,
-                                          w->corr, w->rnorm);
+                                          w->drop, w->lastrow, w->corr, w->rnorm);
     KCHECK("resid_kernel");
     cudaMemsetAsync(w->counters, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(w->counters + 2, 0xff, sizeof(int), st);
@@ -675,7 +687,8 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, w->nbase, nb, nullptr);
       KCHECK("davidson restart");
       // append the corrections, apply H to them (FP32 for phase-1 k, FP64 for phase-2 k)
-      append_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->iterk, w->nbase, w->nnc, w->todo, w->corr, w->phi);
+      append_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->iterk, w->nbase, w->nnc, w->todo, w->corr, w->phi,
+                                             w->lastrow);
       KCHECK("davidson append");
       for (int ph = 1; ph <= 2; ++ph) {
         const int cnt = ph == 2 ? n64 : total - n64;
@@ -694,7 +707,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, w->nbase, 0, w->nnc);
       KCHECK("davidson gram");
       if ((rc = launch_rr(nk, MB, nb, w->nbase, w->iterk, w->Hr, w->Sr, w->W, w->ev, w->eps_new,
-                          w->status, st)))
+                          w->status, st, w->drop)))
         return rc;
       trace_reduced(w, it);
       update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->iterk, 0,

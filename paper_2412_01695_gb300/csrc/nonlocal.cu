@@ -9,7 +9,7 @@
 //
 // The paper computes these as matrix-matrix products over the bands of a k-point.  Here one
 // CTA takes eight consecutive work items (one warp each); the bands of one k share its
-// projectors, so the CTA stages beta(k) through shared memory in tiles of nl_chunk projectors
+// projectors, so the CTA stages beta(k) through shared memory in tiles of PC projectors
 // x kNlTile plane waves and every warp of that k reads the tile from there: beta(k) crosses
 // L2 once per eight bands instead of once per band.  Tiles move by asynchronous copies
 // (cp.async) through a ring of kNlStages buffers, so a CTA keeps two tiles in flight while it
@@ -32,8 +32,23 @@ namespace {
 constexpr int kNlItems = 8;     // work items (warps) per CTA
 constexpr int kNlTile = 128;    // plane waves per staged tile
 // projectors per staged tile (the accumulators of a chunk live in registers)
-template <typename T>
-__host__ __device__ constexpr int nl_chunk() { return sizeof(T) == 4 ? 16 : 8; }
+// Projectors per staged tile, PC, is a template parameter: every projector loop is unrolled
+// over exactly PC accumulators.  The host picks PC from {4, 8, 9, 12, 16} so that the chunks
+// cover nkb with the fewest unused slots (9 for one s+p+d atom, 12 for four such atoms).
+constexpr int kNlPcs[] = {16, 12, 9, 8, 4};
+int nl_pick_pc(int nkb, int max_pc) {
+  int best = 4, best_waste = 1 << 30, best_chunks = 1 << 30;
+  for (int pc : kNlPcs) {
+    if (pc > max_pc) continue;
+    const int chunks = (nkb + pc - 1) / pc, waste = chunks * pc - nkb;
+    if (waste < best_waste || (waste == best_waste && chunks < best_chunks)) {
+      best = pc;
+      best_waste = waste;
+      best_chunks = chunks;
+    }
+  }
+  return best;
+}
 
 // (k, vin, vout) of work item `item`; k = -1 when the warp has nothing to do.
 __device__ __forceinline__ void nl_item(const NlArgs& a, int item, int& k, int& vin, int& vout) {
@@ -82,11 +97,11 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 // Shared-memory ring of kNlStages tiles: beta(k) projectors [c0, c0 + nc) x plane waves
 // [g0, g0 + kNlTile) and, for the projection, the same plane waves of the CTA's input vectors.
-template <typename T, typename TI>
+template <typename T, typename TI, int PC>
 struct NlRing {
   using V = c2_t<T>;
   using VI = c2_t<TI>;
-  static constexpr int kChunk = nl_chunk<T>();
+  static constexpr int kChunk = PC;
   static constexpr size_t kBeta = (size_t)kChunk * kNlTile * sizeof(V);
   static constexpr size_t kPsi = (size_t)kNlItems * kNlTile * sizeof(VI);
   static constexpr size_t kSlot = kBeta + kPsi;
@@ -116,11 +131,11 @@ struct NlRing {
   }
 };
 
-template <typename T, typename TI>
-__global__ void __launch_bounds__(kNlThreads, 3) nl_project_kernel(NlArgs a) {
+template <typename T, typename TI, int PC>
+__global__ void __launch_bounds__(kNlThreads, sizeof(T) == 4 ? 3 : 2) nl_project_kernel(NlArgs a) {
   using V = c2_t<T>;
   using VI = c2_t<TI>;
-  using Ring = NlRing<T, TI>;
+  using Ring = NlRing<T, TI, PC>;
   constexpr int kNlChunk = Ring::kChunk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Ring ring{smem_raw};
@@ -216,11 +231,11 @@ __global__ void __launch_bounds__(kNlThreads, 3) nl_project_kernel(NlArgs a) {
   }
 }
 
-template <typename T, typename TI>
-__global__ void __launch_bounds__(kNlThreads, 3) nl_addback_kernel(NlArgs a) {
+template <typename T, typename TI, int PC>
+__global__ void __launch_bounds__(kNlThreads, sizeof(T) == 4 ? 3 : 2) nl_addback_kernel(NlArgs a) {
   using V = c2_t<T>;
   using VI = c2_t<TI>;
-  using Ring = NlRing<T, TI>;
+  using Ring = NlRing<T, TI, PC>;
   constexpr int kNlChunk = Ring::kChunk;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const Ring ring{smem_raw};
@@ -247,7 +262,8 @@ __global__ void __launch_bounds__(kNlThreads, 3) nl_addback_kernel(NlArgs a) {
     const int nstep = ntile * nchunk;   // steps in the order (g tile, projector chunk)
     const V* bk = static_cast<const V*>(a.beta) + (size_t)kk * a.nkb * a.npw_max;
     const bool mine = k == kk;
-    VI* pout = static_cast<VI*>(a.out) + ((size_t)kk * a.nvec_out + vout) * a.npw_max;
+    VI* pout = a.out != nullptr ? static_cast<VI*>(a.out) + ((size_t)kk * a.nvec_out + vout) * a.npw_max
+                                : nullptr;   // null: S only
     VI* sout = with_s ? static_cast<VI*>(a.sout) + ((size_t)kk * a.nvec_out + vout) * a.npw_max : nullptr;
     const VI* pin = static_cast<const VI*>(a.in) + ((size_t)kk * a.nvec_in + vin) * a.npw_max;
     auto issue = [&](int st) {
@@ -269,7 +285,7 @@ __global__ void __launch_bounds__(kNlThreads, 3) nl_addback_kernel(NlArgs a) {
         for (int u = 0; u < kNlTile / 32; ++u) {
           const int g = t * kNlTile + lane + 32 * u;
           ah[u] = as[u] = V{T(0), T(0)};
-          hv[u] = g < np ? pout[g] : VI{TI(0), TI(0)};
+          hv[u] = (g < np && pout != nullptr) ? pout[g] : VI{TI(0), TI(0)};
           if (with_s) cv[u] = g < np ? pin[g] : VI{TI(0), TI(0)};
         }
       }
@@ -300,7 +316,7 @@ __global__ void __launch_bounds__(kNlThreads, 3) nl_addback_kernel(NlArgs a) {
           for (int u = 0; u < kNlTile / 32; ++u) {
             const int g = t * kNlTile + lane + 32 * u;
             if (g < np) {
-              pout[g] = VI{TI(T(hv[u].x) + ah[u].x), TI(T(hv[u].y) + ah[u].y)};
+              if (pout != nullptr) pout[g] = VI{TI(T(hv[u].x) + ah[u].x), TI(T(hv[u].y) + ah[u].y)};
               if (with_s) sout[g] = VI{TI(T(cv[u].x) + as[u].x), TI(T(cv[u].y) + as[u].y)};
             }
           }
@@ -314,40 +330,65 @@ __global__ void __launch_bounds__(kNlThreads, 3) nl_addback_kernel(NlArgs a) {
   }
 }
 
-template <typename T, typename TI>
+template <typename T, typename TI, int PC>
 size_t nl_smem(int nkb, bool addback) {
-  return kNlStages * NlRing<T, TI>::kSlot + (size_t)kNlItems * nkb * (addback ? 2 : 1) * sizeof(c2_t<T>);
+  return kNlStages * NlRing<T, TI, PC>::kSlot + (size_t)kNlItems * nkb * (addback ? 2 : 1) * sizeof(c2_t<T>);
 }
 
-template <typename T, typename TI>
-int launch_nl_typed(const NlArgs& a, cudaStream_t st) {
-  const int nblocks = (a.nitems + kNlItems - 1) / kNlItems;
-  if (nblocks == 0 || (a.nkb == 0 && (a.phase == 0 || a.sout == nullptr))) return PWK_OK;
-  const size_t s1 = nl_smem<T, TI>(a.nkb, false);
-  const size_t s3 = nl_smem<T, TI>(a.nkb, true);
-  if (cudaError_t e = allow_full_smem(nl_project_kernel<T, TI>); e != cudaSuccess)
-    return cuda_fail(e, "cudaFuncSetAttribute(nl_project)");
-  if (cudaError_t e = allow_full_smem(nl_addback_kernel<T, TI>); e != cudaSuccess)
-    return cuda_fail(e, "cudaFuncSetAttribute(nl_addback)");
+template <typename T, typename TI, int PC>
+int launch_nl_pc(const NlArgs& a, int nblocks, cudaStream_t st) {
+  const size_t s1 = nl_smem<T, TI, PC>(a.nkb, false);
+  const size_t s3 = nl_smem<T, TI, PC>(a.nkb, true);
   if (a.phase == 0) {
-    nl_project_kernel<T, TI><<<nblocks, kNlThreads, s1, st>>>(a);
+    if (cudaError_t e = allow_full_smem(nl_project_kernel<T, TI, PC>); e != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute(nl_project)");
+    nl_project_kernel<T, TI, PC><<<nblocks, kNlThreads, s1, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "nl_project_kernel");
   } else {
-    nl_addback_kernel<T, TI><<<nblocks, kNlThreads, s3, st>>>(a);
+    if (cudaError_t e = allow_full_smem(nl_addback_kernel<T, TI, PC>); e != cudaSuccess)
+      return cuda_fail(e, "cudaFuncSetAttribute(nl_addback)");
+    nl_addback_kernel<T, TI, PC><<<nblocks, kNlThreads, s3, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "nl_addback_kernel");
   }
   return PWK_OK;
 }
 
+template <typename T>
+constexpr int nl_max_pc() { return sizeof(T) == 4 ? 16 : 9; }
+
+template <typename T, typename TI>
+int launch_nl_typed(const NlArgs& a, cudaStream_t st) {
+  const int nblocks = (a.nitems + kNlItems - 1) / kNlItems;
+  if (nblocks == 0 || (a.nkb == 0 && (a.phase == 0 || a.sout == nullptr))) return PWK_OK;
+  switch (nl_pick_pc(a.nkb, nl_max_pc<T>())) {
+    case 16: return launch_nl_pc<T, TI, 16>(a, nblocks, st);
+    case 12: return launch_nl_pc<T, TI, 12>(a, nblocks, st);
+    case 9: return launch_nl_pc<T, TI, 9>(a, nblocks, st);
+    case 8: return launch_nl_pc<T, TI, 8>(a, nblocks, st);
+    default: return launch_nl_pc<T, TI, 4>(a, nblocks, st);
+  }
+}
+
+template <typename T, typename TI>
+size_t nl_smem_picked(int nkb) {
+  switch (nl_pick_pc(nkb, nl_max_pc<T>())) {
+    case 16: return nl_smem<T, TI, 16>(nkb, true);
+    case 12: return nl_smem<T, TI, 12>(nkb, true);
+    case 9: return nl_smem<T, TI, 9>(nkb, true);
+    case 8: return nl_smem<T, TI, 8>(nkb, true);
+    default: return nl_smem<T, TI, 4>(nkb, true);
+  }
+}
+
 }  // namespace
 
 size_t nl_shared_bytes(int nkb, int precision) {
   switch (precision) {
-    case PWK_FP64: return std::max(nl_smem<double, double>(nkb, false), nl_smem<double, double>(nkb, true));
-    case PWK_FP32: return std::max(nl_smem<float, float>(nkb, false), nl_smem<float, float>(nkb, true));
-    default: return std::max(nl_smem<float, double>(nkb, false), nl_smem<float, double>(nkb, true));
+    case PWK_FP64: return nl_smem_picked<double, double>(nkb);
+    case PWK_FP32: return nl_smem_picked<float, float>(nkb);
+    default: return nl_smem_picked<float, double>(nkb);
   }
 }
 

@@ -360,7 +360,7 @@ int autotune_shape(pwk_plan* p, int precision) {
         if (c.smem <= 227 * 1024) cands.push_back(c);
       }
   if (cands.empty()) return PWK_OK;   // the default shape stands (plan creation checked it)
-  const int nv = 8, nkt = std::min(p->nk, 192);
+  const int nv = 8, nkt = std::min(p->nk, precision == PWK_FP64 ? 64 : 192);
   const size_t bytes = (size_t)nkt * nv * p->npw_max * io_elem;
   void *in = nullptr, *out = nullptr;
   if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&out, bytes) != cudaSuccess) {
@@ -374,27 +374,36 @@ int autotune_shape(pwk_plan* p, int precision) {
   cudaEventCreate(&e1);
   FusedArgs a = hpsi_args(p, precision, in, out);
   a.nvec_in = a.nvec_out = nv;
+  // two interleaved rounds over the candidates, the faster of each candidate's two timings
+  // counts (a clock ramp or another process's burst during one timing does not decide)
+  std::vector<float> tbest(cands.size(), 1e30f);
+  for (int round = 0; round < 2; ++round) {
+    for (size_t ci = 0; ci < cands.size(); ++ci) {
+      const LaunchShape& c = cands[ci];
+      a.L = c.L;
+      use_kind(p, a, c.kind);
+      if (launch_variant(precision, N, a, nkt * nv, c, 0) != PWK_OK) {
+        cudaGetLastError();
+        continue;
+      }
+      cudaEventRecord(e0, 0);
+      for (int r = 0; r < 3; ++r) launch_variant(precision, N, a, nkt * nv, c, 0);
+      cudaEventRecord(e1, 0);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        cudaGetLastError();
+        continue;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tbest[ci] = std::min(tbest[ci], ms);
+    }
+  }
   float best = 1e30f;
   LaunchShape pick = p->shape[precision];
-  for (const LaunchShape& c : cands) {
-    a.L = c.L;
-    use_kind(p, a, c.kind);
-    if (launch_variant(precision, N, a, nkt * nv, c, 0) != PWK_OK) {
-      cudaGetLastError();
-      continue;
-    }
-    cudaEventRecord(e0, 0);
-    for (int r = 0; r < 3; ++r) launch_variant(precision, N, a, nkt * nv, c, 0);
-    cudaEventRecord(e1, 0);
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      cudaGetLastError();
-      continue;
-    }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best) {
-      best = ms;
-      pick = c;
+  for (size_t ci = 0; ci < cands.size(); ++ci) {
+    if (tbest[ci] < best) {
+      best = tbest[ci];
+      pick = cands[ci];
     }
   }
   cudaEventDestroy(e0);
@@ -431,7 +440,7 @@ FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out)
 // Stream-ordered pool for per-call scratch (one per device, kept for the life of the
 // process).  Its release threshold is unbounded, so memory freed at the end of a call stays
 // mapped and the next call's allocation is a pool hit instead of a new mapping.
-static cudaError_t scratch_pool(cudaMemPool_t* pool) {
+cudaError_t scratch_pool(cudaMemPool_t* pool) {
   static std::mutex mu;
   static std::map<int, cudaMemPool_t> pools;
   int dev = 0;
@@ -454,6 +463,13 @@ static cudaError_t scratch_pool(cudaMemPool_t* pool) {
   if (e != cudaSuccess) return e;
   pools[dev] = *pool;
   return cudaSuccess;
+}
+
+cudaError_t scratch_alloc(void** ptr, size_t bytes, cudaStream_t st) {
+  cudaMemPool_t pool;
+  cudaError_t e = scratch_pool(&pool);
+  if (e == cudaSuccess) e = cudaMallocFromPoolAsync(ptr, bytes, pool, st);
+  return e;
 }
 
 int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* items,
@@ -487,10 +503,8 @@ int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* i
     n.q = f64 ? static_cast<const void*>(p->d_q) : static_cast<const void*>(p->d_q32);
     const size_t cbytes = (size_t)nblocks * 2 * p->nkb * (f64 ? 16 : 8);
     if (cbytes > 0) {
-      cudaMemPool_t pool;
-      cudaError_t e = scratch_pool(&pool);
-      if (e == cudaSuccess) e = cudaMallocFromPoolAsync(&n.coef, cbytes, pool, st);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaMallocFromPoolAsync(projector coefficients)");
+      cudaError_t e = scratch_alloc(&n.coef, cbytes, st);
+      if (e != cudaSuccess) return cuda_fail(e, "scratch_alloc(projector coefficients)");
     }
     n.phase = 0;
     if (int r = launch_nl(precision, n, st)) {
@@ -498,13 +512,16 @@ int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* i
       return r;
     }
   }
-  FusedArgs a = hpsi_args(p, precision, in, out);
-  a.items = items;
-  a.d_count = d_count;
-  a.nvec_in = nvec_in;
-  a.nvec_out = nvec_out;
-  use_kind(p, a, p->shape[precision].kind);
-  int r = launch_variant(precision, p->N, a, nblocks, p->shape[precision], st);
+  int r = PWK_OK;
+  if (out != nullptr) {   // out == null: S only (no local term, no H add-back)
+    FusedArgs a = hpsi_args(p, precision, in, out);
+    a.items = items;
+    a.d_count = d_count;
+    a.nvec_in = nvec_in;
+    a.nvec_out = nvec_out;
+    use_kind(p, a, p->shape[precision].kind);
+    r = launch_variant(precision, p->N, a, nblocks, p->shape[precision], st);
+  }
   if (nl) {
     if (r == PWK_OK) {
       n.phase = 1;

@@ -149,6 +149,9 @@ struct NlArgs {
   void* coef = nullptr;        // [nitems][2][nkb] complex of the arithmetic type
 };
 int launch_nl(int precision, const NlArgs& a, cudaStream_t st);
+// stream-ordered scratch from the library's per-device pool (memory returned with
+// cudaFreeAsync stays mapped in the pool for later calls)
+cudaError_t scratch_alloc(void** ptr, size_t bytes, cudaStream_t st);
 size_t nl_shared_bytes(int nkb, int precision);
 
 // launchers (one per arithmetic/io variant), defined in hpsi_*.cu
@@ -168,7 +171,8 @@ void window_strides(int N, int L, int* zs, int* yps);
 // fill FusedArgs for H|psi> with this plan
 FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out);
 // H (and, with sout set, S) on nblocks work items: projections, local + kinetic term,
-// nonlocal add-back (three launches on st).  sout must not alias in.
+// nonlocal add-back (three launches on st).  sout must not alias in.  out == null with sout
+// set applies S alone.
 int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* items,
              const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st,
              void* sout = nullptr);
@@ -178,4 +182,6 @@ int build_sphere_map(pwk_plan* p, SphereMap& sm, int nk, const int* npw_in, int 
                      const int* miller_in, const int* npw_out, int npw_out_max,
                      const int* miller_out, const int* d_npw_in, const int* d_npw_out);
 LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int ctas_per_sm);
+// stick maps from plan_k's spheres to plan_kq's (union of their sticks), kept in plan_kq
+int ensure_xfer(pwk_plan* pq, const pwk_plan* pk);
 }  // namespace pwk

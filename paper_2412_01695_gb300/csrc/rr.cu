@@ -50,10 +50,11 @@ __device__ double2 block_sum2(double2 v, double* red) {
 // Hr, Sr: [nk][ld][ld] (row-major, full Hermitian in the leading n x n block)
 // W: [nk][3][ld][ld] workspace; ev: [nk][ld][nb]; eps: [nk][nb]; status [nk]
 // nbase == nullptr: every problem has size ld.  status may be null (not written).
+// drop_out: [nk][ld] dependent-vector flags of the Cholesky step, or null.
 __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const int* nbase,
                                                  const int* active, const double2* Hr,
                                                  const double2* Sr, double2* W, double2* ev,
-                                                 double* eps, int* status) {
+                                                 double* eps, int* status, unsigned char* drop_out) {
   const int k = blockIdx.x;
   if (k >= nk || (active != nullptr && !active[k])) return;
   const int n = nbase != nullptr ? nbase[k] : ld;
@@ -114,6 +115,8 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     }
     __syncthreads();
   }
+  if (drop_out != nullptr)
+    for (int i = tid; i < n; i += nth) drop_out[(size_t)k * ld + i] = dropped[i];
   if (flag) {
     if (tid == 0 && status != nullptr) status[k] = PWK_ERR_NOT_POSDEF;
     return;
@@ -433,8 +436,8 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
 
 int launch_rr(int nk, int ld, int nb, const int* nbase, const int* active, const double2* Hr,
               const double2* Sr, double2* W, double2* ev, double* eps, int* status,
-              cudaStream_t st) {
-  rr_kernel<<<nk, 256, 0, st>>>(nk, ld, nb, nbase, active, Hr, Sr, W, ev, eps, status);
+              cudaStream_t st, unsigned char* drop_out) {
+  rr_kernel<<<nk, 256, 0, st>>>(nk, ld, nb, nbase, active, Hr, Sr, W, ev, eps, status, drop_out);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PWK_OK : cuda_fail(e, "rr_kernel");
 }

@@ -11,7 +11,8 @@ void destroy_dav_work(pwk_plan* p);
 void destroy_cg_work(pwk_plan* p);
 
 // batched generalized eigensolver of the reduced problem (rr.cu)
+// drop_out (optional, [nk][ld]): 1 for each basis vector left out as numerically dependent
 int launch_rr(int nk, int ld, int nb, const int* nbase, const int* active, const double2* Hr,
               const double2* Sr, double2* W, double2* ev, double* eps, int* status,
-              cudaStream_t st);
+              cudaStream_t st, unsigned char* drop_out = nullptr);
 }  // namespace pwk

@@ -325,6 +325,30 @@ __global__ void __launch_bounds__(256) cg_step_kernel(int nocc, int np, const in
   }
 }
 
+// The stick maps of the pair (k sphere of plan_k -> k+q sphere of plan_kq, the union of their
+// z-sticks), built once per pair of plans and kept in plan_kq.
+int ensure_xfer(pwk_plan* pq, const pwk_plan* pk) {
+  if (pq->xfer_src == pk) return PWK_OK;
+  if (pq->xfer.d_nstick) {
+    plan_free(pq, pq->xfer.d_nstick);
+    plan_free(pq, pq->xfer.d_gin);
+    plan_free(pq, pq->xfer.d_gout);
+    plan_free(pq, pq->xfer.d_sid);
+    pq->xfer = SphereMap();
+    pq->xfer_src = nullptr;
+  }
+  int rc = build_sphere_map(pq, pq->xfer, pq->nk, pk->h_npw.data(), pk->npw_max, pk->h_miller.data(),
+                            pq->h_npw.data(), pq->npw_max, pq->h_miller.data(), pk->d_npw, pq->d_npw);
+  if (rc) return rc;
+  pq->xshape = choose_shape(pq->N, 16, pq->xfer, 1);
+  if (pq->xshape.smem > 227 * 1024) {
+    set_error("transfer kernel does not fit in shared memory");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  pq->xfer_src = pk;
+  return PWK_OK;
+}
+
 static int nblk(size_t n, int t = 256) { return (int)((n + t - 1) / t); }
 
 #define KCK(what)                                      \
@@ -362,26 +386,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc;
-  // transfer map k sphere -> k+q sphere (built once per pair of plans)
-  if (pq->xfer_src != pk) {
-    if (pq->xfer.d_nstick) {
-      plan_free(pq, pq->xfer.d_nstick);
-      plan_free(pq, pq->xfer.d_gin);
-      plan_free(pq, pq->xfer.d_gout);
-      plan_free(pq, pq->xfer.d_sid);
-      pq->xfer = SphereMap();
-      pq->xfer_src = nullptr;
-    }
-    rc = build_sphere_map(pq, pq->xfer, pq->nk, pk->h_npw.data(), pk->npw_max, pk->h_miller.data(),
-                          pq->h_npw.data(), pq->npw_max, pq->h_miller.data(), pk->d_npw, pq->d_npw);
-    if (rc) return rc;
-    pq->xshape = choose_shape(pq->N, 16, pq->xfer, 1);
-    if (pq->xshape.smem > 227 * 1024) {
-      set_error("transfer kernel does not fit in shared memory");
-      return PWK_ERR_UNSUPPORTED;
-    }
-    pq->xfer_src = pk;
-  }
+  if ((rc = ensure_xfer(pq, pk))) return rc;
   if ((rc = ensure_cg_work(pq, nocc))) return rc;
   CgWork* w = pq->cg;
   const int nk = pq->nk, np = pq->npw_max, npairs = nk * nocc;

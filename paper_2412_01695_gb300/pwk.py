@@ -22,7 +22,7 @@ PRECISIONS = {"fp64": PWK_FP64, "fp32": PWK_FP32, "fp32_c128": PWK_FP32_C128}
 EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
            "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_supported_grid",
            "pwk_hpsi_batched", "pwk_hpsi_items", "pwk_plan_set_overlap", "pwk_plan_has_overlap",
-           "pwk_hspsi_batched", "pwk_hspsi_items", "pwk_davidson_batched",
+           "pwk_hspsi_batched", "pwk_hspsi_items", "pwk_drho_batched", "pwk_davidson_batched",
            "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_eigh_batched_noalloc",
            "pwk_strerror", "pwk_last_error_detail", "pwk_version")
 
@@ -56,6 +56,7 @@ def load(path: str = LIB_PATH):
         "pwk_plan_has_overlap": (_I, [_P]),
         "pwk_hspsi_batched": (_I, [_P, _I, _P, _P, _P, _I, _P]),
         "pwk_hspsi_items": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P]),
+        "pwk_drho_batched": (_I, [_P, _P, _I, _P, _P, _P, _I, _P, _P, _P]),
         "pwk_davidson_batched": (_I, [_P, _I, _P, _P, _I, _D, _D, _I, _I, _P, _P, _P, _P]),
         "pwk_sternheimer_cg_batched": (_I, [_P, _P, _I, _P, _P, _P, _I, _P, _P, _P, _D, _I, _P,
                                             _P, _P]),
@@ -237,6 +238,21 @@ def hspsi_items(plan: Plan, precision: int, psi, hpsi, spsi, items, nvec_per_k: 
     _check(load().pwk_hspsi_items(plan.handle, precision, _ptr(psi), _ptr(hpsi), _ptr(spsi),
                                   _ptr(items) if n else None, n, nvec_per_k, _stream(stream)),
            "pwk_hspsi_items")
+
+
+def drho_batched(plan_kq: Plan, plan_k: Plan, precision: int, psi_k, psi_kq, dpsi, nocc: int,
+                 weights, drho, stream=None) -> None:
+    """pwk_drho_batched: drho (complex128 [N, N, N]) from u_k, the k+q valence states and du."""
+    import torch
+    nk = plan_kq.nk
+    _need(psi_k, (nk, nocc, plan_k.npw_max), torch.complex128, "psi_k")
+    _need(psi_kq, (nk, nocc, plan_kq.npw_max), torch.complex128, "psi_kq")
+    _need(dpsi, (nk, nocc, plan_kq.npw_max), torch.complex128, "dpsi")
+    _need(weights, (nk,), torch.float64, "weights")
+    _need(drho, (plan_kq.N,) * 3, torch.complex128, "drho")
+    _check(load().pwk_drho_batched(plan_kq.handle, plan_k.handle, precision, _ptr(psi_k), _ptr(psi_kq),
+                                   _ptr(dpsi), nocc, _ptr(weights), _ptr(drho), _stream(stream)),
+           "pwk_drho_batched")
 
 
 def davidson_batched(plan: Plan, mode: int, psi, eig, nb: int, eth: float, res_tol: float = 0.0,
