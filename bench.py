@@ -381,6 +381,40 @@ def run_solvers(dev, stream, quick=False):
         sres[name] = {"time_s": dt, "pairs_above_tol": int(rc), "iters_max": int(iters.max()),
                       "iters_mean": float(iters.mean()), "max_true_residual": float(resid.max())}
     out["sternheimer"] = sres
+
+    # induced density (Eq. drho) from the Sternheimer solution just computed
+    w = torch.full((nk4,), 1.0 / nk4, dtype=torch.float64, device=dev)
+    drho = torch.empty((pk.N,) * 3, dtype=torch.complex128, device=dev)
+    dres = {"k_points": nk4, "nocc": nocc, "pairs": nk4 * nocc}
+    for name, prec in (("fp32", pwk.PWK_FP32_C128), ("fp64", pwk.PWK_FP64)):
+        pwk.drho_batched(plan_q, plan_k, prec, psi_k, psi_q, dpsi, nocc, w, drho, stream)
+        torch.cuda.synchronize()
+        reps = 5
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            pwk.drho_batched(plan_q, plan_k, prec, psi_k, psi_q, dpsi, nocc, w, drho, stream)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / reps
+        dres[name] = {"time_ms": dt * 1e3, "pairs_per_s": nk4 * nocc / dt}
+    # the GPU result on 4 k-points (weights 1/nk4), checked against the oracle by the host leg
+    ks_s = [0, 1, nk4 // 2, nk4 - 1]
+    sub = torch.tensor(ks_s, device=dev)
+    pk_s = synth.make_config(4, k_subset=ks_s, with_psi=False)
+    pq_s = synth.make_config(4, k_subset=ks_s, with_psi=False, shift_q=True)
+    pl_k, pl_q = pwk.plan_from_problem(pk_s, device=dev), pwk.plan_from_problem(pq_s, device=dev)
+    # the sample plans pad to their own (smaller) npw_max: the entries cut are zero padding
+    u_k = psi_k[sub][:, :, :pk_s.npw_max].contiguous()
+    u_q = psi_q[sub][:, :, :pq_s.npw_max].contiguous()
+    d_s = dpsi[sub][:, :, :pq_s.npw_max].contiguous()
+    w_s = torch.full((4,), 1.0 / nk4, dtype=torch.float64, device=dev)
+    out_s = torch.empty_like(drho)
+    pwk.drho_batched(pl_q, pl_k, pwk.PWK_FP64, u_k, u_q, d_s, nocc, w_s, out_s, stream)
+    torch.cuda.synchronize()
+    out["_drho_sample"] = (ks_s, nk4, u_k.cpu().numpy(), u_q.cpu().numpy(), d_s.cpu().numpy(),
+                           out_s.cpu().numpy())
+    pl_k.close()
+    pl_q.close()
+    out["drho"] = dres
     plan_k.close()
     plan_q.close()
     return out
@@ -490,12 +524,13 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("gloo")
     res, prob, (psi32, out32) = run_ours(args, rank, world, local_rank)
-    eig_mixed = None
+    eig_mixed = drho_sample = None
     if rank == 0 and not args.no_solvers:
         import torch
         sol = run_solvers(torch.device("cuda", local_rank), torch.cuda.current_stream(),
                           quick=args.quick)
         eig_mixed = sol.pop("_eig_mixed", None)
+        drho_sample = sol.pop("_drho_sample", None)
         res.update(sol)
         if not args.no_serving:
             res["serving"] = run_serving(n_jobs=20 if args.quick else 40)
@@ -515,6 +550,14 @@ def main():
             errs = [float(np.max(np.abs(eig_mixed[ik] - dav.lowest_eigenpairs(
                 ham.problem_h(p2, ik, vt), p2.nb)[0]))) for ik in synth.sample_k(p2.nk, 3, seed=4)]
             res["davidson"]["mixed"]["max_abs_eig_err_ry_vs_oracle"] = max(errs)
+        if drho_sample is not None:
+            from oracle import drho as odr
+            from paper_2412_01695_gb300 import synth
+            ks_s, nk4, u_k, u_q, d_s, got = drho_sample
+            pk_s = synth.make_config(4, k_subset=ks_s, with_psi=False)
+            pq_s = synth.make_config(4, k_subset=ks_s, with_psi=False, shift_q=True)
+            ref = odr.drho(pk_s, pq_s, u_k, u_q, d_s, weights=np.full(len(ks_s), 1.0 / nk4))
+            res["drho"]["fp64_rel_err_vs_oracle_4k"] = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -84,15 +84,17 @@ void pwk_plan_destroy(pwk_plan* plan);
 size_t pwk_plan_device_bytes(const pwk_plan* plan);
 
 /* Launch shape of the H|psi> kernel for one precision (PWK_FP64, PWK_FP32 or PWK_FP32_C128):
- * kernel kind (0: general sphere kernel; 1: window kernel, usable when every |m_i| <= N/4),
- * threads per CTA, l3 planes per shared-memory chunk and dynamic shared memory per CTA.
- * pwk_plan_create times the candidate shapes on the plan's own k-points and keeps the
- * fastest; every shape computes the same operator (bitwise the same result within a kind).
+ * kernel kind (0: general sphere kernel; 1: window kernel, usable when every |m_i| <= N/4,
+ * the CTA taking l3 planes in chunks; 2: the window kernel with each warp taking its own
+ * planes, l3_chunk = planes per warp, 1 or 2), threads per CTA, l3 planes per chunk and
+ * dynamic shared memory per CTA.  pwk_plan_create times the candidate shapes on the plan's
+ * own k-points and keeps the fastest; every shape computes the same operator (bitwise the
+ * same result for kinds 1 and 2 and any threads / chunk; kind 0 rounds differently).
  * Any output pointer may be NULL. */
 int pwk_plan_launch_shape(const pwk_plan* plan, int precision, int* kind, int* threads,
                           int* l3_chunk, size_t* smem_bytes);
 
-/* Override the launch shape of one precision: kind 0 or 1, threads 96, 128, 192 or 256,
+/* Override the launch shape of one precision: kind 0, 1 or 2, threads 96, 128, 192 or 256,
  * 1 <= l3_chunk <= N.  Returns PWK_ERR_UNSUPPORTED if the shape does not fit in shared
  * memory or the window kernel does not apply to the plan (the shape is then unchanged). */
 int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threads, int l3_chunk);

@@ -218,4 +218,74 @@ template <typename T, int N, int DIR> struct LineFFT {
   }
 };
 
+// ------------------------------------------------------------------ known-zero inputs
+// A radix-R butterfly whose inputs n with bit n of ZM set are known to be zero (compile-time
+// mask; the zero inputs must hold zeros).  IEEE arithmetic forbids dropping "x + 0" (the
+// sign of a zero), so the compiler cannot prune these operations itself: when at most half
+// the inputs are present the butterfly becomes the direct sum over them, with trivial
+// twiddles (+-1, +-i) free; otherwise the full butterfly runs on the zeros.
+__host__ __device__ constexpr int popcount_bits(unsigned m) { return m == 0u ? 0 : int(m & 1u) + popcount_bits(m >> 1); }
+
+template <typename T, int R, int DIR, unsigned ZM>
+struct ButterflyZ {
+  using V = c2_t<T>;
+  template <int S>
+  static PWK_HD void run(V* x) {
+    if constexpr (2 * (R - popcount_bits(ZM)) > R) {
+      Butterfly<T, R, DIR>::template run<S>(x);   // more than half the inputs present
+    } else if constexpr (ZM == (1u << R) - 1u) {
+      static_for<R>([&](auto kc) { x[decltype(kc)::value * S] = V{T(0), T(0)}; });
+    } else {
+      V in[R];
+      static_for<R>([&](auto nc) {
+        constexpr int n = decltype(nc)::value;
+        if constexpr (!((ZM >> n) & 1u)) in[n] = x[n * S];
+      });
+      static_for<R>([&](auto kc) {
+        constexpr int k = decltype(kc)::value;
+        V acc{T(0), T(0)};
+        bool first = true;
+        static_for<R>([&](auto nc) {
+          constexpr int n = decltype(nc)::value;
+          if constexpr (!((ZM >> n) & 1u)) {
+            const V t = twiddle<T, R, n * k, DIR>(in[n]);
+            acc = first ? t : cadd(acc, t);
+            first = false;
+          }
+        });
+        x[k * S] = acc;
+      });
+    }
+  }
+};
+
+// The line transform of LineFFT (same factorisation, same output slots) when the inputs x[i]
+// with Z::zero(i) true are known to be zero: only the first butterfly stage sees them, and
+// it is pruned; the twiddles and the inner transforms are those of LineFFT.
+template <typename T, int N, int DIR, typename Z>
+struct LineFFTZ {
+  using V = c2_t<T>;
+  static constexpr int R = first_radix(N);
+  static constexpr int M = N / R;
+  template <int n2>
+  __host__ __device__ static constexpr unsigned mask() {
+    unsigned m = 0;
+    for (int n1 = 0; n1 < R; ++n1)
+      if (Z::zero(M * n1 + n2)) m |= 1u << n1;
+    return m;
+  }
+  static PWK_HD void run(V* x) {
+    if constexpr (M == 1) {
+      ButterflyZ<T, R, DIR, mask<0>()>::template run<1>(x);
+    } else {
+      static_for<M>([&](auto n2) {
+        constexpr int j = decltype(n2)::value;
+        ButterflyZ<T, R, DIR, mask<j>()>::template run<M>(x + j);
+      });
+      LineFFT<T, N, DIR>::apply_twiddles(x, std::make_integer_sequence<int, N>{});
+      static_for<R>([&](auto k1) { LineFFT<T, M, DIR>::run(x + M * decltype(k1)::value); });
+    }
+  }
+};
+
 }  // namespace pwk

@@ -27,7 +27,19 @@ struct Win {
   __host__ __device__ static constexpr int idx(int i) { return i <= W ? i + W : i - N + W; }  // 0 .. 2W
 };
 
-template <typename T, typename TI, int N, int W>
+// inputs outside the window, known zero in the inverse transforms (LineFFTZ prunes them)
+template <int N, int W>
+struct OutOfWin {
+  __host__ __device__ static constexpr bool zero(int i) { return !Win<N, W>::in(i); }
+};
+
+// MODE 0: the CTA takes the l3 planes in chunks of L, with block barriers between the y, x
+//         and y passes of a chunk.
+// MODE 1: each warp takes its own L planes at a time (planes w L, w L + 1, ... in rounds of
+//         nwarps L) through the y, x and y passes with warp-level synchronisation only; block
+//         barriers remain only around the z passes.  The arithmetic of every line is the same
+//         in both modes (the results are bitwise equal); only the thread mapping differs.
+template <typename T, typename TI, int N, int W, int MODE>
 __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
   using V = c2_t<T>;
   using VI = c2_t<TI>;
@@ -58,7 +70,9 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
 
   V* Z = reinterpret_cast<V*>(smem_raw);               // [NW*NW][zs]
   V* Y = Z + (size_t)NW * NW * zs;                      // [NW][yps] (N x L used per plane)
-  short* rows = reinterpret_cast<short*>(Y + (size_t)NW * yps);  // [nstick_max]
+  // plane buffers: one [NW][yps] for the CTA (MODE 0) or one per warp (MODE 1), then the rows
+  const int ycopies = MODE == 1 ? (int)(blockDim.x >> 5) : 1;
+  short* rows = reinterpret_cast<short*>(Y + (size_t)ycopies * NW * yps);  // [nstick_max]
 
   const VI* pin = static_cast<const VI*>(a.in) + ((size_t)k * a.nvec_in + vin) * a.npw_in_max;
   VI* pout = static_cast<VI*>(a.out) + ((size_t)k * a.nvec_out + vout) * a.npw_out_max;
@@ -89,11 +103,12 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
     V x[N];
     V* zr = Z + rows[s] * zs;
     PWK_SFOR(N, j, x[j] = Wn::in(j) ? zr[j] : V{T(0), T(0)});
-    LineFFT<T, N, +1>::run(x);
+    LineFFTZ<T, N, +1, OutOfWin<N, W>>::run(x);
     PWK_SFOR(N, j, zr[j] = x[OutSlot<N, j>::value]);
   }
   __syncthreads();
 
+  if constexpr (MODE == 0) {
   // ---- 3: planes l3 in chunks of L
   for (int l0 = 0; l0 < N; l0 += L) {
     const int lc = min(L, N - l0);
@@ -103,7 +118,7 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
       V x[N];
       const V* zp = Z + (size_t)p * NW * zs + l0 + c;
       PWK_SFOR(N, j, x[j] = Wn::in(j) ? zp[Wn::idx(j) * zs] : V{T(0), T(0)});
-      LineFFT<T, N, +1>::run(x);
+      LineFFTZ<T, N, +1, OutOfWin<N, W>>::run(x);
       V* yp = Y + (size_t)p * yps + c;
       PWK_SFOR(N, l2, yp[l2 * L] = x[OutSlot<N, l2>::value]);
     }
@@ -117,7 +132,7 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
       V x[N];
       const V* yl = Y + (size_t)l2 * L + c;
       PWK_SFOR(N, i, x[i] = Wn::in(i) ? yl[(size_t)Wn::idx(i) * yps] : V{T(0), T(0)});
-      LineFFT<T, N, +1>::run(x);
+      LineFFTZ<T, N, +1, OutOfWin<N, W>>::run(x);
       V y[N];
       PWK_SFOR(N, l1, {
         const V u = x[OutSlot<N, l1>::value];
@@ -141,6 +156,60 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
       PWK_SFOR(N, j, {
         if constexpr (Wn::in(j)) zp[Wn::idx(j) * zs] = x[OutSlot<N, j>::value];
       });
+    }
+    __syncthreads();
+  }
+  } else {
+    // ---- 3 (MODE 1): each warp carries L planes of its own through y, x, y
+    const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
+    V* Yw = Y + (size_t)warp * NW * yps;        // [NW][yps]: plane p row, (l2, cc) at l2 L + cc
+    for (int l0 = warp * L; l0 < N; l0 += nw * L) {
+      const int lc = min(L, N - l0);
+      // y inverse: lane -> (plane p, column cc), inputs on the m2 window
+      for (int t = lane; t < NW * lc; t += 32) {
+        const int c = t / NW, p = t - c * NW;
+        V x[N];
+        const V* zp = Z + (size_t)p * NW * zs + l0 + c;
+        PWK_SFOR(N, j, x[j] = Wn::in(j) ? zp[Wn::idx(j) * zs] : V{T(0), T(0)});
+        LineFFTZ<T, N, +1, OutOfWin<N, W>>::run(x);
+        V* yp = Yw + (size_t)p * yps + c;
+        PWK_SFOR(N, l2, yp[l2 * L] = x[OutSlot<N, l2>::value]);
+      }
+      __syncwarp();
+      // x lines: inverse x, V(r) product, forward x (window outputs only)
+      for (int t = lane; t < N * lc; t += 32) {
+        const int l2 = t / lc, c = t - l2 * lc;
+        T w[N];
+        load_vline<T, N>(static_cast<const T*>(a.V) + ((size_t)l2 * N + l0 + c) * N, w);
+        V x[N];
+        const V* yl = Yw + (size_t)l2 * L + c;
+        PWK_SFOR(N, i, x[i] = Wn::in(i) ? yl[(size_t)Wn::idx(i) * yps] : V{T(0), T(0)});
+        LineFFTZ<T, N, +1, OutOfWin<N, W>>::run(x);
+        V y[N];
+        PWK_SFOR(N, l1, {
+          const V u = x[OutSlot<N, l1>::value];
+          y[l1] = V{u.x * w[l1], u.y * w[l1]};
+        });
+        LineFFT<T, N, -1>::run(y);
+        V* yo = Yw + (size_t)l2 * L + c;
+        PWK_SFOR(N, i, {
+          if constexpr (Wn::in(i)) yo[(size_t)Wn::idx(i) * yps] = y[OutSlot<N, i>::value];
+        });
+      }
+      __syncwarp();
+      // y forward, window outputs back to the stick square (this warp's columns only)
+      for (int t = lane; t < NW * lc; t += 32) {
+        const int c = t / NW, p = t - c * NW;
+        V x[N];
+        const V* yp = Yw + (size_t)p * yps + c;
+        PWK_SFOR(N, l2, x[l2] = yp[l2 * L]);
+        LineFFT<T, N, -1>::run(x);
+        V* zp = Z + (size_t)p * NW * zs + l0 + c;
+        PWK_SFOR(N, j, {
+          if constexpr (Wn::in(j)) zp[Wn::idx(j) * zs] = x[OutSlot<N, j>::value];
+        });
+      }
+      __syncwarp();
     }
     __syncthreads();
   }
@@ -183,7 +252,8 @@ int launch_window(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, 
   switch (N) {
 #define PWK_WCASE(n)                                                                            \
   case n: {                                                                                     \
-    auto kern = fused_window_kernel<T, TI, n, window_of(n)>;                                    \
+    auto kern = s.kind == 2 ? fused_window_kernel<T, TI, n, window_of(n), 1>                    \
+                            : fused_window_kernel<T, TI, n, window_of(n), 0>;                   \
     cudaError_t e = allow_full_smem(kern);                                                      \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(window)");                  \
     kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \

@@ -98,11 +98,11 @@ void window_strides(int N, int L, int* zs, int* yps) {
   *yps = y;
 }
 
-size_t window_smem_bytes(int N, int elem_bytes, int L, int nstick_max) {
+size_t window_smem_bytes(int N, int elem_bytes, int L, int nstick_max, int copies) {
   const int W = N / 4, NW = 2 * W + 1;
   int zs, yps;
   window_strides(N, L, &zs, &yps);
-  size_t elems = (size_t)NW * NW * zs + (size_t)NW * yps;
+  size_t elems = (size_t)NW * NW * zs + (size_t)copies * NW * yps;
   return elems * elem_bytes + (size_t)nstick_max * sizeof(short) + 16;
 }
 
@@ -307,7 +307,7 @@ LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int ctas_pe
 
 static int launch_variant(int precision, int N, const FusedArgs& a, int nblocks,
                           const LaunchShape& s, cudaStream_t st) {
-  if (s.kind == 1) {
+  if (s.kind >= 1) {
     switch (precision) {
       case PWK_FP64: return launch_window_f64(N, a, nblocks, s, st);
       case PWK_FP32: return launch_window_f32(N, a, nblocks, s, st);
@@ -323,7 +323,7 @@ static int launch_variant(int precision, int N, const FusedArgs& a, int nblocks,
 
 // Point the kernel arguments at the tables of the chosen kernel kind.
 static void use_kind(const pwk_plan* p, FusedArgs& a, int kind) {
-  if (kind == 1) {
+  if (kind >= 1) {
     a.gin = a.gout = p->d_wgmap;
     a.sid = p->d_wrows;
     window_strides(p->N, a.L, &a.zs, &a.yps);
@@ -346,16 +346,18 @@ int autotune_shape(pwk_plan* p, int precision) {
   const int io_elem = precision == PWK_FP32 ? 8 : 16;
   std::vector<LaunchShape> cands;
   const int Ls[4] = {N, (N + 1) / 2, (N + 2) / 3, (N + 3) / 4};
-  for (int kind = 0; kind < (p->window_ok ? 2 : 1); ++kind)
+  for (int kind = 0; kind < (p->window_ok ? 3 : 1); ++kind)
     for (int T : {96, 128, 192, 256})
       for (int li = 0; li < 4; ++li) {
-        const int L = Ls[li];
-        if (li > 0 && L == Ls[li - 1]) continue;
+        // kinds 0, 1: L planes per chunk of the CTA; kind 2: L = 1 or 2 planes per warp
+        const int L = kind == 2 ? li + 1 : Ls[li];
+        if (kind == 2 && L > 2) continue;
+        if (kind != 2 && li > 0 && L == Ls[li - 1]) continue;
         LaunchShape c;
         c.kind = kind;
         c.threads = T;
         c.L = L;
-        c.smem = kind == 1 ? window_smem_bytes(N, elem, L, p->self.nstick_max)
+        c.smem = kind >= 1 ? window_smem_bytes(N, elem, L, p->self.nstick_max, kind == 2 ? T / 32 : 1)
                            : fused_smem_bytes(N, elem, p->self.nstick_max, p->self.P, L, p->npw_max);
         if (c.smem <= 227 * 1024) cands.push_back(c);
       }
@@ -564,13 +566,13 @@ const char* pwk_strerror(int code) {
 size_t pwk_plan_device_bytes(const pwk_plan* p) { return p ? p->bytes : 0; }
 
 int pwk_plan_set_launch_shape(pwk_plan* p, int precision, int kind, int threads, int l3_chunk) {
-  if (p == nullptr || precision < 0 || precision > 2 || kind < 0 || kind > 1 ||
+  if (p == nullptr || precision < 0 || precision > 2 || kind < 0 || kind > 2 ||
       (threads != 96 && threads != 128 && threads != 192 && threads != 256) || l3_chunk < 1 ||
       l3_chunk > p->N) {
-    set_error("bad plan, precision, kind (0/1), threads (96/128/192/256) or l3 chunk (1..N)");
+    set_error("bad plan, precision, kind (0/1/2), threads (96/128/192/256) or l3 chunk (1..N)");
     return PWK_ERR_INVALID;
   }
-  if (kind == 1 && !p->window_ok) {
+  if (kind >= 1 && !p->window_ok) {
     set_error("the window kernel needs every |m_i| <= N/4");
     return PWK_ERR_UNSUPPORTED;
   }
@@ -579,7 +581,7 @@ int pwk_plan_set_launch_shape(pwk_plan* p, int precision, int kind, int threads,
   c.kind = kind;
   c.threads = threads;
   c.L = l3_chunk;
-  c.smem = kind == 1 ? window_smem_bytes(p->N, elem, l3_chunk, p->self.nstick_max)
+  c.smem = kind >= 1 ? window_smem_bytes(p->N, elem, l3_chunk, p->self.nstick_max, kind == 2 ? threads / 32 : 1)
                      : fused_smem_bytes(p->N, elem, p->self.nstick_max, p->self.P, l3_chunk, p->npw_max);
   if (c.smem > 227 * 1024) {
     set_error("shape needs more than 227 KB of shared memory");

@@ -49,7 +49,8 @@ struct SphereMap {
 
 // Launch shape of the fused kernel for one precision.
 struct LaunchShape {
-  int kind = 0;         // 0: generic fused kernel, 1: window-specialised kernel
+  int kind = 0;         // 0: generic fused kernel, 1: window kernel, CTA-wide plane chunks,
+                        // 2: window kernel, L planes per warp
   int threads = 256;
   int L = 0;            // l3 planes per chunk of the y/x passes
   size_t smem = 0;
@@ -164,7 +165,8 @@ int launch_window_f64(int N, const FusedArgs& a, int nblocks, const LaunchShape&
 int launch_window_f32(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
 int launch_window_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchShape& s,
                           cudaStream_t st);
-size_t window_smem_bytes(int N, int elem_bytes, int L, int nstick_max);
+// copies: plane buffers (1 for a CTA-wide chunk, the warp count for per-warp planes)
+size_t window_smem_bytes(int N, int elem_bytes, int L, int nstick_max, int copies);
 // strides of the window kernel's shared buffers for chunk L (bank-conflict-free y/x passes)
 void window_strides(int N, int L, int* zs, int* yps);
 
