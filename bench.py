@@ -130,15 +130,19 @@ def nonlocal_bytes_per_band(prob, elem_bytes: int) -> float:
     return 3.0 * npw * elem_bytes + 2.0 * prob.nkb * npw * elem_bytes / prob.nb
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the kernel, from the ncu
-# capture summarised in profiles/ (None once the kernel has changed since the capture)
-TRAFFIC = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per launch (bytes) of the kernel, from the
+# ncu capture summarised in profiles/fused_window_kernel_hpsi_cfg2_fp32.md (48.4 MB read +
+# 6.6 MB written); to be removed once the kernel changes after that capture
+TRAFFIC = {"fused_window_kernel<float,float,24,6>": 55.0e6}
 
 
 def kernel_name(N: int, shape) -> str:
     """Name of the H|psi> kernel the plan launches for a (kind, threads, L, smem) shape."""
-    return (f"fused_window_kernel<float,float,{N},{N // 4}>" if shape[0] == 1
-            else f"fused_kernel<float,float,{N},false>")
+    if shape[0] == 1:
+        return f"fused_window_kernel<float,float,{N},{N // 4}>"
+    if shape[0] == 2:
+        return f"fused_window_kernel<float,float,{N},{N // 4}> (per-warp planes)"
+    return f"fused_kernel<float,float,{N},false>"
 
 
 def stick_stats(prob):
