@@ -167,7 +167,7 @@ int pwk_hspsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, 
  *   mode     PWK_FP64: every H application in FP64.
  *            PWK_FP32_C128: expansion steps use FP32 H applications until the eigenvalue
  *            changes fall below max(eth, 1e-4 Ry) and the residuals below
- *            max(res_tol, 1e-3) (the FP32 noise floor), or for at most max_iter/2
+ *            max(res_tol, 1e-3) (the FP32 noise floor), or for at most min(max_iter/2, 60)
  *            iterations; then the Ritz vectors get FP64 H applications and the iteration
  *            continues in FP64 to eth and res_tol (FP64 refinement).
  *            Reduced matrices, the eigensolve, norms and residuals are FP64 in both modes.

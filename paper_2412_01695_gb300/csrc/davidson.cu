@@ -26,6 +26,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fft_line.cuh"
 #include "solvers.h"
 
 namespace pwk {
@@ -38,6 +39,11 @@ struct DavWork {
   double* sdiag = nullptr;
   unsigned char* drop = nullptr;   // [nk][MB] basis vectors the last eigensolve left out
   int* lastrow = nullptr;          // [nk][nb] basis row of each band's latest correction
+  // mixed mode: FP32 basis of the phase-1 k-points (same layouts as the FP64 arrays)
+  bool mixed = false;
+  float2 *phi32 = nullptr, *hphi32 = nullptr, *sphi32 = nullptr, *corr32 = nullptr;
+  float2 *t32a = nullptr, *t32b = nullptr, *t32c = nullptr;
+  float *hdiag32 = nullptr, *sdiag32 = nullptr;
   double2 *Hr = nullptr, *Sr = nullptr, *W = nullptr, *ev = nullptr;
   double *eps = nullptr, *eps_new = nullptr, *hdiag = nullptr, *rnorm = nullptr;
   int *nbase = nullptr, *nnc = nullptr, *todo = nullptr, *active = nullptr, *moved = nullptr;
@@ -61,9 +67,11 @@ static int dalloc(pwk_plan* p, DavWork* w, T** ptr, size_t n) {
   return rc;
 }
 
-static int ensure_dav_work(pwk_plan* p, int nb, int MB) {
+static int ensure_dav_work(pwk_plan* p, int nb, int MB, bool mixed) {
   const bool with_s = p->d_q != nullptr;
-  if (p->dav && p->dav->nb == nb && p->dav->MB == MB && p->dav->with_s == with_s) return PWK_OK;
+  if (p->dav && p->dav->nb == nb && p->dav->MB == MB && p->dav->with_s == with_s &&
+      p->dav->mixed == mixed)
+    return PWK_OK;
   destroy_dav_work(p);
   DavWork* w = new DavWork();
   p->dav = w;
@@ -72,8 +80,20 @@ static int ensure_dav_work(pwk_plan* p, int nb, int MB) {
   w->MB = MB;
   w->npw_max = p->npw_max;
   w->with_s = with_s;
+  w->mixed = mixed;
   const size_t nk = p->nk, np = p->npw_max;
   int rc;
+  if (mixed && ((rc = dalloc(p, w, &w->phi32, nk * MB * np)) || (rc = dalloc(p, w, &w->hphi32, nk * MB * np)) ||
+                (rc = dalloc(p, w, &w->corr32, nk * nb * np)) || (rc = dalloc(p, w, &w->t32a, nk * nb * np)) ||
+                (rc = dalloc(p, w, &w->t32b, nk * nb * np)) || (rc = dalloc(p, w, &w->hdiag32, nk * np)))) {
+    destroy_dav_work(p);
+    return rc;
+  }
+  if (mixed && with_s && ((rc = dalloc(p, w, &w->sphi32, nk * MB * np)) || (rc = dalloc(p, w, &w->t32c, nk * nb * np)) ||
+                          (rc = dalloc(p, w, &w->sdiag32, nk * np)))) {
+    destroy_dav_work(p);
+    return rc;
+  }
   if (with_s && ((rc = dalloc(p, w, &w->sphi, nk * MB * np)) || (rc = dalloc(p, w, &w->tmp3, nk * nb * np)) ||
                  (rc = dalloc(p, w, &w->sdiag, nk * np)))) {
     destroy_dav_work(p);
@@ -102,20 +122,27 @@ static int ensure_dav_work(pwk_plan* p, int nb, int MB) {
 }
 
 // ------------------------------------------------------------------ kernels
-__device__ __forceinline__ double2 cmul_(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+template <typename V>
+__device__ __forceinline__ V cmul_(V a, V b) {
+  return V{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
-__device__ __forceinline__ double2 cmulc_(double2 a, double2 b) {  // conj(a) b
-  return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+template <typename V>
+__device__ __forceinline__ V cmulc_(V a, V b) {  // conj(a) b
+  return V{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x};
+}
+// true when k-point k takes part in a launch restricted to phase `want` (0: any phase)
+__device__ __forceinline__ bool in_phase(const int* phase, int want, int k) {
+  return want == 0 || phase[k] == want;
 }
 
-__device__ double bsum(double v, double* red) {
+template <typename T>
+__device__ T bsum(T v, T* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   __syncthreads();
   if (l == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
+  T s = T(0);
   for (int i = 0; i < nw; ++i) s += red[i];
   __syncthreads();
   return s;
@@ -152,15 +179,16 @@ __global__ void hdiag_kernel(int nk, int np, int nkb, const int* npw, const doub
   if (sd != nullptr) sd[i] = so;
 }
 
-// copy nv vectors per k between arrays with different per-k strides
-__global__ void copy_vecs_kernel(int nk, int nv, int np, const double2* src, int src_nvec,
-                                 int src_off, double2* dst, int dst_nvec, int dst_off,
-                                 const int* only) {
+// copy nv vectors per k between arrays with different per-k strides (and precisions)
+template <typename TS, typename TD>
+__global__ void copy_vecs_kernel(int nk, int nv, int np, const c2_t<TS>* src, int src_nvec,
+                                 int src_off, c2_t<TD>* dst, int dst_nvec, int dst_off,
+                                 const int* only, const int* phase, int want) {
   const int k = blockIdx.x / nv, j = blockIdx.x % nv;
-  if (only != nullptr && !only[k]) return;
-  const double2* s = src + ((size_t)k * src_nvec + src_off + j) * np;
-  double2* d = dst + ((size_t)k * dst_nvec + dst_off + j) * np;
-  for (int g = threadIdx.x; g < np; g += blockDim.x) d[g] = s[g];
+  if ((only != nullptr && !only[k]) || !in_phase(phase, want, k)) return;
+  const c2_t<TS>* s = src + ((size_t)k * src_nvec + src_off + j) * np;
+  c2_t<TD>* d = dst + ((size_t)k * dst_nvec + dst_off + j) * np;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) d[g] = c2_t<TD>{TD(s[g].x), TD(s[g].y)};
 }
 
 // work list: (k, base[k] + t) for t < cnt[k] on k with mask[k] (and phase[k] == want_phase
@@ -179,25 +207,48 @@ __global__ void items_kernel(int nk, int nb, const int* active, const int* base,
   items[3 * i + 2] = on ? b + t : 0;
 }
 
+// Compensated FP32 accumulation of products (hi + lo): a*b is split exactly into its rounded
+// value and the FMA residual, and the running sum by a two-sum, so the pair carries about
+// twice the FP32 precision.
+struct CompSum {
+  float hi = 0.f, lo = 0.f;
+  // (round-to-nearest intrinsics: the compiler may not contract or reorder these steps)
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = fmaf(a, b, -p);   // exact: a * b = p + pe
+    const float s = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));   // hi + p = s + e
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
 // New columns b = base + t (t < cnt) of H~ and S~: rows a < base + cnt.  Each (a, b) is
 // written by one CTA (rows a >= base only for a <= b) together with its mirror (b, a).
-// S~_ab = <phi_a|S phi_b> with sphi = S phi (sphi = phi when S = 1).
+// S~_ab = <phi_a|S phi_b> with sphi = S phi (sphi = phi when S = 1).  T is the precision of
+// the stored vectors and of the sums (FP32 for phase-1 k-points of the mixed mode); the
+// reduced matrices are FP64.
+template <typename T>
 __global__ void __launch_bounds__(256) gram_kernel(int nb, int MB, int np, const int* npw,
                                                    const int* active, const int* base,
                                                    int base_const, const int* cnt, int cnt_const,
-                                                   const double2* phi, const double2* hphi,
-                                                   const double2* sphi, double2* Hr, double2* Sr) {
+                                                   const c2_t<T>* phi, const c2_t<T>* hphi,
+                                                   const c2_t<T>* sphi, double2* Hr, double2* Sr,
+                                                   const int* phase, int want) {
+  using V = c2_t<T>;
   const int k = blockIdx.x / nb, t = blockIdx.x % nb;
-  if (!active[k]) return;
+  if (!active[k] || !in_phase(phase, want, k)) return;
   const int b0 = base ? base[k] : base_const, c = cnt ? cnt[k] : cnt_const;
   if (t >= c) return;
   const int b = b0 + t, nrow = b0 + c, n = npw[k];
-  extern __shared__ double2 sh[];
-  double2* pb = sh;
-  double2* hb = sh + np;
-  const double2* P = phi + (size_t)k * MB * np;
-  const double2* HP = hphi + (size_t)k * MB * np;
-  const double2* SP = sphi + (size_t)k * MB * np;
+  extern __shared__ __align__(16) unsigned char gsh[];
+  V* pb = reinterpret_cast<V*>(gsh);
+  V* hb = pb + np;
+  const V* P = phi + (size_t)k * MB * np;
+  const V* HP = hphi + (size_t)k * MB * np;
+  const V* SP = sphi + (size_t)k * MB * np;
   for (int g = threadIdx.x; g < n; g += blockDim.x) {
     pb[g] = SP[(size_t)b * np + g];
     hb[g] = HP[(size_t)b * np + g];
@@ -208,16 +259,38 @@ __global__ void __launch_bounds__(256) gram_kernel(int nb, int MB, int np, const
   double2* S = Sr + (size_t)k * MB * MB;
   for (int a = warp; a < nrow; a += nw) {
     if (a >= b0 && a > b) continue;
-    const double2* pa = P + (size_t)a * np;
+    const V* pa = P + (size_t)a * np;
     double hx = 0, hy = 0, sx = 0, sy = 0;
-    for (int g = lane; g < n; g += 32) {
-      const double2 x = pa[g];
-      const double2 h = cmulc_(x, hb[g]);
-      const double2 s = cmulc_(x, pb[g]);
-      hx += h.x;
-      hy += h.y;
-      sx += s.x;
-      sy += s.y;
+    if constexpr (sizeof(T) == 8) {
+      for (int g = lane; g < n; g += 32) {
+        const V x = pa[g];
+        const V h = cmulc_(x, hb[g]);
+        const V s = cmulc_(x, pb[g]);
+        hx += h.x;
+        hy += h.y;
+        sx += s.x;
+        sy += s.y;
+      }
+    } else {
+      // FP32 vectors: products and sums carried as unevaluated pairs hi + lo (error-free
+      // product by FMA, two-sum), so S~ and H~ are those of the stored vectors to about
+      // 1e-14 while the arithmetic stays on the FP32 pipe
+      CompSum ah, bh, as, bs;
+      for (int g = lane; g < n; g += 32) {
+        const V x = pa[g], y = hb[g], z = pb[g];
+        ah.add_prod(x.x, y.x);
+        ah.add_prod(x.y, y.y);   // Re conj(x) y
+        bh.add_prod(x.x, y.y);
+        bh.add_prod(-x.y, y.x);  // Im conj(x) y
+        as.add_prod(x.x, z.x);
+        as.add_prod(x.y, z.y);
+        bs.add_prod(x.x, z.y);
+        bs.add_prod(-x.y, z.x);
+      }
+      hx = ah.value();
+      hy = bh.value();
+      sx = as.value();
+      sy = bs.value();
     }
     for (int o = 16; o > 0; o >>= 1) {
       hx += __shfl_xor_sync(0xffffffffu, hx, o);
@@ -239,27 +312,33 @@ __global__ void __launch_bounds__(256) gram_kernel(int nb, int MB, int np, const
   }
 }
 
-// out[k][j] = sum_{i < nbase} ev[k][i][j] in[k][i]   (j < nb), for k with only[k] != 0
+// out[k][j] = sum_{i < nbase} ev[k][i][j] in[k][i]   (j < nb), for k with only[k] != 0;
+// arithmetic in the input precision TI, output converted to TO
+template <typename TI, typename TO>
 __global__ void __launch_bounds__(256) rotate_kernel(int nb, int MB, int np, const int* nbase,
                                                      const int* only, const double2* ev,
-                                                     const double2* in, double2* out,
-                                                     int out_nvec) {
+                                                     const c2_t<TI>* in, c2_t<TO>* out,
+                                                     int out_nvec, const int* phase, int want) {
+  using V = c2_t<TI>;
   const int k = blockIdx.x / nb, j = blockIdx.x % nb;
-  if (only != nullptr && !only[k]) return;
+  if ((only != nullptr && !only[k]) || !in_phase(phase, want, k)) return;
   const int n = nbase[k];
-  __shared__ double2 c[kMaxBasis];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) c[i] = ev[((size_t)k * MB + i) * nb + j];
+  __shared__ V c[kMaxBasis];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 e = ev[((size_t)k * MB + i) * nb + j];
+    c[i] = V{TI(e.x), TI(e.y)};
+  }
   __syncthreads();
-  const double2* X = in + (size_t)k * MB * np;
-  double2* o = out + ((size_t)k * out_nvec + j) * np;
+  const V* X = in + (size_t)k * MB * np;
+  c2_t<TO>* o = out + ((size_t)k * out_nvec + j) * np;
   for (int g = threadIdx.x; g < np; g += blockDim.x) {
-    double sx = 0, sy = 0;
+    TI sx = 0, sy = 0;
     for (int i = 0; i < n; ++i) {
-      const double2 t = cmul_(c[i], X[(size_t)i * np + g]);
+      const V t = cmul_(c[i], X[(size_t)i * np + g]);
       sx += t.x;
       sy += t.y;
     }
-    o[g] = make_double2(sx, sy);
+    o[g] = c2_t<TO>{TO(sx), TO(sy)};
   }
 }
 
@@ -269,54 +348,59 @@ __global__ void __launch_bounds__(256) rotate_kernel(int nb, int MB, int np, con
 // direction whenever it is not zero) is used instead when c is numerically parallel to the
 // Ritz vector (|cos| > 1 - 1e-6: H diagonal in plane waves, exact preconditioner) or when the
 // band's previous correction was left out of the reduced problem as dependent on the basis.
-// sphi = phi and sdiag = null when S = 1.
+// sphi = phi and sdiag = null when S = 1.  T: precision of the vectors and the arithmetic.
+template <typename T>
 __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, const int* npw,
                                                     const int* nbase, const int* active,
                                                     const int* moved, int all_bands,
                                                     const double2* ev, const double* eps,
-                                                    const double2* phi, const double2* hphi,
-                                                    const double2* sphi, const double* hdiag,
-                                                    const double* sdiag, const unsigned char* drop,
-                                                    const int* lastrow, double2* corr,
-                                                    double* rnorm) {
+                                                    const c2_t<T>* phi, const c2_t<T>* hphi,
+                                                    const c2_t<T>* sphi, const T* hdiag,
+                                                    const T* sdiag, const unsigned char* drop,
+                                                    const int* lastrow, c2_t<T>* corr,
+                                                    double* rnorm, const int* phase, int want) {
+  using V = c2_t<T>;
   const int k = blockIdx.x / nb, i = blockIdx.x % nb;
-  if (!active[k]) return;
+  if (!active[k] || !in_phase(phase, want, k)) return;
   if (!all_bands && !moved[k * nb + i]) return;
   const int n = nbase[k], npk = npw[k];
-  __shared__ double2 c[kMaxBasis];
-  __shared__ double red[32];
-  for (int j = threadIdx.x; j < n; j += blockDim.x) c[j] = ev[((size_t)k * MB + j) * nb + i];
+  __shared__ V c[kMaxBasis];
+  __shared__ T red[32];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const double2 e = ev[((size_t)k * MB + j) * nb + i];
+    c[j] = V{T(e.x), T(e.y)};
+  }
   __syncthreads();
-  const double e = eps[k * nb + i];
-  const double2* P = phi + (size_t)k * MB * np;
-  const double2* HP = hphi + (size_t)k * MB * np;
-  const double2* SP = sphi + (size_t)k * MB * np;
-  double2* out = corr + ((size_t)k * nb + i) * np;
-  const double* hd = hdiag + (size_t)k * np;
-  const double* sdk = sdiag != nullptr ? sdiag + (size_t)k * np : nullptr;
-  double rr = 0.0, cc = 0.0, zz = 0.0, zcx = 0.0, zcy = 0.0;
+  const T e = T(eps[k * nb + i]);
+  const V* P = phi + (size_t)k * MB * np;
+  const V* HP = hphi + (size_t)k * MB * np;
+  const V* SP = sphi + (size_t)k * MB * np;
+  V* out = corr + ((size_t)k * nb + i) * np;
+  const T* hd = hdiag + (size_t)k * np;
+  const T* sdk = sdiag != nullptr ? sdiag + (size_t)k * np : nullptr;
+  T rr = 0, cc = 0, zz = 0, zcx = 0, zcy = 0;
   for (int g = threadIdx.x; g < npk; g += blockDim.x) {
-    double rx = 0, ry = 0, zx = 0, zy = 0;
+    T rx = 0, ry = 0, zx = 0, zy = 0;
     for (int j = 0; j < n; ++j) {
-      const double2 hp = HP[(size_t)j * np + g], p = P[(size_t)j * np + g], sp = SP[(size_t)j * np + g];
-      const double2 d = make_double2(hp.x - e * sp.x, hp.y - e * sp.y);
-      const double2 t = cmul_(c[j], d);
-      const double2 z = cmul_(c[j], p);
+      const V hp = HP[(size_t)j * np + g], p = P[(size_t)j * np + g], sp = SP[(size_t)j * np + g];
+      const V d = V{hp.x - e * sp.x, hp.y - e * sp.y};
+      const V t = cmul_(c[j], d);
+      const V z = cmul_(c[j], p);
       rx += t.x;
       ry += t.y;
       zx += z.x;
       zy += z.y;
     }
     rr += rx * rx + ry * ry;
-    double x = hd[g] - e * (sdk != nullptr ? sdk[g] : 1.0);
-    const double s = x >= 0.0 ? 1.0 : -1.0;
-    x = s * fmax(fabs(x), 1e-2);
-    const double2 v = make_double2(rx / x, ry / x);
+    T x = hd[g] - e * (sdk != nullptr ? sdk[g] : T(1));
+    const T s = x >= T(0) ? T(1) : T(-1);
+    x = s * fmax(fabs(x), T(1e-2));
+    const V v = V{rx / x, ry / x};
     cc += v.x * v.x + v.y * v.y;
     zz += zx * zx + zy * zy;
     zcx += zx * v.x + zy * v.y;   // <ritz|v>
     zcy += zx * v.y - zy * v.x;
-    out[g] = make_double2(rx, ry);
+    out[g] = V{rx, ry};
   }
   rr = bsum(rr, red);
   cc = bsum(cc, red);
@@ -325,24 +409,24 @@ __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, cons
   zcy = bsum(zcy, red);
   const int lr = lastrow[k * nb + i];
   const bool was_dropped = lr >= 0 && lr < n && drop[(size_t)k * MB + lr] != 0;
-  const bool parallel = was_dropped || (zcx * zcx + zcy * zcy) > (1.0 - 1e-6) * (1.0 - 1e-6) * zz * cc;
-  const double nrm2 = parallel ? rr : cc;
-  const double inv = nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0;
+  const bool parallel = was_dropped || (zcx * zcx + zcy * zcy) > T(1.0 - 1e-6) * T(1.0 - 1e-6) * zz * cc;
+  const T nrm2 = parallel ? rr : cc;
+  const T inv = nrm2 > T(0) ? T(1) / sqrt(nrm2) : T(0);
   for (int g = threadIdx.x; g < np; g += blockDim.x) {
     if (g < npk) {
-      const double2 r = out[g];
-      double sc = inv;
+      const V r = out[g];
+      T sc = inv;
       if (!parallel) {
-        double x = hd[g] - e * (sdk != nullptr ? sdk[g] : 1.0);
-        const double s = x >= 0.0 ? 1.0 : -1.0;
-        sc = inv / (s * fmax(fabs(x), 1e-2));
+        T x = hd[g] - e * (sdk != nullptr ? sdk[g] : T(1));
+        const T s = x >= T(0) ? T(1) : T(-1);
+        sc = inv / (s * fmax(fabs(x), T(1e-2)));
       }
-      out[g] = make_double2(r.x * sc, r.y * sc);
+      out[g] = V{r.x * sc, r.y * sc};
     } else {
-      out[g] = make_double2(0.0, 0.0);
+      out[g] = V{T(0), T(0)};
     }
   }
-  if (threadIdx.x == 0) rnorm[k * nb + i] = sqrt(rr);
+  if (threadIdx.x == 0) rnorm[k * nb + i] = sqrt((double)rr);
 }
 
 // Which bands still need a correction, per k-point and its phase (1: FP32 H, 2: FP64 H).
@@ -403,16 +487,23 @@ __global__ void set_value_kernel(int nk, const int* mask, int* a, int v) {
   if (k < nk && mask[k]) a[k] = v;
 }
 
+template <typename T>
 __global__ void append_kernel(int nb, int MB, int np, const int* active, const int* nbase,
-                              const int* nnc, const int* todo, const double2* corr, double2* phi,
-                              int* lastrow) {
+                              const int* nnc, const int* todo, const c2_t<T>* corr, c2_t<T>* phi,
+                              int* lastrow, const int* phase, int want) {
   const int k = blockIdx.x / nb, t = blockIdx.x % nb;
-  if (!active[k] || t >= nnc[k]) return;
+  if (!active[k] || t >= nnc[k] || !in_phase(phase, want, k)) return;
   const int i = todo[k * nb + t];
   if (threadIdx.x == 0) lastrow[k * nb + i] = nbase[k] + t;
-  const double2* s = corr + ((size_t)k * nb + i) * np;
-  double2* d = phi + ((size_t)k * MB + nbase[k] + t) * np;
+  const c2_t<T>* s = corr + ((size_t)k * nb + i) * np;
+  c2_t<T>* d = phi + ((size_t)k * MB + nbase[k] + t) * np;
   for (int g = threadIdx.x; g < np; g += blockDim.x) d[g] = s[g];
+}
+
+// FP32 copies of the plane-wave diagonals of H and S for the phase-1 arithmetic
+__global__ void to_float_kernel(size_t n, const double* a, float* b) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
 }
 
 __global__ void set_nbase_kernel(int nk, const int* only, int* nbase, int value, const int* add) {
@@ -554,7 +645,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       return PWK_ERR_INVALID;
     }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  int rc = ensure_dav_work(p, nb, MB);
+  int rc = ensure_dav_work(p, nb, MB, mode == PWK_FP32_C128);
   if (rc) return rc;
   DavWork* w = p->dav;
   const int nk = p->nk, np = p->npw_max;
@@ -564,16 +655,26 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
     set_error("npw_max too large for the Gram kernel (2 vectors in shared memory)");
     return PWK_ERR_UNSUPPORTED;
   }
-  if (cudaError_t e = allow_full_smem(gram_kernel); e != cudaSuccess)
+  if (cudaError_t e = allow_full_smem(gram_kernel<double>); e != cudaSuccess)
+    return cuda_fail(e, "cudaFuncSetAttribute(gram)");
+  if (cudaError_t e = allow_full_smem(gram_kernel<float>); e != cudaSuccess)
     return cuda_fail(e, "cudaFuncSetAttribute(gram)");
   long long napply[2] = {0, 0};
   int total = 0, given_up = 0, host_dbg[4] = {0, 0, 0, 0};
   bool dumped = false;
+  const bool mixed = w->mixed;
+  // phase filters of the FP64 launches: every k in FP64 mode, the phase-2 k in mixed mode
+  const int want64 = mixed ? 2 : 0;
 
-  double2* const sphi = w->with_s ? w->sphi : w->phi;   // S phi (S = 1: phi itself)
+  double2* const sphi = w->with_s ? w->sphi : w->phi;       // S phi (S = 1: phi itself)
+  float2* const sphi32 = w->with_s ? w->sphi32 : w->phi32;
   hdiag_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>(nk, np, p->nkb, p->d_npw, p->d_g2, p->v_mean,
                                                         p->d_beta, p->d_D, w->hdiag, p->d_q,
                                                         w->with_s ? w->sdiag : nullptr);
+  if (mixed) {
+    to_float_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>((size_t)nk * np, w->hdiag, w->hdiag32);
+    if (w->with_s) to_float_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>((size_t)nk * np, w->sdiag, w->sdiag32);
+  }
   KCHECK("hdiag_kernel");
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, 1);
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iters, 0);
@@ -583,40 +684,63 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->failcount, 0);
   fill_int_kernel<<<1, 32, 0, st>>>(4, w->dbg, 0);
   fill_int_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk * nb, w->lastrow, -1);
-  copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi, MB, 0, nullptr);
+  if (mixed)
+    copy_vecs_kernel<double, float><<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi32, MB, 0, nullptr,
+                                                             nullptr, 0);
+  else
+    copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi, MB, 0, nullptr,
+                                                              nullptr, 0);
   KCHECK("davidson init");
 
   // Phase 1 (mixed mode) stops at the FP32 noise floor: eigenvalues of the reduced problem
   // built from FP32 H applications move by ~1e-6 |H| between iterations and residuals bottom
   // out near 1e-5, so a k-point leaves phase 1 when its bands stop moving by 1e-4 Ry with
-  // ||r|| < 1e-3, or after max_iter/2 correction steps; it then restarts from its Ritz
+  // ||r|| < 1e-3, or after min(max_iter/2, 60) correction steps; it then restarts from its Ritz
   // vectors with FP64 H applications (phase 2) and goes on to eth and res_tol.  Each k-point
-  // switches on its own: the others keep iterating in their phase.
+  // switches on its own: the others keep iterating in their phase.  Phase-1 k-points keep
+  // their basis, H basis and corrections in FP32 and do the vector arithmetic (corrections,
+  // reduced-matrix columns, rotations) in FP32; the reduced matrices and their eigensolve
+  // are FP64 in both phases.
   const double eth1 = mode == PWK_FP32_C128 ? std::max(eth, 1e-4) : eth;
   const double rt1 = mode == PWK_FP32_C128 && res_tol > 0 ? std::max(res_tol, 1e-3) : res_tol;
-  const int cap1 = std::max(1, max_iter / 2);
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->phase, mode == PWK_FP32_C128 ? 1 : 2);
+  // a k-point still short of the FP32 floor after 60 correction steps (a slow band next to a
+  // small gap) finishes in FP64 instead of spending the rest of max_iter in FP32
+  const int cap1 = std::max(1, std::min(max_iter / 2, 60));
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->phase, mixed ? 1 : 2);
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->switchk, 0);
   fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, 0);
 
-  // H on phi[0:nb] of the k-points in mask, their nb x nb reduced matrices and eigensolve
-  auto start_block = [&](int prec, int* mask, int count) -> int {
+  // new columns of H~, S~ for the k-points in mask, in the precision of their phase
+  auto gram = [&](const int* mask, const int* base, int base_const, const int* cnt, int cnt_const) {
+    if (mixed)
+      gram_kernel<float><<<nk * nb, 256, gram_smem / 2, st>>>(nb, MB, np, p->d_npw, mask, base, base_const, cnt,
+                                                             cnt_const, w->phi32, w->hphi32, sphi32, w->Hr,
+                                                             w->Sr, w->phase, 1);
+    gram_kernel<double><<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, mask, base, base_const, cnt,
+                                                         cnt_const, w->phi, w->hphi, sphi, w->Hr, w->Sr,
+                                                         w->phase, want64);
+  };
+
+  // H on phi[0:nb] of the k-points in mask (all in phase ph), their nb x nb reduced matrices
+  // and eigensolve
+  auto start_block = [&](int ph, int* mask, int count) -> int {
     items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, mask, nullptr, 0, nullptr, nb,
                                                           w->phase, 0, w->items);
     KCHECK("items_kernel");
-    int r = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st,
-                     w->with_s ? w->sphi : nullptr);
+    int r = ph == 1 ? run_hpsi(p, PWK_FP32, w->phi32, w->hphi32, w->items, nullptr, nk * nb, MB, MB, st,
+                               w->with_s ? w->sphi32 : nullptr)
+                    : run_hpsi(p, PWK_FP64, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st,
+                               w->with_s ? w->sphi : nullptr);
     if (r) return r;
-    napply[prec == PWK_FP64 ? 0 : 1] += (long long)count * nb;
-    gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, mask, nullptr, 0, nullptr, nb,
-                                                 w->phi, w->hphi, sphi, w->Hr, w->Sr);
+    napply[ph == 2 ? 0 : 1] += (long long)count * nb;
+    gram(mask, nullptr, 0, nullptr, nb);
     KCHECK("gram_kernel");
     set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, mask, w->nbase, nb, nullptr);
     return launch_rr(nk, MB, nb, w->nbase, mask, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st,
                      w->drop);
   };
 
-  if ((rc = start_block(mode == PWK_FP64 ? PWK_FP64 : PWK_FP32_C128, w->active, nk))) return rc;
+  if ((rc = start_block(mixed ? 1 : 2, w->active, nk))) return rc;
   update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->active, 1,
                                                          w->eps_new, w->eps, w->moved, w->status,
                                                          nullptr, w->nbase, w->force, w->failcount,
@@ -625,11 +749,17 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
 
   int it = 0;
   int hc[8];
+  const int allb = (rt1 > 0 || res_tol > 0) ? 1 : 0;
   for (;;) {
-    resid_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved,
-                                          (rt1 > 0 || res_tol > 0) ? 1 : 0, w->ev, w->eps, w->phi,
-                                          w->hphi, sphi, w->hdiag, w->with_s ? w->sdiag : nullptr,
-                                          w->drop, w->lastrow, w->corr, w->rnorm);
+    if (mixed)
+      resid_kernel<float><<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved, allb,
+                                                   w->ev, w->eps, w->phi32, w->hphi32, sphi32, w->hdiag32,
+                                                   w->with_s ? w->sdiag32 : nullptr, w->drop, w->lastrow,
+                                                   w->corr32, w->rnorm, w->phase, 1);
+    resid_kernel<double><<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved, allb,
+                                                  w->ev, w->eps, w->phi, w->hphi, sphi, w->hdiag,
+                                                  w->with_s ? w->sdiag : nullptr, w->drop, w->lastrow,
+                                                  w->corr, w->rnorm, w->phase, want64);
     KCHECK("resid_kernel");
     cudaMemsetAsync(w->counters, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(w->counters + 2, 0xff, sizeof(int), st);
@@ -660,12 +790,15 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
     if (total == 0 && nswitch == 0) break;
     if (++it > max_iter) break;
     if (nswitch > 0) {
-      // FP64 refinement start of the k-points leaving phase 1: Ritz vectors, FP64 H on them
-      rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->switchk, w->ev, w->phi, w->tmp1, nb);
-      copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, w->switchk);
+      // FP64 refinement start of the k-points leaving phase 1: their Ritz vectors from the
+      // FP32 basis, in FP64, then FP64 H on them
+      rotate_kernel<float, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->switchk, w->ev, w->phi32,
+                                                            w->tmp1, nb, nullptr, 0);
+      copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0,
+                                                                w->switchk, nullptr, 0);
       set_value_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->switchk, w->phase, 2);
       KCHECK("phase switch");
-      if ((rc = start_block(PWK_FP64, w->switchk, nswitch))) return rc;
+      if ((rc = start_block(2, w->switchk, nswitch))) return rc;
       update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->switchk, 0,
                                                              w->eps_new, w->eps, w->moved, w->status,
                                                              nullptr, w->nbase, w->force, w->failcount,
@@ -674,21 +807,45 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
     }
     if (total > 0) {
       // restart the k-points whose basis would overflow
-      rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->phi, w->tmp1, nb);
-      rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->hphi, w->tmp2, nb);
-      copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0, w->restart);
-      copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp2, nb, 0, w->hphi, MB, 0, w->restart);
-      if (w->with_s) {
-        rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->sphi, w->tmp3, nb);
-        copy_vecs_kernel<<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp3, nb, 0, w->sphi, MB, 0, w->restart);
+      if (mixed) {
+        rotate_kernel<float, float><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->phi32,
+                                                             w->t32a, nb, w->phase, 1);
+        rotate_kernel<float, float><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->hphi32,
+                                                             w->t32b, nb, w->phase, 1);
+        copy_vecs_kernel<float, float><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->t32a, nb, 0, w->phi32, MB, 0,
+                                                                w->restart, w->phase, 1);
+        copy_vecs_kernel<float, float><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->t32b, nb, 0, w->hphi32, MB, 0,
+                                                                w->restart, w->phase, 1);
+        if (w->with_s) {
+          rotate_kernel<float, float><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev,
+                                                               w->sphi32, w->t32c, nb, w->phase, 1);
+          copy_vecs_kernel<float, float><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->t32c, nb, 0, w->sphi32, MB, 0,
+                                                                  w->restart, w->phase, 1);
+        }
       }
-      gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->restart, nullptr, 0, nullptr,
-                                                   nb, w->phi, w->hphi, sphi, w->Hr, w->Sr);
+      rotate_kernel<double, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->phi,
+                                                             w->tmp1, nb, w->phase, want64);
+      rotate_kernel<double, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->hphi,
+                                                             w->tmp2, nb, w->phase, want64);
+      copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0,
+                                                                w->restart, w->phase, want64);
+      copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp2, nb, 0, w->hphi, MB, 0,
+                                                                w->restart, w->phase, want64);
+      if (w->with_s) {
+        rotate_kernel<double, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev,
+                                                               w->sphi, w->tmp3, nb, w->phase, want64);
+        copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp3, nb, 0, w->sphi, MB, 0,
+                                                                  w->restart, w->phase, want64);
+      }
+      gram(w->restart, nullptr, 0, nullptr, nb);
       set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, w->nbase, nb, nullptr);
       KCHECK("davidson restart");
       // append the corrections, apply H to them (FP32 for phase-1 k, FP64 for phase-2 k)
-      append_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->iterk, w->nbase, w->nnc, w->todo, w->corr, w->phi,
-                                             w->lastrow);
+      if (mixed)
+        append_kernel<float><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->iterk, w->nbase, w->nnc, w->todo,
+                                                      w->corr32, w->phi32, w->lastrow, w->phase, 1);
+      append_kernel<double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->iterk, w->nbase, w->nnc, w->todo, w->corr,
+                                                     w->phi, w->lastrow, w->phase, want64);
       KCHECK("davidson append");
       for (int ph = 1; ph <= 2; ++ph) {
         const int cnt = ph == 2 ? n64 : total - n64;
@@ -696,14 +853,18 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
         items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, w->iterk, w->nbase, 0, w->nnc, 0,
                                                               w->phase, ph, w->items);
         KCHECK("items_kernel");
-        const int prec = ph == 2 ? PWK_FP64 : PWK_FP32_C128;
-        if ((rc = run_hpsi(p, prec, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st,
-                           w->with_s ? w->sphi : nullptr)))
-          return rc;
+        if (ph == 1) {
+          if ((rc = run_hpsi(p, PWK_FP32, w->phi32, w->hphi32, w->items, nullptr, nk * nb, MB, MB, st,
+                             w->with_s ? w->sphi32 : nullptr)))
+            return rc;
+        } else {
+          if ((rc = run_hpsi(p, PWK_FP64, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st,
+                             w->with_s ? w->sphi : nullptr)))
+            return rc;
+        }
         napply[ph == 2 ? 0 : 1] += cnt;
       }
-      gram_kernel<<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, w->iterk, w->nbase, 0, w->nnc,
-                                                   0, w->phi, w->hphi, sphi, w->Hr, w->Sr);
+      gram(w->iterk, w->nbase, 0, w->nnc, 0);
       set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, w->nbase, 0, w->nnc);
       KCHECK("davidson gram");
       if ((rc = launch_rr(nk, MB, nb, w->nbase, w->iterk, w->Hr, w->Sr, w->W, w->ev, w->eps_new,
@@ -717,8 +878,13 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       KCHECK("update_kernel");
     }
   }
-  // eigenvectors out: psi = phi v; eigenvalues out
-  rotate_kernel<<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi, psi, nb);
+  // eigenvectors out: psi = phi v (from the FP32 basis for k-points still in phase 1);
+  // eigenvalues out
+  if (mixed)
+    rotate_kernel<float, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi32, psi,
+                                                          nb, w->phase, 1);
+  rotate_kernel<double, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi, psi, nb,
+                                                         w->phase, want64);
   KCHECK("final rotate");
   cudaError_t ce = cudaMemcpyAsync(eig, w->eps, sizeof(double) * nk * nb, cudaMemcpyDeviceToDevice, st);
   std::vector<int> h_iters(nk), h_nnc(nk);

@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
       __syncthreads();
       continue;
     }
-    const double piv = Lm[j * ld + j].x;
-    for (int r = j + 1 + tid; r < n; r += nth) Lm[r * ld + j] = make_double2(Lm[r * ld + j].x / piv, Lm[r * ld + j].y / piv);
+    const double ipiv = 1.0 / Lm[j * ld + j].x;
+    for (int r = j + 1 + tid; r < n; r += nth) Lm[r * ld + j] = make_double2(Lm[r * ld + j].x * ipiv, Lm[r * ld + j].y * ipiv);
     __syncthreads();
     // trailing update, lower triangle: L[r][c] -= L[r][j] conj(L[c][j]), c <= r
     const int m = n - j - 1;
@@ -121,7 +121,10 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     if (tid == 0 && status != nullptr) status[k] = PWK_ERR_NOT_POSDEF;
     return;
   }
-  // ---- 2. X = L^-1 H (column c per thread), then C = L^-1 X^H (column c per thread)
+  // ---- 2. X = L^-1 H (column c per thread), then C = L^-1 X^H (column c per thread); the
+  //      inverse diagonal of L is formed once (FP64 division is a long instruction sequence)
+  for (int r = tid; r < n; r += nth) rc[r] = 1.0 / Lm[r * ld + r].x;
+  __syncthreads();
   for (int c = tid; c < n; c += nth) {
     for (int r = 0; r < n; ++r) {
       double2 s = H[r * ld + c];
@@ -130,8 +133,8 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
         s.x -= t.x;
         s.y -= t.y;
       }
-      const double l = Lm[r * ld + r].x;
-      X[r * ld + c] = make_double2(s.x / l, s.y / l);
+      const double il = rc[r];
+      X[r * ld + c] = make_double2(s.x * il, s.y * il);
     }
   }
   __syncthreads();
@@ -143,8 +146,8 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
         s.x -= t.x;
         s.y -= t.y;
       }
-      const double l = Lm[r * ld + r].x;
-      C[r * ld + c] = make_double2(s.x / l, s.y / l);
+      const double il = rc[r];
+      C[r * ld + c] = make_double2(s.x * il, s.y * il);
     }
   }
   __syncthreads();
@@ -283,25 +286,52 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     tiny = 2.2e-16 * fmax(1.0, fmax(dmax, sqrt(emax)));
   }
   __syncthreads();
+  // multisection: P threads per eigenvalue evaluate the Sturm count at P interior points of
+  // its interval, which shrinks by P + 1 per round (bisection is P = 1); the same number of
+  // rounds for every eigenvalue (all start from the Gershgorin interval)
+  __shared__ double blo[kMaxBasis], bhi[kMaxBasis];
+  __shared__ unsigned char above[256];
+  const int P = max(1, min(16, nth / nb));
   for (int j = tid; j < nb; j += nth) {
-    // the j-th smallest eigenvalue: count(x) = number of eigenvalues below x (Sturm sequence
-    // of the LDL^T factorisation of T - x)
-    double a = glo, b = ghi;
-    for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (a + b);
-      if (mid <= a || mid >= b || b - a <= 4.4e-16 * fmax(fabs(a), fabs(b)) + 2.0 * pivmin) break;
-      double q = d[0] - mid;
-      int cnt = q < 0.0;
-      for (int i = 1; i < n; ++i) {
-        if (fabs(q) < pivmin) q = -pivmin;
-        q = d[i] - mid - e2[i - 1] / q;
-        cnt += q < 0.0;
-      }
-      if (cnt > j) b = mid;
-      else a = mid;
-    }
-    lam[j] = 0.5 * (a + b);
+    blo[j] = glo;
+    bhi[j] = ghi;
   }
+  int rounds;
+  {
+    const double width = ghi - glo, tol = 4.4e-16 * fmax(fabs(glo), fabs(ghi)) + 2.0 * pivmin;
+    rounds = (int)ceil(log(fmax(width / tol, 2.0)) / log((double)(P + 1))) + 1;
+    rounds = min(rounds, 200);
+  }
+  __syncthreads();
+  for (int round = 0; round < rounds; ++round) {
+    for (int slot = tid; slot < nb * P; slot += nth) {
+      const int j = slot / P, q = slot - j * P;
+      const double a = blo[j], b = bhi[j];
+      const double x = a + (b - a) * (double)(q + 1) / (double)(P + 1);
+      double dq = d[0] - x;
+      int cnt = dq < 0.0;
+      for (int i = 1; i < n; ++i) {
+        if (fabs(dq) < pivmin) dq = -pivmin;
+        dq = d[i] - x - e2[i - 1] / dq;
+        cnt += dq < 0.0;
+      }
+      above[slot] = cnt > j ? 1 : 0;   // x lies above the j-th eigenvalue
+    }
+    __syncthreads();
+    for (int j = tid; j < nb; j += nth) {
+      const double a = blo[j], b = bhi[j];
+      int f = P;
+      for (int q = 0; q < P; ++q)
+        if (above[j * P + q]) {
+          f = q;
+          break;
+        }
+      if (f > 0) blo[j] = a + (b - a) * (double)f / (double)(P + 1);
+      if (f < P) bhi[j] = a + (b - a) * (double)(f + 1) / (double)(P + 1);
+    }
+    __syncthreads();
+  }
+  for (int j = tid; j < nb; j += nth) lam[j] = 0.5 * (blo[j] + bhi[j]);
   __syncthreads();
   double* XS = reinterpret_cast<double*>(X);   // x_j at XS + j n, pivots of T - lam_j at XS + (nb + j) n
   // Clusters: consecutive eigenvalues closer than ortol = 1e-3 max(1, |lam|) (the reorthogonalisation
@@ -331,22 +361,25 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
       double lj = lam[j];
       if (j > cl_start[c] && lj < lprev + eps3) lj = lprev + eps3;
       lprev = lj;
+      // LDL^T of T - lj; Dv keeps 1/D (the solves below then multiply only)
       double D = d[0] - lj;
       if (fabs(D) < tiny) D = D < 0.0 ? -tiny : tiny;
-      Dv[0] = D;
+      double iD = 1.0 / D;
+      Dv[0] = iD;
       for (int i = 1; i < n; ++i) {
-        D = d[i] - lj - e2[i - 1] / Dv[i - 1];
+        D = d[i] - lj - e2[i - 1] * iD;
         if (fabs(D) < tiny) D = D < 0.0 ? -tiny : tiny;
-        Dv[i] = D;
+        iD = 1.0 / D;
+        Dv[i] = iD;
       }
       for (int i = 0; i < n; ++i) {   // start vector: a fixed pseudo-random pattern per (i, j)
         const unsigned h = (unsigned)(i + 1) * 2654435761u ^ (unsigned)(j + 1) * 2246822519u;
         x[i] = 0.5 + (double)(h >> 8) * (1.0 / 16777216.0);
       }
       for (int iter = 0; iter < 5; ++iter) {
-        for (int i = 1; i < n; ++i) x[i] -= (e[i - 1] / Dv[i - 1]) * x[i - 1];   // L y = b
-        x[n - 1] /= Dv[n - 1];                                                   // D z = y, L^T x = z
-        for (int i = n - 2; i >= 0; --i) x[i] = x[i] / Dv[i] - (e[i] / Dv[i]) * x[i + 1];
+        for (int i = 1; i < n; ++i) x[i] -= (e[i - 1] * Dv[i - 1]) * x[i - 1];   // L y = b
+        x[n - 1] *= Dv[n - 1];                                                   // D z = y, L^T x = z
+        for (int i = n - 2; i >= 0; --i) x[i] = (x[i] - e[i] * x[i + 1]) * Dv[i];
         for (int q = cl_start[c]; q < j; ++q) {   // modified Gram-Schmidt against the cluster
           const double* xq = XS + (size_t)q * n;
           double s2 = 0.0;
