@@ -286,52 +286,28 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     tiny = 2.2e-16 * fmax(1.0, fmax(dmax, sqrt(emax)));
   }
   __syncthreads();
-  // multisection: P threads per eigenvalue evaluate the Sturm count at P interior points of
-  // its interval, which shrinks by P + 1 per round (bisection is P = 1); the same number of
-  // rounds for every eigenvalue (all start from the Gershgorin interval)
-  __shared__ double blo[kMaxBasis], bhi[kMaxBasis];
-  __shared__ unsigned char above[256];
-  const int P = max(1, min(16, nth / nb));
+  // bisection, one thread per eigenvalue (threads of a warp in lockstep, so every FP64
+  // instruction serves up to 32 eigenvalues); FP64 throughput, not latency, bounds this
+  // kernel when the batch is full, so the Sturm counts are not multiplied across threads
   for (int j = tid; j < nb; j += nth) {
-    blo[j] = glo;
-    bhi[j] = ghi;
-  }
-  int rounds;
-  {
-    const double width = ghi - glo, tol = 4.4e-16 * fmax(fabs(glo), fabs(ghi)) + 2.0 * pivmin;
-    rounds = (int)ceil(log(fmax(width / tol, 2.0)) / log((double)(P + 1))) + 1;
-    rounds = min(rounds, 200);
-  }
-  __syncthreads();
-  for (int round = 0; round < rounds; ++round) {
-    for (int slot = tid; slot < nb * P; slot += nth) {
-      const int j = slot / P, q = slot - j * P;
-      const double a = blo[j], b = bhi[j];
-      const double x = a + (b - a) * (double)(q + 1) / (double)(P + 1);
-      double dq = d[0] - x;
-      int cnt = dq < 0.0;
+    // the j-th smallest eigenvalue: count(x) = number of eigenvalues below x (Sturm sequence
+    // of the LDL^T factorisation of T - x)
+    double a = glo, b = ghi;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (a + b);
+      if (mid <= a || mid >= b || b - a <= 4.4e-16 * fmax(fabs(a), fabs(b)) + 2.0 * pivmin) break;
+      double q = d[0] - mid;
+      int cnt = q < 0.0;
       for (int i = 1; i < n; ++i) {
-        if (fabs(dq) < pivmin) dq = -pivmin;
-        dq = d[i] - x - e2[i - 1] / dq;
-        cnt += dq < 0.0;
+        if (fabs(q) < pivmin) q = -pivmin;
+        q = d[i] - mid - e2[i - 1] / q;
+        cnt += q < 0.0;
       }
-      above[slot] = cnt > j ? 1 : 0;   // x lies above the j-th eigenvalue
+      if (cnt > j) b = mid;
+      else a = mid;
     }
-    __syncthreads();
-    for (int j = tid; j < nb; j += nth) {
-      const double a = blo[j], b = bhi[j];
-      int f = P;
-      for (int q = 0; q < P; ++q)
-        if (above[j * P + q]) {
-          f = q;
-          break;
-        }
-      if (f > 0) blo[j] = a + (b - a) * (double)f / (double)(P + 1);
-      if (f < P) bhi[j] = a + (b - a) * (double)(f + 1) / (double)(P + 1);
-    }
-    __syncthreads();
+    lam[j] = 0.5 * (a + b);
   }
-  for (int j = tid; j < nb; j += nth) lam[j] = 0.5 * (blo[j] + bhi[j]);
   __syncthreads();
   double* XS = reinterpret_cast<double*>(X);   // x_j at XS + j n, pivots of T - lam_j at XS + (nb + j) n
   // Clusters: consecutive eigenvalues closer than ortol = 1e-3 max(1, |lam|) (the reorthogonalisation
