@@ -3,16 +3,22 @@
 //
 // The paper runs LAPACK ZHEGV(X) converted to device routines, one thread per k, with a
 // non-recursive Cholesky (ZPOTRF2 rewritten).  Here a whole CTA works on one k:
-//   1. Cholesky S~ = L L^H (right-looking, column by column);
-//   2. C = L^-1 H~ L^-H by two triangular solves (one thread per right-hand side);
+//   1. Cholesky S~ = L L^H (right-looking, column by column, lower triangle only);
+//   2. C = L^-1 H~ L^-H: X = L^-1 H~ by forward substitution (one thread per column), then
+//      the lower triangle of C = X L^-H by row-wise substitution (one thread per row);
 //   3. Householder reduction of C to a real symmetric tridiagonal T = Q^H C Q
-//      (reflectors H = I - tau v v^H, beta real, two-sided rank-2 updates);
+//      (reflectors H = I - tau v v^H, beta real, two-sided rank-2 updates of the lower
+//      triangle);
 //   4. the nb lowest eigenvalues of T by bisection on Sturm counts and their eigenvectors by
 //      inverse iteration on T (one thread per cluster of close eigenvalues, clusters in
 //      parallel; the members of a cluster reorthogonalised inside the iteration);
 //   5. back-transform x = L^-H Q z (reflectors applied in reverse order, then back
 //      substitution).
 // All matrices live in a per-k global workspace (L2-resident while the CTA works on it).
+// The kernel is bound by the FP64 pipe (1/64 of the FP32 rate on this GPU) when the batch
+// is full, so the loops count FP64 instructions: fused multiply-add chains (4 per complex
+// multiply-add), triangles visited without masked lanes, reciprocal pivots formed once,
+// reductions of the reflector step done by one warp.
 // A dependent vector among the first nb (pivot below 1e-6 of its diagonal) marks the k-point
 // with status PWK_ERR_NOT_POSDEF; a non-finite eigenvector, or eigenvectors of T that are not
 // orthonormal to 1e-8, mark it PWK_ERR_NUMERIC.
@@ -29,6 +35,54 @@ __device__ __forceinline__ double2 cmulc(double2 a, double2 b) {  // conj(a) * b
   return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+// accumulate with two fused multiply-adds per real component (4 FP64 instructions per
+// complex multiply-add)
+__device__ __forceinline__ void cfma(double2& s, double2 a, double2 b) {   // s += a b
+  s.x = fma(a.x, b.x, s.x);
+  s.x = fma(-a.y, b.y, s.x);
+  s.y = fma(a.x, b.y, s.y);
+  s.y = fma(a.y, b.x, s.y);
+}
+__device__ __forceinline__ void cfma_c(double2& s, double2 a, double2 b) {   // s += a conj(b)
+  s.x = fma(a.x, b.x, s.x);
+  s.x = fma(a.y, b.y, s.x);
+  s.y = fma(a.y, b.x, s.y);
+  s.y = fma(-a.x, b.y, s.y);
+}
+__device__ __forceinline__ void cfms(double2& s, double2 a, double2 b) {   // s -= a b
+  s.x = fma(-a.x, b.x, s.x);
+  s.x = fma(a.y, b.y, s.x);
+  s.y = fma(-a.x, b.y, s.y);
+  s.y = fma(-a.y, b.x, s.y);
+}
+__device__ __forceinline__ void cfms_c(double2& s, double2 a, double2 b) {   // s -= a conj(b)
+  s.x = fma(-a.x, b.x, s.x);
+  s.x = fma(-a.y, b.y, s.x);
+  s.y = fma(-a.y, b.x, s.y);
+  s.y = fma(a.x, b.y, s.y);
+}
+
+// Visit every (r, c) with 0 <= c <= r < m once, spread over the block: rows p and m-1-p are
+// paired (p + 1 and m - p entries, m + 1 together), so the flat index runs over
+// ceil(m/2) (m + 1) slots and the triangle masks off no lane.  Threads step their (p, o)
+// position by the block size without dividing.
+template <class F>
+__device__ __forceinline__ void for_lower(int m, int tid, int nth, F f) {
+  const int w = m + 1, total = ((m + 1) >> 1) * w;
+  if (tid >= total) return;
+  int p = tid / w, o = tid - p * w;
+  const int dp = nth / w, dq = nth - dp * w;
+  for (int i = tid; i < total; i += nth) {
+    if (o <= p) f(p, o);
+    else if (m - 1 - p != p) f(m - 1 - p, o - p - 1);
+    p += dp;
+    o += dq;
+    if (o >= w) {
+      o -= w;
+      ++p;
+    }
+  }
+}
 
 // block-wide sum of a double (all threads get the result)
 __device__ double block_sum(double v, double* red) {
@@ -61,7 +115,8 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   const int tid = threadIdx.x, nth = blockDim.x;
   __shared__ double red[32];
   __shared__ double d[kMaxBasis], e[kMaxBasis], rc[kMaxBasis], rs[kMaxBasis];
-  __shared__ double2 tau[kMaxBasis];
+  __shared__ double2 tau[kMaxBasis], vv[kMaxBasis], ww[kMaxBasis];
+  __shared__ double lam[kMaxBasis];
   __shared__ int flag;
   __shared__ unsigned char dropped[kMaxBasis];
   const size_t ldsq = (size_t)ld * ld;
@@ -78,9 +133,10 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   //      Schur complement of an exactly dependent vector (seen up to 4e-8 when the earlier
   //      basis is itself ill-conditioned), which a smaller bound can mistake for a new
   //      direction and turn into a spurious Ritz value.
+  //      Only the lower triangle of S and L is read or written.
   for (int i = tid; i < n * n; i += nth) {
     const int r = i / n, c = i - r * n;
-    Lm[r * ld + c] = S[r * ld + c];
+    if (c <= r) Lm[r * ld + c] = S[r * ld + c];
   }
   for (int i = tid; i < n; i += nth) dropped[i] = 0;
   __syncthreads();
@@ -90,29 +146,29 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
       const bool drop = !(p > 1e-6 * S[j * ld + j].x);
       dropped[j] = drop ? 1 : 0;
       if (drop && j < nb) flag = 1;   // the leading nb vectors must be independent
-      Lm[j * ld + j] = make_double2(drop ? 1.0 : sqrt(p), 0.0);
+      const double l = drop ? 1.0 : sqrt(p);
+      Lm[j * ld + j] = make_double2(l, 0.0);
+      rc[j] = 1.0 / l;
     }
     __syncthreads();
+    const int m = n - j - 1;
     if (dropped[j]) {
       for (int r = j + 1 + tid; r < n; r += nth) Lm[r * ld + j] = make_double2(0.0, 0.0);
       for (int q = tid; q < j; q += nth) Lm[j * ld + q] = make_double2(0.0, 0.0);
       __syncthreads();
       continue;
     }
-    const double ipiv = 1.0 / Lm[j * ld + j].x;
-    for (int r = j + 1 + tid; r < n; r += nth) Lm[r * ld + j] = make_double2(Lm[r * ld + j].x * ipiv, Lm[r * ld + j].y * ipiv);
-    __syncthreads();
-    // trailing update, lower triangle: L[r][c] -= L[r][j] conj(L[c][j]), c <= r
-    const int m = n - j - 1;
-    for (int i = tid; i < m * m; i += nth) {
-      const int r = j + 1 + i / m, c = j + 1 + i % m;
-      if (c <= r) {
-        const double2 a = Lm[r * ld + j], b = Lm[c * ld + j];
-        const double2 t = cmul(a, cconj(b));
-        Lm[r * ld + c].x -= t.x;
-        Lm[r * ld + c].y -= t.y;
-      }
+    const double ipiv = rc[j];
+    for (int r = tid; r < m; r += nth) {
+      double2 v = Lm[(j + 1 + r) * ld + j];
+      v = make_double2(v.x * ipiv, v.y * ipiv);
+      Lm[(j + 1 + r) * ld + j] = v;
+      vv[r] = v;
     }
+    __syncthreads();
+    // trailing update of the lower triangle: L[r][c] -= L[r][j] conj(L[c][j]), c <= r
+    double2* L22 = Lm + (size_t)(j + 1) * ld + (j + 1);
+    for_lower(m, tid, nth, [&](int r, int c) { cfms_c(L22[r * ld + c], vv[r], vv[c]); });
     __syncthreads();
   }
   if (drop_out != nullptr)
@@ -121,139 +177,124 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     if (tid == 0 && status != nullptr) status[k] = PWK_ERR_NOT_POSDEF;
     return;
   }
-  // ---- 2. X = L^-1 H (column c per thread), then C = L^-1 X^H (column c per thread); the
-  //      inverse diagonal of L is formed once (FP64 division is a long instruction sequence)
-  for (int r = tid; r < n; r += nth) rc[r] = 1.0 / Lm[r * ld + r].x;
-  __syncthreads();
+  // ---- 2. X = L^-1 H (forward substitution, one column of H per thread), then the lower
+  //      triangle of C = X L^-H row by row: row r of C solves C[r][:] L^H = X[r][:], and its
+  //      entries c <= r need only the entries before them, so the lower triangle costs n^3/6
+  //      complex multiply-adds instead of the n^3/2 of a full solve.  The inverse diagonal of
+  //      L (rc) was formed once by the Cholesky step.
   for (int c = tid; c < n; c += nth) {
     for (int r = 0; r < n; ++r) {
       double2 s = H[r * ld + c];
-      for (int q = 0; q < r; ++q) {
-        const double2 t = cmul(Lm[r * ld + q], X[q * ld + c]);
-        s.x -= t.x;
-        s.y -= t.y;
-      }
+      const double2* lr = Lm + (size_t)r * ld;
+      for (int q = 0; q < r; ++q) cfms(s, lr[q], X[q * ld + c]);
       const double il = rc[r];
       X[r * ld + c] = make_double2(s.x * il, s.y * il);
     }
   }
   __syncthreads();
-  for (int c = tid; c < n; c += nth) {
-    for (int r = 0; r < n; ++r) {
-      double2 s = cconj(X[c * ld + r]);   // (X^H)[r][c]
-      for (int q = 0; q < r; ++q) {
-        const double2 t = cmul(Lm[r * ld + q], C[q * ld + c]);
-        s.x -= t.x;
-        s.y -= t.y;
-      }
-      const double il = rc[r];
-      C[r * ld + c] = make_double2(s.x * il, s.y * il);
-    }
-  }
-  __syncthreads();
-  // symmetrise (C is Hermitian up to rounding)
-  for (int i = tid; i < n * n; i += nth) {
-    const int r = i / n, c = i - r * n;
-    if (c < r) {
-      const double2 a = C[r * ld + c], b = C[c * ld + r];
-      const double2 m = make_double2(0.5 * (a.x + b.x), 0.5 * (a.y - b.y));
-      C[r * ld + c] = m;
-      C[c * ld + r] = cconj(m);
-    } else if (c == r) {
-      C[r * ld + c].y = 0.0;
+  for (int r = tid; r < n; r += nth) {
+    const double2* xr = X + (size_t)r * ld;
+    double2* cr = C + (size_t)r * ld;
+    for (int c = 0; c <= r; ++c) {
+      double2 s = xr[c];
+      const double2* lc = Lm + (size_t)c * ld;
+      for (int q = 0; q < c; ++q) cfms_c(s, cr[q], lc[q]);   // s -= C[r][q] conj(L[c][q])
+      const double il = rc[c];
+      cr[c] = make_double2(s.x * il, c == r ? 0.0 : s.y * il);   // C is Hermitian: real diagonal
     }
   }
   __syncthreads();
   // dropped vectors: decouple their row/column and park their eigenvalue above the spectrum
+  // (||C||_F from the lower triangle)
   {
     double f = 0.0;
-    for (int i = tid; i < n * n; i += nth) {
-      const int r = i / n, c = i - r * n;
+    for_lower(n, tid, nth, [&](int r, int c) {
       const double2 v = C[r * ld + c];
-      f += v.x * v.x + v.y * v.y;
-    }
+      f += (r == c ? 1.0 : 2.0) * (v.x * v.x + v.y * v.y);
+    });
     f = block_sum(f, red);
     const double big = 4.0 * sqrt(f) + 1.0;
-    for (int i = tid; i < n * n; i += nth) {
-      const int r = i / n, c = i - r * n;
+    for_lower(n, tid, nth, [&](int r, int c) {
       if (dropped[r] || dropped[c]) C[r * ld + c] = make_double2(r == c ? big : 0.0, 0.0);
-    }
+    });
     __syncthreads();
   }
-  // ---- 3. Householder tridiagonalisation; v_j stored in C[j+1..n-1][j] with v[0] = 1
-  double2* wv = X;   // w vector scratch (first column block of X, reused)
+  // ---- 3. Householder tridiagonalisation of the Hermitian C held in its lower triangle;
+  //      v_j stored in C[j+1..n-1][j] with v[0] = 1.  Per step: the reflector (warp 0), the
+  //      product w = tau C22 v (one row per thread, the upper half read through the lower
+  //      triangle), the correction w += alpha2 v (warp 0), and the rank-2 update of the lower
+  //      triangle of C22.
   for (int j = 0; j + 1 < n; ++j) {
     const int m = n - j - 1;       // length of x = C[j+1..n-1][j]
-    double xn2 = 0.0;
-    for (int i = 1 + tid; i < m; i += nth) {
-      const double2 v = C[(j + 1 + i) * ld + j];
-      xn2 += v.x * v.x + v.y * v.y;
-    }
-    xn2 = block_sum(xn2, red);
-    const double2 alpha = C[(j + 1) * ld + j];
-    double2 t = make_double2(0.0, 0.0);
-    double beta = alpha.x;
-    if (xn2 > 0.0 || alpha.y != 0.0) {
-      const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
-      beta = alpha.x >= 0.0 ? -nrm : nrm;
-      t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-      // u = x / (alpha - beta)
-      const double2 den = make_double2(alpha.x - beta, alpha.y);
-      const double dd = den.x * den.x + den.y * den.y;
-      const double2 inv = make_double2(den.x / dd, -den.y / dd);
-      for (int i = 1 + tid; i < m; i += nth) {
-        const int r = j + 1 + i;
-        C[r * ld + j] = cmul(C[r * ld + j], inv);
+    if (tid < 32) {
+      double xn2 = 0.0;
+      for (int i = 1 + tid; i < m; i += 32) {
+        const double2 v = C[(j + 1 + i) * ld + j];
+        vv[i] = v;
+        xn2 = fma(v.x, v.x, fma(v.y, v.y, xn2));
       }
-    }
-    __syncthreads();
-    if (tid == 0) {
-      tau[j] = t;
-      e[j] = beta;
-      d[j] = C[j * ld + j].x;
-      C[(j + 1) * ld + j] = make_double2(1.0, 0.0);   // v[0] = 1
-    }
-    __syncthreads();
-    if (t.x != 0.0 || t.y != 0.0) {
-      // w = tau * C22 v  (C22 = C[j+1.., j+1..], full Hermitian)
-      for (int r = tid; r < m; r += nth) {
-        double2 s = make_double2(0.0, 0.0);
-        const double2* row = C + (size_t)(j + 1 + r) * ld + (j + 1);
-        for (int q = 0; q < m; ++q) {
-          const double2 a = row[q], v = C[(j + 1 + q) * ld + j];
-          s.x += a.x * v.x - a.y * v.y;
-          s.y += a.x * v.y + a.y * v.x;
+      for (int o = 16; o > 0; o >>= 1) xn2 += __shfl_xor_sync(0xffffffffu, xn2, o);
+      const double2 alpha = C[(j + 1) * ld + j];
+      double2 t = make_double2(0.0, 0.0);
+      double beta = alpha.x;
+      if (xn2 > 0.0 || alpha.y != 0.0) {
+        const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xn2);
+        beta = alpha.x >= 0.0 ? -nrm : nrm;
+        const double ib = 1.0 / beta;
+        t = make_double2((beta - alpha.x) * ib, -alpha.y * ib);
+        // u = x / (alpha - beta)
+        const double2 den = make_double2(alpha.x - beta, alpha.y);
+        const double idd = 1.0 / (den.x * den.x + den.y * den.y);
+        const double2 inv = make_double2(den.x * idd, -den.y * idd);
+        for (int i = 1 + tid; i < m; i += 32) {
+          const double2 u = cmul(vv[i], inv);
+          vv[i] = u;
+          C[(j + 1 + i) * ld + j] = u;
         }
-        wv[r] = cmul(t, s);
       }
-      __syncthreads();
-      // alpha2 = -1/2 tau (w^H v)
-      double2 wv_dot = make_double2(0.0, 0.0);
-      for (int r = tid; r < m; r += nth) {
-        const double2 p = cmulc(wv[r], C[(j + 1 + r) * ld + j]);
-        wv_dot.x += p.x;
-        wv_dot.y += p.y;
+      __syncwarp();   // every lane has read alpha before it is overwritten
+      if (tid == 0) {
+        tau[j] = t;
+        e[j] = beta;
+        d[j] = C[j * ld + j].x;
+        C[(j + 1) * ld + j] = make_double2(1.0, 0.0);   // v[0] = 1
+        vv[0] = make_double2(1.0, 0.0);
       }
-      wv_dot = block_sum2(wv_dot, red);
-      const double2 a2 = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), wv_dot);
-      for (int r = tid; r < m; r += nth) {
-        const double2 v = C[(j + 1 + r) * ld + j];
-        const double2 av = cmul(a2, v);
-        wv[r].x += av.x;
-        wv[r].y += av.y;
-      }
-      __syncthreads();
-      // C22 -= v w^H + w v^H
-      for (int i = tid; i < m * m; i += nth) {
-        const int r = i / m, c = i - r * m;
-        const double2 vr = C[(j + 1 + r) * ld + j], vc = C[(j + 1 + c) * ld + j];
-        const double2 a = cmul(vr, cconj(wv[c])), b = cmul(wv[r], cconj(vc));
-        double2& x = C[(size_t)(j + 1 + r) * ld + (j + 1 + c)];
-        x.x -= a.x + b.x;
-        x.y -= a.y + b.y;
-      }
-      __syncthreads();
     }
+    __syncthreads();
+    const double2 t = tau[j];
+    if (t.x == 0.0 && t.y == 0.0) continue;   // uniform across the block
+    // w = tau * C22 v  (C22 = C[j+1.., j+1..], Hermitian, lower triangle stored)
+    const double2* C22 = C + (size_t)(j + 1) * ld + (j + 1);
+    for (int r = tid; r < m; r += nth) {
+      double2 s = make_double2(0.0, 0.0);
+      const double2* row = C22 + (size_t)r * ld;
+      for (int q = 0; q <= r; ++q) cfma(s, row[q], vv[q]);
+      for (int q = r + 1; q < m; ++q) cfma_c(s, vv[q], C22[(size_t)q * ld + r]);   // conj(C[q][r]) v_q
+      ww[r] = cmul(t, s);
+    }
+    __syncthreads();
+    // alpha2 = -1/2 tau (w^H v); w += alpha2 v
+    if (tid < 32) {
+      double2 dot = make_double2(0.0, 0.0);
+      for (int r = tid; r < m; r += 32) cfma_c(dot, vv[r], ww[r]);   // conj(w_r) v_r
+      for (int o = 16; o > 0; o >>= 1) {
+        dot.x += __shfl_xor_sync(0xffffffffu, dot.x, o);
+        dot.y += __shfl_xor_sync(0xffffffffu, dot.y, o);
+      }
+      const double2 a2 = cmul(make_double2(-0.5 * t.x, -0.5 * t.y), dot);
+      for (int r = tid; r < m; r += 32) cfma(ww[r], a2, vv[r]);
+    }
+    __syncthreads();
+    // C22 -= v w^H + w v^H  (lower triangle)
+    double2* C22w = C + (size_t)(j + 1) * ld + (j + 1);
+    for_lower(m, tid, nth, [&](int r, int c) {
+      double2& x = C22w[r * ld + c];
+      cfms_c(x, vv[r], ww[c]);
+      cfms_c(x, ww[r], vv[c]);
+      if (r == c) x.y = 0.0;   // Hermitian: real diagonal
+    });
+    __syncthreads();
   }
   if (tid == 0) {
     d[n - 1] = C[(n - 1) * ld + (n - 1)].x;
@@ -264,9 +305,11 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   //      counts for the eigenvalues (one thread per eigenvalue: the threads of a warp work in
   //      lockstep, so every FP64 instruction serves up to 32 eigenvalues), then inverse
   //      iteration for the eigenvectors.
-  double* lam = rc;
   double* e2 = rs;
-  __shared__ double glo, ghi, pivmin, tiny;
+  __shared__ double glo, ghi, pivmin, tiny, werr;
+  __shared__ float d32[kMaxBasis], e232[kMaxBasis];
+  __shared__ float pivmin32;
+  __shared__ int use32;
   if (tid == 0) {
     double lo = 1e300, hi = -1e300, emax = 0.0, dmax = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -284,26 +327,65 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     ghi = hi + 1e-14 * span + 1e-300;
     pivmin = 1e-290 * fmax(1.0, emax);
     tiny = 2.2e-16 * fmax(1.0, fmax(dmax, sqrt(emax)));
+    // FP32 Sturm counts are exact for a T perturbed by at most u32 (2 dmax + |x| + 3 max|e|)
+    // (u32 = 2^-24: rounding of d, e^2 to FP32 and of each step of the recurrence), so an
+    // FP32 bracket widened by werr (8 times that bound, |x| <= dmax + 2 max|e|) holds the
+    // eigenvalue; the FP64 counts confirm it before it is used.
+    werr = 4.8e-7 * (3.0 * dmax + 5.0 * sqrt(emax));
+    use32 = dmax < 1e15 && emax < 1e28;
+    pivmin32 = (float)(1e-30 * fmax(1.0, emax));
   }
+  __syncthreads();
+  if (use32)
+    for (int i = tid; i < n; i += nth) {
+      d32[i] = (float)d[i];
+      e232[i] = i + 1 < n ? (float)e2[i] : 0.0f;
+    }
   __syncthreads();
   // bisection, one thread per eigenvalue (threads of a warp in lockstep, so every FP64
   // instruction serves up to 32 eigenvalues); FP64 throughput, not latency, bounds this
-  // kernel when the batch is full, so the Sturm counts are not multiplied across threads
+  // kernel when the batch is full, so the Sturm counts are not multiplied across threads.
+  // count(x) = number of eigenvalues below x (Sturm sequence of the LDL^T factorisation of
+  // T - x).  The bracket is first narrowed in FP32 (64 times the FP64 rate) down to werr;
+  // the FP64 bisection then starts from that bracket widened by werr on both sides.
+  auto count64 = [&](double x) {
+    double q = d[0] - x;
+    int cnt = q < 0.0;
+    for (int i = 1; i < n; ++i) {
+      if (fabs(q) < pivmin) q = -pivmin;
+      q = d[i] - x - e2[i - 1] / q;
+      cnt += q < 0.0;
+    }
+    return cnt;
+  };
   for (int j = tid; j < nb; j += nth) {
-    // the j-th smallest eigenvalue: count(x) = number of eigenvalues below x (Sturm sequence
-    // of the LDL^T factorisation of T - x)
     double a = glo, b = ghi;
+    if (use32) {
+      float a32 = __double2float_rd(glo), b32 = __double2float_ru(ghi);
+      const float w32 = (float)werr;
+      for (int it = 0; it < 160; ++it) {
+        const float mid = 0.5f * (a32 + b32);
+        if (mid <= a32 || mid >= b32 || b32 - a32 <= w32) break;
+        float q = d32[0] - mid;
+        int cnt = q < 0.0f;
+        for (int i = 1; i < n; ++i) {
+          if (fabsf(q) < pivmin32) q = -pivmin32;
+          q = d32[i] - mid - e232[i - 1] / q;
+          cnt += q < 0.0f;
+        }
+        if (cnt > j) b32 = mid;
+        else a32 = mid;
+      }
+      const double a1 = fmax(glo, (double)a32 - werr), b1 = fmin(ghi, (double)b32 + werr);
+      if (count64(a1) <= j && count64(b1) > j) {
+        a = a1;
+        b = b1;
+      }
+    }
     for (int it = 0; it < 200; ++it) {
       const double mid = 0.5 * (a + b);
       if (mid <= a || mid >= b || b - a <= 4.4e-16 * fmax(fabs(a), fabs(b)) + 2.0 * pivmin) break;
-      double q = d[0] - mid;
-      int cnt = q < 0.0;
-      for (int i = 1; i < n; ++i) {
-        if (fabs(q) < pivmin) q = -pivmin;
-        q = d[i] - mid - e2[i - 1] / q;
-        cnt += q < 0.0;
-      }
-      if (cnt > j) b = mid;
+      if (count64(mid) > j) b = mid;
       else a = mid;
     }
     lam[j] = 0.5 * (a + b);
@@ -434,8 +516,8 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
         s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
       }
       if (lane == 0) {
-        const double l = Lm[r * ld + r].x;
-        E[r * nb + j] = make_double2((E[r * nb + j].x - s.x) / l, (E[r * nb + j].y - s.y) / l);
+        const double il = rc[r];
+        E[r * nb + j] = make_double2((E[r * nb + j].x - s.x) * il, (E[r * nb + j].y - s.y) * il);
       }
       __syncwarp();
     }
