@@ -120,6 +120,25 @@ int pwk_supported_grid(int N);
 int pwk_hpsi_batched(pwk_plan* plan, int precision, const void* psi, void* hpsi, int nb,
                      void* stream);
 
+/* pwk_hpsi_batched_host: the operator of pwk_hpsi_batched on vectors that live in HOST
+ * memory, for callers whose batches arrive from and return to the host (a serving loop):
+ * the k-points are split into nchunk consecutive groups, and the copy of group c + 1 to the
+ * device, the H application of group c and the copy of group c - 1 back to the host run at
+ * the same time (two copy streams and a second compute stream of the plan, created on first
+ * use, ordered against `stream` by events; groups alternate between `stream` and the second
+ * compute stream; the transfers are one asynchronous copy per group and direction).
+ *   h_psi, h_hpsi  host [nk][nb][npw_max] complex128 (complex64 for PWK_FP32); page-locked
+ *                  memory (cudaHostAlloc / cudaHostRegister) for the copies to overlap
+ *   d_psi, d_hpsi  device work buffers of the same shape (the caller's; d_hpsi may equal
+ *                  d_psi); on return from the stream they hold the batch and its result
+ *   nchunk         groups, 1 <= nchunk (values above nk are taken as nk)
+ * The result equals pwk_hpsi_batched's bit for bit (same kernels per band-k).  Asynchronous:
+ * h_hpsi is complete when the work queued on `stream` by this call has completed.  Errors:
+ * PWK_ERR_INVALID for a null pointer, nb < 1, nchunk < 1 or an unknown precision; CUDA
+ * failures as for pwk_hpsi_batched. */
+int pwk_hpsi_batched_host(pwk_plan* plan, int precision, const void* h_psi, void* h_hpsi,
+                          void* d_psi, void* d_hpsi, int nb, int nchunk, void* stream);
+
 /* pwk_hpsi_items: the same operator on an explicit work list, for uneven batches (only the
  * listed vectors are transformed; the others are not touched).
  *   psi, hpsi   device [nk][nvec_per_k][npw_max] of the precision's complex type

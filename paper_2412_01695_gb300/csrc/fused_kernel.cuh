@@ -82,8 +82,9 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
       return;
     }
   } else {
-    k = item / a.nvec_in;
-    vin = vout = item - k * a.nvec_in;
+    const int kr = item / a.nvec_in;
+    vin = vout = item - kr * a.nvec_in;
+    k = a.k0 + kr;
   }
   const int tid = threadIdx.x, nth = blockDim.x;
   const int npi = a.npw_in[k], npo = a.npw_out[k];

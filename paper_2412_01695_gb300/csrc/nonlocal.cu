@@ -63,8 +63,9 @@ __device__ __forceinline__ void nl_item(const NlArgs& a, int item, int& k, int& 
     if (kk < 0 || kk >= a.nk || vin < 0 || vin >= a.nvec_in || vout < 0 || vout >= a.nvec_out) return;
     k = kk;
   } else {
-    k = item / a.nvec_in;
-    vin = vout = item - k * a.nvec_in;
+    const int kr = item / a.nvec_in;
+    vin = vout = item - kr * a.nvec_in;
+    k = a.k0 + kr;
   }
 }
 

@@ -20,6 +20,20 @@ static thread_local std::string g_detail;
 
 void set_error(const std::string& msg) { g_detail = msg; }
 
+namespace {
+std::mutex g_smem_mu;
+std::map<std::pair<const void*, int>, bool> g_smem_raised;
+}  // namespace
+
+bool smem_limit_raised(const void* kern, int dev) {
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  return g_smem_raised.count({kern, dev}) != 0;
+}
+void mark_smem_limit_raised(const void* kern, int dev) {
+  std::lock_guard<std::mutex> lock(g_smem_mu);
+  g_smem_raised[{kern, dev}] = true;
+}
+
 int cuda_fail(cudaError_t e, const char* what) {
   char buf[256];
   std::snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
@@ -476,7 +490,7 @@ cudaError_t scratch_alloc(void** ptr, size_t bytes, cudaStream_t st) {
 
 int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* items,
              const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st,
-             void* sout) {
+             void* sout, int k0) {
   if (precision < 0 || precision > 2) {
     set_error("unknown precision");
     return PWK_ERR_INVALID;
@@ -492,6 +506,7 @@ int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* i
     n.sout = sout;
     n.items = items;
     n.d_count = d_count;
+    n.k0 = k0;
     n.nitems = nblocks;
     n.nvec_in = nvec_in;
     n.nvec_out = nvec_out;
@@ -519,6 +534,7 @@ int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* i
     FusedArgs a = hpsi_args(p, precision, in, out);
     a.items = items;
     a.d_count = d_count;
+    a.k0 = k0;
     a.nvec_in = nvec_in;
     a.nvec_out = nvec_out;
     use_kind(p, a, p->shape[precision].kind);
@@ -608,6 +624,9 @@ int pwk_plan_launch_shape(const pwk_plan* p, int precision, int* kind, int* thre
 void pwk_plan_destroy(pwk_plan* p) {
   if (p == nullptr) return;
   destroy_solver_work(p);
+  if (p->copy_in != nullptr) cudaStreamDestroy(p->copy_in);
+  if (p->copy_out != nullptr) cudaStreamDestroy(p->copy_out);
+  if (p->compute2 != nullptr) cudaStreamDestroy(p->compute2);
   for (void* q : p->allocs) cudaFree(q);
   delete p;
 }
@@ -776,6 +795,75 @@ int pwk_hpsi_batched(pwk_plan* p, int precision, const void* psi, void* hpsi, in
   }
   return run_hpsi(p, precision, psi, hpsi, nullptr, nullptr, (int)nblocks, nb, nb,
                   static_cast<cudaStream_t>(stream));
+}
+
+int pwk_hpsi_batched_host(pwk_plan* p, int precision, const void* h_psi, void* h_hpsi,
+                          void* d_psi, void* d_hpsi, int nb, int nchunk, void* stream) {
+  if (p == nullptr || h_psi == nullptr || h_hpsi == nullptr || d_psi == nullptr ||
+      d_hpsi == nullptr || nb < 1 || nchunk < 1) {
+    set_error("null pointer, nb < 1 or nchunk < 1");
+    return PWK_ERR_INVALID;
+  }
+  if (precision < 0 || precision > 2) {
+    set_error("unknown precision");
+    return PWK_ERR_INVALID;
+  }
+  if ((long long)p->nk * nb > 0x7fffffffLL) {
+    set_error("nk * nb too large for one launch");
+    return PWK_ERR_UNSUPPORTED;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    std::lock_guard<std::mutex> lock(p->copy_mu);
+    if (p->copy_in == nullptr) {
+      cudaError_t e = cudaStreamCreateWithFlags(&p->copy_in, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->copy_out, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->compute2, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags(copy streams)");
+    }
+  }
+  nchunk = std::min(nchunk, p->nk);
+  const size_t per_k = (size_t)nb * p->npw_max * (precision == PWK_FP32 ? 8 : 16);
+  // events: start, then per chunk "copied in" and "applied", then "copied out"
+  std::vector<cudaEvent_t> ev(2 + 2 * (size_t)nchunk, nullptr);
+  int rc = PWK_OK;
+  cudaError_t e = cudaSuccess;
+  for (auto& x : ev)
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+  // the copies into d_psi and the second compute stream wait for the work already queued on
+  // the caller's stream
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_in, ev[0], 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->compute2, ev[0], 0);
+  const char* bi = static_cast<const char*>(h_psi);
+  char* bo = static_cast<char*>(h_hpsi);
+  char* di = static_cast<char*>(d_psi);
+  char* dout = static_cast<char*>(d_hpsi);
+  for (int c = 0; c < nchunk && e == cudaSuccess && rc == PWK_OK; ++c) {
+    const int k0 = (int)((long long)p->nk * c / nchunk), k1 = (int)((long long)p->nk * (c + 1) / nchunk);
+    const size_t off = (size_t)k0 * per_k, bytes = (size_t)(k1 - k0) * per_k;
+    cudaEvent_t in_done = ev[1 + 2 * c], applied = ev[2 + 2 * c];
+    // groups alternate between two compute streams, so the small grids of one group's three
+    // launches fill the GPU together with the next group's
+    cudaStream_t cs = (c & 1) ? p->compute2 : st;
+    e = cudaMemcpyAsync(di + off, bi + off, bytes, cudaMemcpyHostToDevice, p->copy_in);
+    if (e == cudaSuccess) e = cudaEventRecord(in_done, p->copy_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, in_done, 0);
+    if (e != cudaSuccess) break;
+    rc = run_hpsi(p, precision, d_psi, d_hpsi, nullptr, nullptr, (k1 - k0) * nb, nb, nb, cs, nullptr, k0);
+    if (rc != PWK_OK) break;
+    e = cudaEventRecord(applied, cs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_out, applied, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bo + off, dout + off, bytes, cudaMemcpyDeviceToHost, p->copy_out);
+  }
+  // the caller's stream completes after the last copy back (which follows every group's
+  // application on either compute stream)
+  if (e == cudaSuccess && rc == PWK_OK) e = cudaEventRecord(ev.back(), p->copy_out);
+  if (e == cudaSuccess && rc == PWK_OK) e = cudaStreamWaitEvent(st, ev.back(), 0);
+  for (auto& x : ev)
+    if (x != nullptr) cudaEventDestroy(x);   // released once the event completes
+  if (rc != PWK_OK) return rc;
+  return e == cudaSuccess ? PWK_OK : cuda_fail(e, "pwk_hpsi_batched_host");
 }
 
 int pwk_plan_set_overlap(pwk_plan* p, const double* q) {

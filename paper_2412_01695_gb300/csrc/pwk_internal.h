@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -16,19 +17,30 @@ namespace pwk {
 void set_error(const std::string& msg);  // thread-local detail for pwk_last_error_detail()
 int cuda_fail(cudaError_t e, const char* what);
 
+// Whether a kernel's shared-memory limit was already raised on a device (plan.cu; a
+// process-wide table guarded by a mutex).
+bool smem_limit_raised(const void* kern, int dev);
+void mark_smem_limit_raised(const void* kern, int dev);
+
 // Raises a kernel's dynamic shared-memory limit to the device's opt-in maximum (less the
-// kernel's static shared memory).  The value set never depends on the launch, so host threads
-// that launch the same kernel at the same time (one per stream in a serving loop) cannot lower
-// the limit under one another's launch.
+// kernel's static shared memory), once per kernel and device: later launches skip the
+// attribute calls (four runtime calls that cost more host time than a small launch).  The
+// value set never depends on the launch, so host threads that launch the same kernel at the
+// same time (one per stream in a serving loop) cannot lower the limit under one another's
+// launch, and setting it twice is harmless.
 template <typename K>
 inline cudaError_t allow_full_smem(K kern) {
   int dev = 0, optin = 0;
-  cudaFuncAttributes fa;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  const void* key = reinterpret_cast<const void*>(kern);
+  if (smem_limit_raised(key, dev)) return cudaSuccess;
+  cudaFuncAttributes fa;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) mark_smem_limit_raised(key, dev);
   return e;
 }
 
@@ -100,6 +112,10 @@ struct pwk_plan {
   std::vector<size_t> alloc_sizes;
   pwk::DavWork* dav = nullptr;
   pwk::CgWork* cg = nullptr;
+  // streams of pwk_hpsi_batched_host (created on first use, non-blocking): copies in,
+  // copies out, and a second compute stream for every other group of k-points
+  std::mutex copy_mu;
+  cudaStream_t copy_in = nullptr, copy_out = nullptr, compute2 = nullptr;
 };
 
 namespace pwk {
@@ -110,8 +126,9 @@ void plan_free(pwk_plan* p, void* ptr);
 struct FusedArgs {
   const void* in = nullptr;   // input vectors (complex of the io type)
   void* out = nullptr;        // output vectors
-  const int* items = nullptr; // [n][3] (k, in_slot, out_slot) or null: item = k * nvec + band
+  const int* items = nullptr; // [n][3] (k, in_slot, out_slot) or null: item = (k - k0) * nvec + band
   const int* d_count = nullptr;  // if set, CTAs with blockIdx.x >= *d_count exit
+  int k0 = 0;                    // first k-point of a batched (items == null) launch
   int nvec_in = 0, nvec_out = 0; // vectors per k in the in/out arrays
   int nk = 0;
   int npw_in_max = 0, npw_out_max = 0;
@@ -139,8 +156,9 @@ struct NlArgs {
   const void* in = nullptr;   // input vectors (complex of the io type)
   void* out = nullptr;        // H output (phase 1 adds to it)
   void* sout = nullptr;       // S output or null
-  const int* items = nullptr; // [n][3] (k, in_slot, out_slot) or null: item = k * nvec + band
+  const int* items = nullptr; // [n][3] (k, in_slot, out_slot) or null: item = (k - k0) * nvec + band
   const int* d_count = nullptr;
+  int k0 = 0;                  // first k-point of a batched (items == null) launch
   int nitems = 0, nvec_in = 0, nvec_out = 0, nk = 0, npw_max = 0;
   const int* npw = nullptr;
   const void* beta = nullptr;  // [nk][nkb][npw_max] complex of the arithmetic type
@@ -175,9 +193,11 @@ FusedArgs hpsi_args(const pwk_plan* p, int precision, const void* in, void* out)
 // H (and, with sout set, S) on nblocks work items: projections, local + kinetic term,
 // nonlocal add-back (three launches on st).  sout must not alias in.  out == null with sout
 // set applies S alone.
+// k0: first k-point of a batched launch (items == null): item i is band i % nvec_in of
+// k-point k0 + i / nvec_in.
 int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* items,
              const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st,
-             void* sout = nullptr);
+             void* sout = nullptr, int k0 = 0);
 
 bool grid_supported(int N);
 int build_sphere_map(pwk_plan* p, SphereMap& sm, int nk, const int* npw_in, int npw_in_max,

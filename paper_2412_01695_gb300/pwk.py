@@ -21,7 +21,8 @@ PRECISIONS = {"fp64": PWK_FP64, "fp32": PWK_FP32, "fp32_c128": PWK_FP32_C128}
 # every symbol declared in include/pwk.h
 EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
            "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_supported_grid",
-           "pwk_hpsi_batched", "pwk_hpsi_items", "pwk_plan_set_overlap", "pwk_plan_has_overlap",
+           "pwk_hpsi_batched", "pwk_hpsi_batched_host", "pwk_hpsi_items", "pwk_plan_set_overlap",
+           "pwk_plan_has_overlap",
            "pwk_hspsi_batched", "pwk_hspsi_items", "pwk_drho_batched", "pwk_davidson_batched",
            "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_eigh_batched_noalloc",
            "pwk_strerror", "pwk_last_error_detail", "pwk_version")
@@ -51,6 +52,7 @@ def load(path: str = LIB_PATH):
         "pwk_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
         "pwk_supported_grid": (_I, [_I]),
         "pwk_hpsi_batched": (_I, [_P, _I, _P, _P, _I, _P]),
+        "pwk_hpsi_batched_host": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P]),
         "pwk_hpsi_items": (_I, [_P, _I, _P, _P, _P, _I, _I, _P]),
         "pwk_plan_set_overlap": (_I, [_P, _P]),
         "pwk_plan_has_overlap": (_I, [_P]),
@@ -200,6 +202,24 @@ def hpsi_batched(plan: Plan, precision: int, psi, hpsi, nb: int, stream=None) ->
     _need(hpsi, shape, dt, "hpsi")
     _check(load().pwk_hpsi_batched(plan.handle, precision, _ptr(psi), _ptr(hpsi), nb,
                                    _stream(stream)), "pwk_hpsi_batched")
+
+
+def hpsi_batched_host(plan: Plan, precision: int, h_psi, h_hpsi, d_psi, d_hpsi, nb: int,
+                      nchunk: int, stream=None) -> None:
+    """H|psi> with the vectors in (page-locked) host tensors; d_psi, d_hpsi are device work
+    buffers of the same shape.  Copies in, applications and copies out of nchunk groups of
+    k-points overlap; the result is in h_hpsi once `stream` has completed."""
+    import torch
+    dt = torch.complex64 if precision == PWK_FP32 else torch.complex128
+    shape = (plan.nk, nb, plan.npw_max)
+    for t, name in ((h_psi, "h_psi"), (h_hpsi, "h_hpsi")):
+        if t.is_cuda or tuple(t.shape) != shape or t.dtype != dt or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous host tensor {shape} of {dt}")
+    _need(d_psi, shape, dt, "d_psi")
+    _need(d_hpsi, shape, dt, "d_hpsi")
+    _check(load().pwk_hpsi_batched_host(plan.handle, precision, ctypes.c_void_p(h_psi.data_ptr()),
+                                        ctypes.c_void_p(h_hpsi.data_ptr()), _ptr(d_psi), _ptr(d_hpsi),
+                                        nb, nchunk, _stream(stream)), "pwk_hpsi_batched_host")
 
 
 def hpsi_items(plan: Plan, precision: int, psi, hpsi, items, nvec_per_k: int, stream=None):
