@@ -264,6 +264,10 @@ def run_ours(args, rank, world, local_rank):
     t_loc = timed(lambda: pwk.hpsi_batched(plan_loc, pwk.PWK_FP32, psi32, out32, nb, stream),
                   min(200, max(3, args.steps // 4)), 5)
     plan_loc.close()
+    # the output the host leg checks against the oracle: the full operator once more (the
+    # timing above left the local-only result in out32)
+    pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream)
+    torch.cuda.synchronize()
     loc_s = float(np.mean(t_loc))
     nl_s = max(kern_s - loc_s, 1e-12)
     loc_flops = local_flops_per_band(prob, nstick_mean, P) * nbk

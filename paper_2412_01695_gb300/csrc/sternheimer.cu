@@ -18,9 +18,10 @@
 //   cg_step : lambda = -Re<d|r>/Re<d|t> (Eq. lambda), x += lambda d, r += lambda t,
 //             d_old = d, rho_old = rho (Eqs. updatex, updater, updatedold)
 // All vectors, dot products and scalars are FP64 and stay on the device; the host reads one
-// counter (pairs still iterating) per iteration.  Mixed mode: the H d inside the CG uses FP32
-// arithmetic and the solve is wrapped in FP64 iterative refinement (the CG restarts from the
-// true FP64 residual of the current x, each inner solve reducing it by 1e-4).
+// counter (pairs still iterating) per iteration.  Mixed mode: the operator inside the CG (H d
+// and the valence projection alpha Q d) uses FP32 arithmetic, and the solve is wrapped in
+// FP64 iterative refinement (the CG restarts from the true FP64 residual of the current x,
+// each inner solve reducing it by 1e-4).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -86,6 +87,8 @@ static int ensure_cg_work(pwk_plan* p, int nocc) {
 }
 
 // ------------------------------------------------------------------ kernels
+constexpr int kCgMaxPw = 2048;   // plane waves whose preconditioner cg_dir keeps in shared memory
+
 __device__ __forceinline__ double2 cmc(double2 a, double2 b) {  // conj(a) b
   return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
@@ -107,6 +110,10 @@ __device__ double bsum2(double v, double* red) {
 // ws null means ws = w.  With S = 1: pm = py = psi_{k+q,v}, ws = w.  With S (Eq. projector):
 // pm = py = S psi_{k+q,v} and ws = S w for the operator (alpha Q w - eps S w), and pm = psi,
 // py = S psi for the right-hand side -(1 - S P_v) w.  The norm of out goes to onorm.
+// T is the arithmetic type (vectors are complex128 in memory): FP64, or FP32 for the operator
+// inside the mixed-mode CG, whose H part is FP32 as well (the refinement's FP64 residuals
+// use the FP64 form).
+template <typename T>
 __global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, const int* npw,
                                                            const int* active,
                                                            const double2* pm, const double2* py,
@@ -115,10 +122,10 @@ __global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, con
                                                            int wmode, const double* eps,
                                                            int pmode, const double* alpha,
                                                            double2* out, double* onorm) {
-  const int k = blockIdx.x / nocc, n = blockIdx.x % nocc;
+  const int k = blockIdx.x / nocc;
   if (active != nullptr && !active[blockIdx.x]) return;
   const int npk = npw[k];
-  __shared__ double2 mu[64];
+  __shared__ T mur[64], mui[64];
   __shared__ double red[32];
   const double2* W = w + (size_t)blockIdx.x * np;
   const double2* WS = ws != nullptr ? ws + (size_t)blockIdx.x * np : W;
@@ -126,22 +133,26 @@ __global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, con
   const double2* Yk = py + (size_t)k * nocc * np;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int v = warp; v < nocc; v += nw) {
-    double sx = 0, sy = 0;
+    T sx = 0, sy = 0;
     const double2* pv = Pk + (size_t)v * np;
     for (int g = lane; g < npk; g += 32) {
-      const double2 c = cmc(pv[g], W[g]);
-      sx += c.x;
-      sy += c.y;
+      const double2 a = pv[g], b = W[g];   // conj(a) b
+      const T ax = T(a.x), ay = T(a.y), bx = T(b.x), by = T(b.y);
+      sx += ax * bx + ay * by;
+      sy += ax * by - ay * bx;
     }
     for (int o = 16; o > 0; o >>= 1) {
       sx += __shfl_xor_sync(0xffffffffu, sx, o);
       sy += __shfl_xor_sync(0xffffffffu, sy, o);
     }
-    if (lane == 0) mu[v] = make_double2(sx, sy);
+    if (lane == 0) {
+      mur[v] = sx;
+      mui[v] = sy;
+    }
   }
   __syncthreads();
-  const double aw = wmode ? -eps[blockIdx.x] : -1.0;
-  const double ap = pmode ? alpha[k] : 1.0;
+  const T aw = wmode ? T(-eps[blockIdx.x]) : T(-1);
+  const T ap = pmode ? T(alpha[k]) : T(1);
   const double2* U = u ? u + (size_t)blockIdx.x * np : nullptr;
   double2* O = out + (size_t)blockIdx.x * np;
   double nn = 0.0;
@@ -150,14 +161,16 @@ __global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, con
       O[g] = make_double2(0.0, 0.0);
       continue;
     }
-    double2 y = make_double2(0.0, 0.0);
+    T yx = 0, yy = 0;
     for (int v = 0; v < nocc; ++v) {
-      const double2 p = Yk[(size_t)v * np + g], m = mu[v];
-      y.x += p.x * m.x - p.y * m.y;
-      y.y += p.x * m.y + p.y * m.x;
+      const double2 p = Yk[(size_t)v * np + g];
+      const T px = T(p.x), pyv = T(p.y), mx = mur[v], my = mui[v];
+      yx += px * mx - pyv * my;
+      yy += px * my + pyv * mx;
     }
     const double2 wg = WS[g];
-    double2 o = make_double2(aw * wg.x + ap * y.x, aw * wg.y + ap * y.y);
+    const T ox = aw * T(wg.x) + ap * yx, oy = aw * T(wg.y) + ap * yy;
+    double2 o = make_double2(double(ox), double(oy));
     if (U) {
       o.x += U[g].x;
       o.y += U[g].y;
@@ -165,8 +178,10 @@ __global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, con
     nn += o.x * o.x + o.y * o.y;
     O[g] = o;
   }
-  nn = bsum2(nn, red);
-  if (onorm != nullptr && threadIdx.x == 0) onorm[blockIdx.x] = sqrt(nn);
+  if (onorm != nullptr) {   // uniform over the block
+    nn = bsum2(nn, red);
+    if (threadIdx.x == 0) onorm[blockIdx.x] = sqrt(nn);
+  }
 }
 
 // <psi_{k+q,n}|T|psi_{k+q,n}> / <psi|psi> for the preconditioner of Sec. 2.4
@@ -232,14 +247,19 @@ __global__ void __launch_bounds__(256) cg_dir_kernel(int nocc, int np, const int
   __shared__ double red[32];
   const int npk = npw[k];
   const double* G = g2 + (size_t)k * np;
-  const double tk = tkin[i];
+  const double itk = 1.0 / tkin[i];
   const double2* R = r + (size_t)i * np;
+  // 1/M_G = 1 / max(1, |k+q+G|^2 / T_kin) (Eq. row2): one division per plane wave, kept in
+  // shared memory for the update pass when the sphere fits (np is uniform over the launch)
+  __shared__ double im[kCgMaxPw];
+  const bool keep = np <= kCgMaxPw;
   double rr = 0.0, rh = 0.0;
   for (int g = threadIdx.x; g < npk; g += blockDim.x) {
     const double2 x = R[g];
-    const double m = fmax(1.0, G[g] / tk);
+    const double mi = 1.0 / fmax(1.0, G[g] * itk);
+    if (keep) im[g] = mi;
     rr += x.x * x.x + x.y * x.y;
-    rh += (x.x * x.x + x.y * x.y) / m;   // Re<M^-1 r | r>
+    rh += (x.x * x.x + x.y * x.y) * mi;   // Re<M^-1 r | r>
   }
   rr = bsum2(rr, red);
   rh = bsum2(rh, red);
@@ -256,8 +276,8 @@ __global__ void __launch_bounds__(256) cg_dir_kernel(int nocc, int np, const int
       D[g] = make_double2(0.0, 0.0);
       continue;
     }
-    const double m = fmax(1.0, G[g] / tk);
-    double2 v = make_double2(R[g].x / m, R[g].y / m);
+    const double mi = keep ? im[g] : 1.0 / fmax(1.0, G[g] * itk);   // im[g]: this thread's, pass 1
+    double2 v = make_double2(R[g].x * mi, R[g].y * mi);
     if (!f) {
       v.x += gam * DO[g].x;
       v.y += gam * DO[g].y;
@@ -433,7 +453,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     su = w->su;
   }
   double2* const sx = w->with_s ? w->sx : nullptr;   // S applied to the operand of A
-  proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, su, nullptr, w->t,
+  proj_combine_kernel<double><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, su, nullptr, w->t,
                                               nullptr, 0, nullptr, 0, nullptr, w->b, w->bnorm);
   tkin_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, psi_kq, w->tkin);
   cudaMemsetAsync(w->iters, 0, sizeof(int) * npairs, st);
@@ -452,7 +472,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
       // t = H x (FP64) on every pair, then t = t - eps x + alpha P_v x, r = t - b
       cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
       if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
-      proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1,
+      proj_combine_kernel<double><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1,
                                                   eps_k, 1, alpha, w->t, nullptr);
       residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, eta,
                                               w->r, w->rnorm, w->thr, w->active, w->first, w->counters);
@@ -471,8 +491,12 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
       cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->items);
       if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx)))
         return rc;
-      proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t, w->d, sx,
-                                                  1, eps_k, 1, alpha, w->t, nullptr);
+      if (inner_prec == PWK_FP64)
+        proj_combine_kernel<double><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
+                                                            w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr);
+      else
+        proj_combine_kernel<float><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
+                                                           w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr);
       cg_step_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, w->d, w->t, x, w->r, w->dold,
                                              w->rho, w->rho_old, w->iters, w->counters);
       KCK("cg_step_kernel");
@@ -483,7 +507,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
   {
     cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
     if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
-    proj_combine_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1, eps_k,
+    proj_combine_kernel<double><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1, eps_k,
                                                 1, alpha, w->t, nullptr);
     residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, 0.0, w->r,
                                             w->rnorm, w->thr, w->active, w->first, w->counters);
