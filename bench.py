@@ -374,21 +374,12 @@ def run_solvers(dev, stream, quick=False):
     plan.close()
 
     # Sternheimer on a block of the DFPT cell
+    from paper_2412_01695_gb300.run_case import sternheimer_block
     nk4 = 64 if quick else 256
-    ks4 = list(range(nk4))
-    pk = synth.make_config(4, k_subset=ks4, nb=16)
-    pq = synth.make_config(4, k_subset=ks4, shift_q=True, nb=16)
-    plan_k = pwk.plan_from_problem(pk, device=dev)
-    plan_q = pwk.plan_from_problem(pq, device=dev)
-    nocc, nbx = 12, 16
-    _, rc1, _, _, eps_k, psi_k = dav(plan_k, pk, pwk.PWK_FP64, nbx)
-    _, rc2, _, _, eps_q, psi_q = dav(plan_q, pq, pwk.PWK_FP64, nbx)
-    psi_k = psi_k[:, :nocc].contiguous()
-    psi_q = psi_q[:, :nocc].contiguous()
-    ek = eps_k[:, :nocc].contiguous()
-    e_all = torch.cat([eps_k[:, :nocc], eps_q[:, :nocc]], dim=1)
-    alpha = torch.clamp(2.0 * (e_all.max(dim=1).values - e_all.min(dim=1).values), min=0.01).contiguous()
-    dv = torch.from_numpy(synth.dv_for(4)).to(dev)
+    blk = sternheimer_block(nk4, dev, stream)
+    pk, pq, plan_k, plan_q = blk["pk"], blk["pq"], blk["plan_k"], blk["plan_q"]
+    nocc, eps_k, eps_q = blk["nocc"], blk["eps_k"], blk["eps_q"]
+    psi_k, psi_q, ek, alpha, dv = blk["psi_k"], blk["psi_q"], blk["ek"], blk["alpha"], blk["dv"]
     sres = {"k_points": nk4, "nocc": nocc,
             "positive_definite_pairs": int((eps_q[:, nocc:nocc + 1] - ek > 0).sum().item())}
     for name, mode in (("mixed", pwk.PWK_FP32_C128), ("fp64", pwk.PWK_FP64)):
