@@ -122,7 +122,8 @@ int pwk_hpsi_batched(pwk_plan* plan, int precision, const void* psi, void* hpsi,
 
 /* pwk_hpsi_batched_host: the operator of pwk_hpsi_batched on vectors that live in HOST
  * memory, for callers whose batches arrive from and return to the host (a serving loop):
- * the k-points are split into nchunk consecutive groups, and the copy of group c + 1 to the
+ * the k-points are split into nchunk consecutive groups (with three or more, the first and
+ * the last hold half as many k-points as the others), and the copy of group c + 1 to the
  * device, the H application of group c and the copy of group c - 1 back to the host run at
  * the same time (two copy streams and a second compute stream of the plan, created on first
  * use, ordered against `stream` by events; groups alternate between `stream` and the second
@@ -234,6 +235,7 @@ int pwk_drho_batched(pwk_plan* plan_kq, pwk_plan* plan_k, int precision, const v
  * problem p < nprob: H_p v = eps S_p v, the nev lowest eigenpairs, FP64, one CTA per problem
  * (Cholesky of S, reduction to standard form, Householder tridiagonalisation, bisection and inverse iteration).
  *   H, S    device complex128 [nprob][n][n], row-major, full Hermitian; S positive definite
+ *           (only its lower triangle is read)
  *   eig     device float64 [nprob][nev], ascending
  *   vec     device complex128 [nprob][n][nev]: column j is the eigenvector of eig[p][j],
  *           S-orthonormal

@@ -797,6 +797,17 @@ int pwk_hpsi_batched(pwk_plan* p, int precision, const void* psi, void* hpsi, in
                   static_cast<cudaStream_t>(stream));
 }
 
+// First k-point of group c of pwk_hpsi_batched_host (group_start(nk, n, n) = nk).  With three
+// or more groups the first and the last get half the weight of the others: the copy in of
+// the first group and the copy out of the last are the parts of the pipeline that nothing
+// overlaps, so they are kept short.
+static int group_start(int nk, int n, int c) {
+  if (n < 3) return (int)((long long)nk * c / n);
+  const long long w2 = 2LL * (n - 1);   // total weight in halves: 1 + 2 (n - 2) + 1
+  const long long h = c == 0 ? 0 : (c == n ? w2 : 2LL * c - 1);
+  return (int)(nk * h / w2);
+}
+
 int pwk_hpsi_batched_host(pwk_plan* p, int precision, const void* h_psi, void* h_hpsi,
                           void* d_psi, void* d_hpsi, int nb, int nchunk, void* stream) {
   if (p == nullptr || h_psi == nullptr || h_hpsi == nullptr || d_psi == nullptr ||
@@ -840,7 +851,7 @@ int pwk_hpsi_batched_host(pwk_plan* p, int precision, const void* h_psi, void* h
   char* di = static_cast<char*>(d_psi);
   char* dout = static_cast<char*>(d_hpsi);
   for (int c = 0; c < nchunk && e == cudaSuccess && rc == PWK_OK; ++c) {
-    const int k0 = (int)((long long)p->nk * c / nchunk), k1 = (int)((long long)p->nk * (c + 1) / nchunk);
+    const int k0 = group_start(p->nk, nchunk, c), k1 = group_start(p->nk, nchunk, c + 1);
     const size_t off = (size_t)k0 * per_k, bytes = (size_t)(k1 - k0) * per_k;
     cudaEvent_t in_done = ev[1 + 2 * c], applied = ev[2 + 2 * c];
     // groups alternate between two compute streams, so the small grids of one group's three
