@@ -270,6 +270,14 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     loc_s = float(np.mean(t_loc))
     nl_s = max(kern_s - loc_s, 1e-12)
+    # the same step with the projections on the tensor cores (3xTF32, pwk_plan_set_projector_path)
+    plan.set_projector_path(1)
+    t_tc = timed(lambda: pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream),
+                 min(200, max(3, args.steps // 4)), 5)
+    plan.set_projector_path(0)
+    pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream)   # the output checked below
+    torch.cuda.synchronize()
+    tc_step_s = float(np.mean(t_tc))
     loc_flops = local_flops_per_band(prob, nstick_mean, P) * nbk
     achieved_tf = loc_flops / loc_s / 1e12
     flops = algorithmic_flops_per_band(prob, nstick_mean, P) * nbk
@@ -307,7 +315,11 @@ def run_ours(args, rank, world, local_rank):
                      "hbm_peak_gbs": pk["hbm_gbs"]},
         "roofline_nonlocal": {"bound": "hbm", "achieved": nl_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
                               "frac": nl_gbs / pk["hbm_gbs"], "ms": nl_s * 1e3,
-                              "kernels": "nl_project_kernel + nl_addback_kernel (step time minus the local kernel)"},
+                              "kernels": "nl_project_kernel + nl_addback_kernel (step time minus the local kernel)",
+                              "tensor_core_projection": {"step_ms": tc_step_s * 1e3,
+                                                         "pair_ms": (tc_step_s - loc_s) * 1e3,
+                                                         "kernels": "nl_project_tc_kernel (tcgen05, 3xTF32) + nl_addback_kernel",
+                                                         "default": False}},
         "e2e": {"value": nbk / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
                 "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size()),

@@ -99,6 +99,16 @@ int pwk_plan_launch_shape(const pwk_plan* plan, int precision, int* kind, int* t
  * memory or the window kernel does not apply to the plan (the shape is then unchanged). */
 int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threads, int l3_chunk);
 
+/* Path of the projections lambda = beta^H C (Eq. lambdah) in FP32 arithmetic:
+ *   0 (default)  the CUDA-core kernel (as FP64 and work-list calls always use);
+ *   1            the 5th-generation tensor cores wherever they apply (batched calls on whole
+ *                k-points, nb + nkb <= 56, nkb <= 16): three TF32 products of a hi/lo split
+ *                (FP32-level accuracy), FP32 accumulation in tensor memory.  On the 512-k
+ *                cell it is slower than the CUDA-core kernel (0.069 against 0.048 ms), hence
+ *                not the default.
+ * The two paths round differently (both to FP32 accuracy).  PWK_ERR_INVALID for another value. */
+int pwk_plan_set_projector_path(pwk_plan* plan, int path);
+
 /* 1 if an N x N x N grid is supported by the fused kernels, else 0. */
 int pwk_supported_grid(int N);
 

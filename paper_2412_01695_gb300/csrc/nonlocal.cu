@@ -394,6 +394,7 @@ size_t nl_shared_bytes(int nkb, int precision) {
 }
 
 int launch_nl(int precision, const NlArgs& a, cudaStream_t st) {
+  if (a.tensor_cores && nl_project_tc_applies(precision, a)) return launch_nl_project_tc(precision, a, st);
   switch (precision) {
     case PWK_FP64: return launch_nl_typed<double, double>(a, st);
     case PWK_FP32: return launch_nl_typed<float, float>(a, st);

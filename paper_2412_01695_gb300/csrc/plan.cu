@@ -507,6 +507,8 @@ int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* i
     n.items = items;
     n.d_count = d_count;
     n.k0 = k0;
+    n.err = p->d_err;
+    n.tensor_cores = p->projector_path == 1;
     n.nitems = nblocks;
     n.nvec_in = nvec_in;
     n.nvec_out = nvec_out;
@@ -580,6 +582,15 @@ const char* pwk_strerror(int code) {
 }
 
 size_t pwk_plan_device_bytes(const pwk_plan* p) { return p ? p->bytes : 0; }
+
+int pwk_plan_set_projector_path(pwk_plan* p, int path) {
+  if (p == nullptr || path < 0 || path > 1) {
+    set_error("null plan or path not 0/1");
+    return PWK_ERR_INVALID;
+  }
+  p->projector_path = path;
+  return PWK_OK;
+}
 
 int pwk_plan_set_launch_shape(pwk_plan* p, int precision, int kind, int threads, int l3_chunk) {
   if (p == nullptr || precision < 0 || precision > 2 || kind < 0 || kind > 2 ||

@@ -105,6 +105,7 @@ struct pwk_plan {
   const pwk_plan* xfer_src = nullptr;
   pwk::LaunchShape shape[3];     // per precision
   pwk::LaunchShape xshape;       // transfer kernel (complex dv, FP64)
+  int projector_path = 0;        // 0: CUDA cores, 1: tensor cores where they apply
   int* d_err = nullptr;          // device error word (bad work items)
   // accounting
   size_t bytes = 0, budget = 0;
@@ -166,8 +167,13 @@ struct NlArgs {
   const void* q = nullptr;     // [nkb][nkb] or null
   int nkb = 0;
   void* coef = nullptr;        // [nitems][2][nkb] complex of the arithmetic type
+  int* err = nullptr;          // plan error word (bit 2: a tensor-core wait ran out)
+  bool tensor_cores = false;   // projections on the tensor cores where they apply
 };
 int launch_nl(int precision, const NlArgs& a, cudaStream_t st);
+// tensor-core projection (nonlocal_tc.cu): whether it applies to a launch, and the launch
+int nl_project_tc_applies(int precision, const NlArgs& a);
+int launch_nl_project_tc(int precision, const NlArgs& a, cudaStream_t st);
 // stream-ordered scratch from the library's per-device pool (memory returned with
 // cudaFreeAsync stays mapped in the pool for later calls)
 cudaError_t scratch_alloc(void** ptr, size_t bytes, cudaStream_t st);

@@ -20,7 +20,8 @@ PRECISIONS = {"fp64": PWK_FP64, "fp32": PWK_FP32, "fp32_c128": PWK_FP32_C128}
 
 # every symbol declared in include/pwk.h
 EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
-           "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_supported_grid",
+           "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_plan_set_projector_path",
+           "pwk_supported_grid",
            "pwk_hpsi_batched", "pwk_hpsi_batched_host", "pwk_hpsi_items", "pwk_plan_set_overlap",
            "pwk_plan_has_overlap",
            "pwk_hspsi_batched", "pwk_hspsi_items", "pwk_drho_batched", "pwk_davidson_batched",
@@ -50,6 +51,7 @@ def load(path: str = LIB_PATH):
         "pwk_plan_device_bytes": (_SZ, [_P]),
         "pwk_plan_launch_shape": (_I, [_P, _I, _P, _P, _P, _P]),
         "pwk_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
+        "pwk_plan_set_projector_path": (_I, [_P, _I]),
         "pwk_supported_grid": (_I, [_I]),
         "pwk_hpsi_batched": (_I, [_P, _I, _P, _P, _I, _P]),
         "pwk_hpsi_batched_host": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P]),
@@ -133,6 +135,10 @@ class Plan:
     def set_launch_shape(self, precision: int, kind: int, threads: int, l3_chunk: int):
         _check(load().pwk_plan_set_launch_shape(self.handle, precision, kind, threads, l3_chunk),
                "pwk_plan_set_launch_shape")
+
+    def set_projector_path(self, path: int) -> None:
+        """pwk_plan_set_projector_path: 0 CUDA cores (default), 1 tensor cores where they apply."""
+        _check(load().pwk_plan_set_projector_path(self.handle, path), "pwk_plan_set_projector_path")
 
     def set_overlap(self, q) -> None:
         """pwk_plan_set_overlap: q host float64 [nkb][nkb] symmetric, or None (S = 1)."""

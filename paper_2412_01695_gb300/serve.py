@@ -399,7 +399,9 @@ class GpuExecutor:
                                                               psi_k, ek[:, :nocc].contiguous(),
                                                               psi_q, nocc, alpha, dv, dpsi, 1e-10,
                                                               500, stream)
-            job.result = (dpsi.cpu().numpy(), resid)
+            # the valence states go with the result: within a degenerate level they are fixed only
+            # up to a unitary mix, which carries over to dpsi (sum_n |dpsi_n><psi_n| is unique)
+            job.result = (dpsi.cpu().numpy(), resid, psi_k.cpu().numpy())
         finally:
             self.release(kk)
             self.release(kq)

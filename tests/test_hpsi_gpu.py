@@ -198,3 +198,32 @@ def test_every_launch_shape_gives_identical_results(precision):
                     outs[key] = out
     assert set(outs) == {0, 1}
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp32_c128"])
+@pytest.mark.parametrize("cfg,nks,nb", [(2, 6, 20), (1, 8, 8), (4, 5, 12), (2, 3, 44)])
+def test_tensor_core_projections_match_cuda_cores_and_oracle(precision, cfg, nks, nb):
+    """The FP32 projections on the tensor cores (three TF32 products of a hi/lo split) and on
+    the CUDA cores both meet the FP32 bound against the oracle, and agree with each other to
+    FP32 rounding (nb + nkb up to 53 of the 56 the tensor-core kernel takes)."""
+    torch = torch_cuda()
+    from paper_2412_01695_gb300 import pwk
+    nkfull = int(np.prod(synth.CONFIGS[cfg]["mp"]))
+    prob = synth.make_config(cfg, k_subset=synth.sample_k(nkfull, nks), nb=nb)
+    psi = prob.psi.astype(np.complex64).astype(np.complex128) if precision == "fp32" else prob.psi
+    ref = oracle_hpsi(prob, psi=psi)
+    plan = pwk.plan_from_problem(prob)
+    prec = pwk.PRECISIONS[precision]
+    dt = torch.complex64 if precision == "fp32" else torch.complex128
+    x = torch.from_numpy(np.ascontiguousarray(psi)).to("cuda", dt)
+    outs = []
+    for path in (0, 1):
+        plan.set_projector_path(path)
+        y = torch.full_like(x, complex(np.nan, np.nan))
+        pwk.hpsi_batched(plan, prec, x, y, prob.nb)
+        torch.cuda.synchronize()
+        outs.append(y.cpu().numpy().astype(np.complex128))
+        assert max_rel_err(outs[-1], ref, prob) <= TOL32, (path, max_rel_err(outs[-1], ref, prob))
+    d = max(np.linalg.norm(outs[0][ik] - outs[1][ik]) / np.linalg.norm(outs[1][ik]) for ik in range(prob.nk))
+    assert d <= 2e-6, d
+    plan.close()

@@ -51,9 +51,14 @@ def test_each_result_alone_equals_result_in_the_mix():
         elif a.kind == "davidson":
             np.testing.assert_allclose(m.result, a.result, atol=1e-8, rtol=0)
         else:
-            xa, ra = a.result
-            xm, rm = m.result
+            # the valence states of each run come from its own FP64 Davidson (on plans tuned
+            # apart), so within a degenerate level they may differ by a unitary mix, which dpsi
+            # follows; sum_n |dpsi_n><psi_n| per k-point is the same either way
+            xa, ra, ua = a.result
+            xm, rm, um = m.result
             assert ra.max() <= 1e-10 and rm.max() <= 1e-10
-            assert np.linalg.norm(xa - xm) <= 1e-6 * np.linalg.norm(xa)
+            ma = np.einsum("kng,knh->kgh", xa, ua.conj())
+            mm = np.einsum("kng,knh->kgh", xm, um.conj())
+            assert np.linalg.norm(ma - mm) <= 1e-6 * np.linalg.norm(ma)
     st = serve.latency_stats(mixed)
     assert st["p99_s"] >= st["p50_s"] > 0
