@@ -104,7 +104,7 @@ int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threa
  *   1            the 5th-generation tensor cores wherever they apply (batched calls on whole
  *                k-points, nb + nkb <= 56, nkb <= 16): three TF32 products of a hi/lo split
  *                (FP32-level accuracy), FP32 accumulation in tensor memory.  On the 512-k
- *                cell it is slower than the CUDA-core kernel (0.069 against 0.048 ms), hence
+ *                cell it is slower than the CUDA-core kernel (about 0.07 against 0.048 ms), hence
  *                not the default.
  * The two paths round differently (both to FP32 accuracy).  PWK_ERR_INVALID for another value. */
 int pwk_plan_set_projector_path(pwk_plan* plan, int path);

@@ -45,7 +45,7 @@ constexpr int kTcTileB = kTcN * 128;   // bytes of one B tile (32 rows x 128 B)
 constexpr uint32_t kTcTmemCols = 32;
 constexpr long kTcWaitLimit = 1L << 24;   // try_wait polls before a wait gives up
 constexpr int kTcRing = 6;                 // raw blocks in the asynchronous-copy ring
-constexpr int kTcStages = 4;               // hi/lo tile stages (MMAs of kTcStages - 1 blocks in flight)
+constexpr int kTcStages = 3;               // hi/lo tile stages (MMAs of kTcStages - 1 blocks in flight)
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -120,7 +120,7 @@ __device__ __forceinline__ void split4(float a, float b, float c, float d, float
 }
 
 template <typename TI>
-__global__ void __launch_bounds__(kTcThreads, 1) nl_project_tc_kernel(NlArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 3) nl_project_tc_kernel(NlArgs a) {
   using VI = c2_t<TI>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t full[kTcStages], empty[kTcStages];
@@ -175,18 +175,39 @@ __global__ void __launch_bounds__(kTcThreads, 1) nl_project_tc_kernel(NlArgs a) 
   // coefficients, nkb rows of 16 projector values (one element per copy; zero past npw(k))
   const VI* cin = static_cast<const VI*>(a.in) + (size_t)k * a.nvec_in * a.npw_max;
   const float2* bin = static_cast<const float2*>(a.beta) + (size_t)k * nkb * a.npw_max;
+  // 16-byte copies (one complex128 or two complex64 values) when every row of both arrays
+  // starts on a 16-byte boundary (the projectors are complex64: npw_max must be even)
+  const bool pairs = a.npw_max % 2 == 0 && (reinterpret_cast<uintptr_t>(a.in) & 15) == 0 &&
+                     (reinterpret_cast<uintptr_t>(a.beta) & 15) == 0;
   auto fetch = [&](int b) {
     if (b < nblk) {
       unsigned char* slot = ring + (b % kTcRing) * raw_slot;
-      for (int t = tid; t < 16 * (nb + nkb); t += kTcProducers) {
-        const int r = t >> 4, j = t & 15, g = 16 * b + j;
-        const bool in = g < np;
-        if (r < nb) {
-          tc_cp_async<sizeof(VI)>(slot + (r * 16 + j) * sizeof(VI), cin + (size_t)r * a.npw_max + (in ? g : 0),
-                                  in ? (int)sizeof(VI) : 0);
-        } else {
-          const int m = r - nb;
-          tc_cp_async<8>(slot + raw_a + (m * 16 + j) * 8, bin + (size_t)m * a.npw_max + (in ? g : 0), in ? 8 : 0);
+      if (pairs) {   // A: 16 bytes = one complex128 or two complex64; beta: two complex64
+        constexpr int per_a = sizeof(VI) == 16 ? 16 : 8;   // copies per A row of 16 plane waves
+        const int na = nb * per_a;
+        for (int t = tid; t < na + 8 * nkb; t += kTcProducers) {
+          if (t < na) {
+            const int r = t / per_a, j = (t - r * per_a) * (16 / (int)sizeof(VI)), g = 16 * b + j;
+            const int nv = min(16 / (int)sizeof(VI), max(0, np - g));   // valid elements of the copy
+            tc_cp_async<16>(slot + (r * 16 + j) * sizeof(VI), cin + (size_t)r * a.npw_max + (nv > 0 ? g : 0),
+                            nv * (int)sizeof(VI));
+          } else {
+            const int m = (t - na) >> 3, j = 2 * ((t - na) & 7), g = 16 * b + j;
+            const int nv = min(2, max(0, np - g));
+            tc_cp_async<16>(slot + raw_a + (m * 16 + j) * 8, bin + (size_t)m * a.npw_max + (nv > 0 ? g : 0), nv * 8);
+          }
+        }
+      } else {
+        for (int t = tid; t < 16 * (nb + nkb); t += kTcProducers) {
+          const int r = t >> 4, j = t & 15, g = 16 * b + j;
+          const bool in = g < np;
+          if (r < nb) {
+            tc_cp_async<sizeof(VI)>(slot + (r * 16 + j) * sizeof(VI), cin + (size_t)r * a.npw_max + (in ? g : 0),
+                                    in ? (int)sizeof(VI) : 0);
+          } else {
+            const int m = r - nb;
+            tc_cp_async<8>(slot + raw_a + (m * 16 + j) * 8, bin + (size_t)m * a.npw_max + (in ? g : 0), in ? 8 : 0);
+          }
         }
       }
     }

@@ -55,6 +55,8 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_c128"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--max-iter", type=int, default=100, help="Davidson iterations")
+    ap.add_argument("--projector-path", type=int, default=0,
+                    help="0: CUDA-core projections, 1: tensor cores where they apply")
     args = ap.parse_args()
 
     import torch
@@ -66,6 +68,7 @@ def main():
     sub = None if args.nk in (0, nkfull) else list(range(args.nk))
     prob = synth.make_config(args.cfg, k_subset=sub, nb=args.nb or None)
     plan = pwk.plan_from_problem(prob)
+    plan.set_projector_path(args.projector_path)
     prec = pwk.PRECISIONS[args.precision]
     times = []
     # the repetitions sit in an NVTX range "run_case" (profilers can select exactly them)
