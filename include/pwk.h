@@ -144,7 +144,9 @@ int pwk_hpsi_batched(pwk_plan* plan, int precision, const void* psi, void* hpsi,
  *                  d_psi); on return from the stream they hold the batch and its result
  *   nchunk         groups, 1 <= nchunk (values above nk are taken as nk)
  * The result equals pwk_hpsi_batched's bit for bit (same kernels per band-k).  Asynchronous:
- * h_hpsi is complete when the work queued on `stream` by this call has completed.  Errors:
+ * h_hpsi is complete when the work queued on `stream` by this call has completed; `stream`
+ * also waits for the helper streams after an error, so its synchronisation always means the
+ * buffers are no longer in use.  Errors:
  * PWK_ERR_INVALID for a null pointer, nb < 1, nchunk < 1 or an unknown precision; CUDA
  * failures as for pwk_hpsi_batched. */
 int pwk_hpsi_batched_host(pwk_plan* plan, int precision, const void* h_psi, void* h_hpsi,

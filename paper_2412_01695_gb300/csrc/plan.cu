@@ -846,8 +846,9 @@ int pwk_hpsi_batched_host(pwk_plan* p, int precision, const void* h_psi, void* h
   }
   nchunk = std::min(nchunk, p->nk);
   const size_t per_k = (size_t)nb * p->npw_max * (precision == PWK_FP32 ? 8 : 16);
-  // events: start, then per chunk "copied in" and "applied", then "copied out"
-  std::vector<cudaEvent_t> ev(2 + 2 * (size_t)nchunk, nullptr);
+  // events: start, then per chunk "copied in" and "applied", then the ends of the three
+  // helper streams
+  std::vector<cudaEvent_t> ev(4 + 2 * (size_t)nchunk, nullptr);
   int rc = PWK_OK;
   cudaError_t e = cudaSuccess;
   for (auto& x : ev)
@@ -878,10 +879,19 @@ int pwk_hpsi_batched_host(pwk_plan* p, int precision, const void* h_psi, void* h
     if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_out, applied, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(bo + off, dout + off, bytes, cudaMemcpyDeviceToHost, p->copy_out);
   }
-  // the caller's stream completes after the last copy back (which follows every group's
-  // application on either compute stream)
-  if (e == cudaSuccess && rc == PWK_OK) e = cudaEventRecord(ev.back(), p->copy_out);
-  if (e == cudaSuccess && rc == PWK_OK) e = cudaStreamWaitEvent(st, ev.back(), 0);
+  // the caller's stream completes after everything this call queued on the helper streams
+  // (on success the last copy back; after an error whatever was queued before it), so that a
+  // synchronisation of `stream` always covers the buffers
+  {
+    cudaStream_t helpers[3] = {p->copy_in, p->compute2, p->copy_out};
+    for (int h = 0; h < 3; ++h) {
+      cudaEvent_t x = ev[ev.size() - 3 + h];
+      if (x == nullptr) continue;
+      cudaError_t e2 = cudaEventRecord(x, helpers[h]);
+      if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, x, 0);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
   for (auto& x : ev)
     if (x != nullptr) cudaEventDestroy(x);   // released once the event completes
   if (rc != PWK_OK) return rc;
