@@ -478,6 +478,39 @@ def run_solvers(dev, stream, quick=False):
     return out
 
 
+def run_other_cells(dev, stream, quick=False):
+    """H|psi> on the other synthetic cells (context beside the headline cell): FP32 and FP64
+    batched band-k/s on every k-point of each cell, L2 flushed before every timed step."""
+    import torch
+    from paper_2412_01695_gb300 import pwk, synth
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for cfg in ((1, 4) if quick else (1, 3, 4)):
+        prob = synth.make_config(cfg)
+        plan = pwk.plan_from_problem(prob, device=dev)
+        row = {"k_points": prob.nk, "bands": prob.nb, "fft": prob.N, "projectors": prob.nkb,
+               "npw_max": prob.npw_max}
+        for name, prec, dt in (("fp32", pwk.PWK_FP32, torch.complex64), ("fp64", pwk.PWK_FP64, torch.complex128)):
+            x = torch.from_numpy(prob.psi).to(dev).to(dt)
+            y = torch.empty_like(x)
+            for _ in range(3):
+                pwk.hpsi_batched(plan, prec, x, y, prob.nb, stream)
+            ts = []
+            for _ in range(10 if name == "fp32" else 3):
+                flush.fill_(1.0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                pwk.hpsi_batched(plan, prec, x, y, prob.nb, stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b) * 1e-3)
+            row[name] = {"band_k_per_s": prob.nk * prob.nb / float(np.mean(ts)), "ms": float(np.mean(ts)) * 1e3}
+        row["launch_shape_fp32"] = list(plan.launch_shape(pwk.PWK_FP32)[:3])
+        plan.close()
+        out[f"cell{cfg}"] = row
+    return out
+
+
 def run_serving(n_jobs=40, rate_hz=200.0):
     """Serving: a seeded Poisson stream of mixed jobs (60% H|psi>, 25% Davidson, 15%
     Sternheimer) on fcc / simple-cubic cells, admitted by HBM footprint into 4 overlapping
@@ -590,6 +623,8 @@ def main():
         eig_mixed = sol.pop("_eig_mixed", None)
         drho_sample = sol.pop("_drho_sample", None)
         res.update(sol)
+        res["other_cells"] = run_other_cells(torch.device("cuda", local_rank), torch.cuda.current_stream(),
+                                             quick=args.quick)
         if not args.no_serving:
             res["serving"] = run_serving(n_jobs=20 if args.quick else 40)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
