@@ -109,6 +109,20 @@ int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threa
  * The two paths round differently (both to FP32 accuracy).  PWK_ERR_INVALID for another value. */
 int pwk_plan_set_projector_path(pwk_plan* plan, int path);
 
+/* Device-side conditions the kernels of a plan recorded since the last clear (bit flags):
+ *   PWK_FLAG_ITEM_SKIPPED  a work-list entry outside the plan was skipped (pwk_hpsi_items)
+ *   PWK_FLAG_WAIT_TIMEOUT  a bounded device-side wait gave up (tensor-core projection): that
+ *                          call's output is not valid; the context and the plan stay usable
+ * Synchronises with the device (a blocking copy of one int); clear != 0 resets the flags. */
+#define PWK_FLAG_ITEM_SKIPPED 1
+#define PWK_FLAG_WAIT_TIMEOUT 2
+int pwk_plan_errors(pwk_plan* plan, int* flags, int clear);
+
+/* Bound on the polls of every device-side wait of the plan's kernels (default 2^24, a few
+ * seconds).  A diagnostic: 0 makes every such wait give up at once, which exercises the error
+ * path above without stalling the device.  PWK_ERR_INVALID for a negative value. */
+int pwk_plan_set_wait_limit(pwk_plan* plan, long long polls);
+
 /* 1 if an N x N x N grid is supported by the fused kernels, else 0. */
 int pwk_supported_grid(int N);
 

@@ -43,7 +43,6 @@ constexpr int kTcN = 32;            // MMA N: 16 projectors, real and imaginary 
 constexpr int kTcMaxProj = 16;
 constexpr int kTcTileB = kTcN * 128;   // bytes of one B tile (32 rows x 128 B)
 constexpr uint32_t kTcTmemCols = 32;
-constexpr long kTcWaitLimit = 1L << 24;   // try_wait polls before a wait gives up
 constexpr int kTcRing = 6;                 // raw blocks in the asynchronous-copy ring
 constexpr int kTcStages = 3;               // hi/lo tile stages (MMAs of kTcStages - 1 blocks in flight)
 
@@ -79,10 +78,11 @@ __device__ __forceinline__ void umma_commit(uint64_t* mbar) {
                : "memory");
 }
 
-// bounded wait for the completion of phase `parity` of an mbarrier; false if it ran out
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// bounded wait for the completion of phase `parity` of an mbarrier (at most `polls` polls);
+// false if it ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long polls) {
   uint32_t done = 0;
-  for (long it = 0; it < kTcWaitLimit && !done; ++it) {
+  for (long long it = 0; it < polls && !done; ++it) {
     asm volatile(
         "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) nl_project_tc_kernel(NlArgs a) 
     for (int b = 0; b < nblk; ++b) {
       const int s = b % kTcStages;
       // stage s is free once the MMAs of block b - kTcStages have completed
-      if (b >= kTcStages && !mbar_wait(&empty[s], (uint32_t)(((b - kTcStages) / kTcStages) & 1))) pfail[b & 1] = 1;
+      if (b >= kTcStages && !mbar_wait(&empty[s], (uint32_t)(((b - kTcStages) / kTcStages) & 1), a.wait_polls)) pfail[b & 1] = 1;
       asm volatile("cp.async.wait_group %0;\n" ::"n"(kTcRing - 2) : "memory");   // own copies of block b landed
       asm volatile("bar.sync 1, %0;\n" ::"n"(kTcProducers) : "memory");         // everyone's; slot b - 1 consumed
       if (pfail[b & 1]) break;   // the same value for every producer
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) nl_project_tc_kernel(NlArgs a) 
 #pragma unroll 1
     for (int b = 0; b < nblk; ++b) {
       const int s = b % kTcStages;
-      if (!mbar_wait(&full[s], (uint32_t)((b / kTcStages) & 1))) {
+      if (!mbar_wait(&full[s], (uint32_t)((b / kTcStages) & 1), a.wait_polls)) {
         failed = 1;
         break;
       }
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 3) nl_project_tc_kernel(NlArgs a) 
   }
   __syncwarp();
   // the last block's commit covers every MMA issued before it
-  if (!failed && nblk > 0 && !mbar_wait(&empty[(nblk - 1) % kTcStages], (uint32_t)(((nblk - 1) / kTcStages) & 1)))
+  if (!failed && nblk > 0 && !mbar_wait(&empty[(nblk - 1) % kTcStages], (uint32_t)(((nblk - 1) / kTcStages) & 1), a.wait_polls))
     failed = 1;
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();

@@ -509,6 +509,7 @@ int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* i
     n.k0 = k0;
     n.err = p->d_err;
     n.tensor_cores = p->projector_path == 1;
+    n.wait_polls = p->wait_polls;
     n.nitems = nblocks;
     n.nvec_in = nvec_in;
     n.nvec_out = nvec_out;
@@ -582,6 +583,29 @@ const char* pwk_strerror(int code) {
 }
 
 size_t pwk_plan_device_bytes(const pwk_plan* p) { return p ? p->bytes : 0; }
+
+int pwk_plan_set_wait_limit(pwk_plan* p, long long polls) {
+  if (p == nullptr || polls < 0) {
+    set_error("null plan or negative poll count");
+    return PWK_ERR_INVALID;
+  }
+  p->wait_polls = polls;
+  return PWK_OK;
+}
+
+int pwk_plan_errors(pwk_plan* p, int* flags, int clear) {
+  if (p == nullptr || flags == nullptr) {
+    set_error("null plan or flags");
+    return PWK_ERR_INVALID;
+  }
+  cudaError_t e = cudaSetDevice(p->device);
+  int v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, p->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && clear) e = cudaMemset(p->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "pwk_plan_errors");
+  *flags = v;
+  return PWK_OK;
+}
 
 int pwk_plan_set_projector_path(pwk_plan* p, int path) {
   if (p == nullptr || path < 0 || path > 1) {

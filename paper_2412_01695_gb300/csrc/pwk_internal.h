@@ -106,6 +106,7 @@ struct pwk_plan {
   pwk::LaunchShape shape[3];     // per precision
   pwk::LaunchShape xshape;       // transfer kernel (complex dv, FP64)
   int projector_path = 0;        // 0: CUDA cores, 1: tensor cores where they apply
+  long long wait_polls = 1LL << 24;   // bound on the polls of each device-side wait
   int* d_err = nullptr;          // device error word (bad work items)
   // accounting
   size_t bytes = 0, budget = 0;
@@ -169,6 +170,7 @@ struct NlArgs {
   void* coef = nullptr;        // [nitems][2][nkb] complex of the arithmetic type
   int* err = nullptr;          // plan error word (bit 2: a tensor-core wait ran out)
   bool tensor_cores = false;   // projections on the tensor cores where they apply
+  long long wait_polls = 1LL << 24;   // bound on the polls of each device-side wait
 };
 int launch_nl(int precision, const NlArgs& a, cudaStream_t st);
 // tensor-core projection (nonlocal_tc.cu): whether it applies to a launch, and the launch

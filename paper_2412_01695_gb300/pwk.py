@@ -17,10 +17,12 @@ LIB_PATH = os.path.join(PKG, "libpwk.so")
 
 PWK_FP64, PWK_FP32, PWK_FP32_C128 = 0, 1, 2
 PRECISIONS = {"fp64": PWK_FP64, "fp32": PWK_FP32, "fp32_c128": PWK_FP32_C128}
+PWK_FLAG_ITEM_SKIPPED, PWK_FLAG_WAIT_TIMEOUT = 1, 2
 
 # every symbol declared in include/pwk.h
 EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
            "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_plan_set_projector_path",
+           "pwk_plan_errors", "pwk_plan_set_wait_limit",
            "pwk_supported_grid",
            "pwk_hpsi_batched", "pwk_hpsi_batched_host", "pwk_hpsi_items", "pwk_plan_set_overlap",
            "pwk_plan_has_overlap",
@@ -52,6 +54,8 @@ def load(path: str = LIB_PATH):
         "pwk_plan_launch_shape": (_I, [_P, _I, _P, _P, _P, _P]),
         "pwk_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
         "pwk_plan_set_projector_path": (_I, [_P, _I]),
+        "pwk_plan_errors": (_I, [_P, ctypes.POINTER(_I), _I]),
+        "pwk_plan_set_wait_limit": (_I, [_P, ctypes.c_longlong]),
         "pwk_supported_grid": (_I, [_I]),
         "pwk_hpsi_batched": (_I, [_P, _I, _P, _P, _I, _P]),
         "pwk_hpsi_batched_host": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P]),
@@ -139,6 +143,16 @@ class Plan:
     def set_projector_path(self, path: int) -> None:
         """pwk_plan_set_projector_path: 0 CUDA cores (default), 1 tensor cores where they apply."""
         _check(load().pwk_plan_set_projector_path(self.handle, path), "pwk_plan_set_projector_path")
+
+    def errors(self, clear: bool = True) -> int:
+        """pwk_plan_errors: the device-side flags (PWK_FLAG_*) recorded since the last clear."""
+        v = _I()
+        _check(load().pwk_plan_errors(self.handle, ctypes.byref(v), 1 if clear else 0), "pwk_plan_errors")
+        return v.value
+
+    def set_wait_limit(self, polls: int) -> None:
+        """pwk_plan_set_wait_limit: bound on the polls of every device-side wait (diagnostic)."""
+        _check(load().pwk_plan_set_wait_limit(self.handle, polls), "pwk_plan_set_wait_limit")
 
     def set_overlap(self, q) -> None:
         """pwk_plan_set_overlap: q host float64 [nkb][nkb] symmetric, or None (S = 1)."""

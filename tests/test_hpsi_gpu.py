@@ -227,3 +227,37 @@ def test_tensor_core_projections_match_cuda_cores_and_oracle(precision, cfg, nks
     d = max(np.linalg.norm(outs[0][ik] - outs[1][ik]) / np.linalg.norm(outs[1][ik]) for ik in range(prob.nk))
     assert d <= 2e-6, d
     plan.close()
+
+
+def test_device_flags_report_skipped_items_and_wait_timeouts():
+    """The plan's device flags: a work-list entry outside the plan is reported as skipped; a
+    tensor-core wait that gives up (every wait bounded to zero polls, so no MMA is ever issued)
+    is reported as a timeout; the plan then works again once the bound is restored."""
+    torch = torch_cuda()
+    from paper_2412_01695_gb300 import pwk
+    prob = synth.make_config(2, k_subset=[0, 7, 99], nb=4)
+    plan = pwk.plan_from_problem(prob)
+    assert plan.errors() == 0
+    x = torch.from_numpy(prob.psi).cuda()
+    y = torch.zeros_like(x)
+    items = torch.tensor([[0, 0, 0], [5, 0, 0]], dtype=torch.int32, device="cuda")   # k = 5 outside
+    pwk.hpsi_items(plan, pwk.PWK_FP64, x, y, items, prob.nb)
+    torch.cuda.synchronize()
+    assert plan.errors() & pwk.PWK_FLAG_ITEM_SKIPPED
+    assert plan.errors() == 0   # cleared by the previous read
+    x32 = x.to(torch.complex64)
+    y32 = torch.zeros_like(x32)
+    plan.set_projector_path(1)
+    plan.set_wait_limit(0)
+    pwk.hpsi_batched(plan, pwk.PWK_FP32, x32, y32, prob.nb)
+    torch.cuda.synchronize()
+    assert plan.errors() & pwk.PWK_FLAG_WAIT_TIMEOUT
+    plan.set_wait_limit(1 << 24)
+    pwk.hpsi_batched(plan, pwk.PWK_FP32, x32, y32, prob.nb)
+    torch.cuda.synchronize()
+    assert plan.errors() == 0
+    ref = oracle_hpsi(prob, psi=x32.cpu().numpy().astype(np.complex128))
+    assert max_rel_err(y32.cpu().numpy().astype(np.complex128), ref, prob) <= TOL32
+    with pytest.raises(pwk.PwkError):
+        plan.set_wait_limit(-1)
+    plan.close()
