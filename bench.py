@@ -420,6 +420,11 @@ def run_solvers(dev, stream, quick=False):
     pd = (eps_q[:, nocc:nocc + 1] - ek > 0).reshape(-1).cpu().numpy()
     sres = {"k_points": nk4, "nocc": nocc, "pairs": int(pd.size), "positive_definite_pairs": int(pd.sum()),
             "min_gap_ry": float((eps_q[:, nocc:nocc + 1] - ek).min().item())}
+    # one untimed solve first: the first call on a pair of plans builds the k -> k+q stick maps
+    # and the solver workspace
+    dpsi = torch.zeros((nk4, nocc, pq.npw_max), dtype=torch.complex128, device=dev)
+    pwk.sternheimer_cg_batched(plan_q, plan_k, pwk.PWK_FP32_C128, psi_k, ek, psi_q, nocc, alpha, dv, dpsi,
+                               1e-10, 500, stream)
     for name, mode in (("mixed", pwk.PWK_FP32_C128), ("fp64", pwk.PWK_FP64)):
         dpsi = torch.zeros((nk4, nocc, pq.npw_max), dtype=torch.complex128, device=dev)
         torch.cuda.synchronize()

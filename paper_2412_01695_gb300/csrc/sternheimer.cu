@@ -114,7 +114,7 @@ __device__ double bsum2(double v, double* red) {
 // inside the mixed-mode CG, whose H part is FP32 as well (the refinement's FP64 residuals
 // use the FP64 form).
 template <typename T>
-__global__ void __launch_bounds__(256) proj_combine_kernel(int nocc, int np, const int* npw,
+__global__ void __launch_bounds__(512) proj_combine_kernel(int nocc, int np, const int* npw,
                                                            const int* active,
                                                            const double2* pm, const double2* py,
                                                            const double2* u, const double2* w,
@@ -453,7 +453,9 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     su = w->su;
   }
   double2* const sx = w->with_s ? w->sx : nullptr;   // S applied to the operand of A
-  proj_combine_kernel<double><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, su, nullptr, w->t,
+  // one warp per valence vector for the projections mu_v (8 to 16 warps)
+  const int pc_threads = 32 * std::min(std::max(nocc, 8), 16);
+  proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, su, nullptr, w->t,
                                               nullptr, 0, nullptr, 0, nullptr, w->b, w->bnorm);
   tkin_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, psi_kq, w->tkin);
   cudaMemsetAsync(w->iters, 0, sizeof(int) * npairs, st);
@@ -472,7 +474,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
       // t = H x (FP64) on every pair, then t = t - eps x + alpha P_v x, r = t - b
       cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
       if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
-      proj_combine_kernel<double><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1,
+      proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1,
                                                   eps_k, 1, alpha, w->t, nullptr);
       residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, eta,
                                               w->r, w->rnorm, w->thr, w->active, w->first, w->counters);
@@ -492,10 +494,10 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
       if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx)))
         return rc;
       if (inner_prec == PWK_FP64)
-        proj_combine_kernel<double><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
+        proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
                                                             w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr);
       else
-        proj_combine_kernel<float><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
+        proj_combine_kernel<float><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
                                                            w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr);
       cg_step_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, w->d, w->t, x, w->r, w->dold,
                                              w->rho, w->rho_old, w->iters, w->counters);
@@ -507,7 +509,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
   {
     cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
     if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
-    proj_combine_kernel<double><<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1, eps_k,
+    proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1, eps_k,
                                                 1, alpha, w->t, nullptr);
     residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, 0.0, w->r,
                                             w->rnorm, w->thr, w->active, w->first, w->counters);
