@@ -116,3 +116,34 @@ def test_fewer_occupied_bands():
     pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv = inp
     rc, x, iters, resid = run_gpu(pk, pq, psi_k, psi_q, eps_k, alpha, dv, "mixed")
     check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid)
+
+
+def test_full_grid_4096k_sampled():
+    """The whole DFPT grid in one call (4096 k-points x 12 bands, the batch bench.py times),
+    inputs from the generator alone: its orthonormal random vectors as the valence states of
+    k and k+q, eps_{k,n} = -20 Ry - 0.1 n Ry (below the spectrum of every H(k+q), so every pair
+    is positive definite whatever the valence states), alpha = 1 Ry.  Every pair reaches the
+    1e-10 target; three sampled pairs match the oracle's dense solution."""
+    ks = list(range(4096))
+    pk = synth.make_config(4, k_subset=ks)
+    pq = synth.make_config(4, k_subset=ks, shift_q=True)
+    psi_k = np.ascontiguousarray(pk.psi[:, :NOCC])
+    psi_q = np.ascontiguousarray(pq.psi[:, :NOCC])
+    eps_k = np.tile(-20.0 - 0.1 * np.arange(NOCC), (pk.nk, 1))
+    alpha = np.ones(pk.nk)
+    dv = synth.dv_for(4)
+    rc, x, iters, resid = run_gpu(pk, pq, psi_k, psi_q, eps_k, alpha, dv, "mixed")
+    assert rc == 0 and resid.max() <= TOL, (rc, resid.max())
+    vt = ham.grid_coefficients(pk.V_r)
+    dvt = ham.grid_coefficients(dv)
+    for i, n in ((0, 0), (2049, 5), (4095, 11)):
+        nkk, nq = pk.npw[i], pq.npw[i]
+        P = psi_q[i, :, :nq]
+        dvpsi = st.dv_psi_dense(pq.miller[i, :nq], pk.miller[i, :nkk], dvt, psi_k[i, :, :nkk])
+        b = st.rhs(dvpsi[n], P)
+        A = st.operator(ham.problem_h(pq, i, vt), P, eps_k[i, n], alpha[i])
+        xr = st.solve_dense(A, b)
+        xg = x[i, n, :nq]
+        assert np.all(x[i, n, nq:] == 0)
+        assert np.linalg.norm(A @ xg - b) <= 1.5 * TOL * np.linalg.norm(b)
+        assert np.linalg.norm(xg - xr) <= 1e-7 * np.linalg.norm(xr)
