@@ -94,3 +94,29 @@ def test_many_pairs_more_than_partial_grids():
     ref = dr.drho(pk, pq, u_k, u_q, du, weights=w)
     out = run_gpu(pk, pq, u_k, u_q, du, w, "fp64")
     assert rel(out, ref) <= 1e-12
+
+
+def test_full_grid_with_weights_on_three_k_points():
+    """All 4096 k-points x 6 bands of the DFPT cell in one call (every pair transformed), with
+    the weights zero except on three k-points: the result must equal the oracle's induced
+    density of those three alone (FP64 bound)."""
+    ks = list(range(4096))
+    nocc = 6
+    pk = synth.make_config(4, k_subset=ks)
+    pq = synth.make_config(4, k_subset=ks, shift_q=True)
+    u_k = np.ascontiguousarray(pk.psi[:, :nocc])
+    u_q = np.ascontiguousarray(pq.psi[:, :nocc])
+    rng = np.random.default_rng(17)
+    du = np.zeros((pq.nk, nocc, pq.npw_max), complex)
+    for i in range(pq.nk):
+        b = pq.npw[i]
+        du[i, :, :b] = rng.normal(size=(nocc, b)) + 1j * rng.normal(size=(nocc, b))
+    sel = [5, 2222, 4090]
+    w = np.zeros(pk.nk)
+    w[sel] = 1.0 / 3.0
+    out = run_gpu(pk, pq, u_k, u_q, du, w, "fp64")
+    sk = synth.make_config(4, k_subset=sel, with_psi=False)
+    sq = synth.make_config(4, k_subset=sel, with_psi=False, shift_q=True)
+    ref = dr.drho(sk, sq, u_k[sel][:, :, :sk.npw_max], u_q[sel][:, :, :sq.npw_max],
+                  du[sel][:, :, :sq.npw_max], weights=w[sel])
+    assert rel(out, ref) <= 1e-12, rel(out, ref)
