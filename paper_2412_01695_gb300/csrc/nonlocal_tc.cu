@@ -370,6 +370,7 @@ int nl_project_tc_applies(int precision, const NlArgs& a) {
   if (precision == PWK_FP64 || a.phase != 0 || a.items != nullptr || a.d_count != nullptr) return 0;
   if (a.nkb < 1 || a.nkb > kTcMaxProj || a.nvec_in != a.nvec_out || a.nvec_in < 1 || a.nvec_in > 128) return 0;
   if (4 * (a.nvec_in + a.nkb) > kTcProducers || a.nitems % a.nvec_in != 0) return 0;
+  if (tc_smem_bytes(a.nvec_in, a.nkb, precision == PWK_FP32 ? 8 : 16) > 227 * 1024) return 0;
   return 1;
 }
 
