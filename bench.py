@@ -131,7 +131,7 @@ def nonlocal_bytes_per_band(prob, elem_bytes: int) -> float:
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum per launch (bytes) of the kernel, from the
-# ncu capture summarised in profiles/fused_window_kernel_hpsi_cfg2_fp32.md (48.4 MB read +
+# ncu capture summarised in profiles/fused_window_kernel_hpsi_fcc512k_20b_fp32.md (48.4 MB read +
 # 6.4 MB written); to be removed once the kernel changes after that capture
 TRAFFIC = {"fused_window_kernel<float,float,24,6>": 54.8e6}
 
