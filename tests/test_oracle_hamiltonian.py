@@ -34,6 +34,18 @@ def test_free_electron_eigenvalues_closed_form():
     assert np.count_nonzero(H - np.diag(np.diag(H))) == 0
 
 
+def test_kinetic_energy_of_named_plane_waves():
+    """|k+G|^2 for named Miller indices at the first MP point against the hand-derived table
+    (Sec. 2.2.1).  G and -G differ there, so |k-G|^2 fails it while the free-electron
+    spectrum above (the sphere mapped onto its inversion) would not."""
+    prob = synth.make_config(1, with_psi=False)
+    unit = 2 * math.pi / 7.5
+    np.testing.assert_allclose(prob.kpts[0], -unit / 4 * np.ones(3), rtol=0, atol=1e-14)
+    rows = np.loadtxt(os.path.join(GOLDEN, "kinetic_fcc_k0_named_g.txt"))
+    g2 = ham.kinetic(prob.kpts[0], rows[:, :3].astype(np.int64), prob.B)
+    np.testing.assert_allclose(g2, unit ** 2 * rows[:, 3] / 16.0, rtol=0, atol=1e-12)
+
+
 def test_free_electron_hpsi_exact(cfg1):
     prob = _free(synth.make_config(1))
     for ik in range(prob.nk):

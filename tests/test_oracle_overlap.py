@@ -176,3 +176,40 @@ def test_s_orthonormal_inputs():
     rng = np.random.default_rng(2)
     X = ov.s_orthonormal(S, rng.normal(size=(5, n)) + 1j * rng.normal(size=(5, n)))
     np.testing.assert_allclose(X.conj() @ S @ X.T, np.eye(5), atol=1e-12)
+
+
+def test_solution_is_the_first_order_eigenvector_change():
+    """First-order perturbation theory for the pencil (H + delta dV, S) with dS = 0 and q = 0:
+    the S-conduction part (1 - P_v S) of d u_n / d delta (central difference of the dense
+    generalized eigenvectors, gauge <u_n(0)|S|u_n(delta)> real) is the solution of the
+    generalized Eq. linear_system.  Fixes the right-hand side's sign and its (1 - S P_v) form."""
+    import scipy.linalg
+    prob, q = _cell1(3)
+    n = prob.npw[0]
+    m = prob.miller[0, :n]
+    H = ham.problem_h(prob, 0)
+    S = ov.overlap_matrix(prob.beta[0][:, :n], q)
+    rng = np.random.default_rng(11)
+    dv_r = rng.normal(size=(prob.N,) * 3)               # any real periodic potential change
+    dvt = ham.grid_coefficients(dv_r)
+    M = ham.local_matrix(m, m, dvt)
+    w, V = scipy.linalg.eigh(H, S)
+    nocc = 4
+    u = V[:, :nocc].T
+    alpha = 0.9
+    dvpsi = st.dv_psi_dense(m, m, dvt, u)
+    gaps = np.minimum(np.diff(w, prepend=-np.inf)[:nocc], np.diff(w)[:nocc])
+    picked = [j for j in range(nocc) if gaps[j] > 1e-3]
+    assert len(picked) >= 2
+    h = 1e-5
+
+    def vec(sign, j):
+        v = scipy.linalg.eigh(H + sign * h * M, S)[1][:, j]
+        ph = np.vdot(u[j], S @ v)
+        return v * (abs(ph) / ph)
+
+    for j in picked:
+        d = (vec(1, j) - vec(-1, j)) / (2 * h)
+        fd = d - u.T @ (u.conj() @ (S @ d))
+        x = np.linalg.solve(ov.operator(H, S, u, w[j], alpha), ov.rhs(dvpsi[j][None, :], S, u)[0])
+        assert np.linalg.norm(fd - x) < 1e-6 * np.linalg.norm(x)

@@ -1,5 +1,6 @@
 """Pins of the Sternheimer / PCG oracle (no GPU): dense LU, closed forms, PCG convergence."""
 import numpy as np
+import scipy.linalg
 
 from oracle import hamiltonian as ham
 from oracle import sternheimer as st
@@ -103,3 +104,40 @@ def test_pcg_reaches_dense_solution():
         assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) < 1e-10
         assert np.linalg.norm(x - xr) / np.linalg.norm(xr) < 1e-8
         assert 2 < it < 2000
+
+
+def _continued_vector(Hd, j, ref, Sd=None):
+    """Eigenvector j of Hd (or of the pencil Hd, Sd), phase fixed so <ref|S|v> is real positive."""
+    _, V = np.linalg.eigh(Hd) if Sd is None else scipy.linalg.eigh(Hd, Sd)
+    v = V[:, j]
+    ph = np.vdot(ref, v if Sd is None else Sd @ v)
+    return v * (abs(ph) / ph)
+
+
+def test_solution_is_the_first_order_eigenvector_change():
+    """First-order perturbation theory: for q = 0 and a real dv, the conduction part of
+    d psi_n / d delta for H + delta dV (central difference of the dense eigenvectors, gauge
+    <psi_n(0)|psi_n(delta)> real) is the solution of Eq. linear_system.  Fixes the sign of its
+    right-hand side and that dV enters as <c|dV|n> and not its conjugate."""
+    pk = synth.make_config(4, k_subset=[2], with_psi=False)
+    n = pk.npw[0]
+    m = pk.miller[0, :n]
+    H = ham.problem_h(pk, 0)
+    dvt = ham.grid_coefficients(np.real(synth.dv_for(4)))
+    M = ham.local_matrix(m, m, dvt)
+    assert np.max(np.abs(M - M.conj().T)) < 1e-14
+    w, V = np.linalg.eigh(H)
+    nocc = 12
+    psi = V[:, :nocc].T
+    alpha = st.alpha_pv(w[:nocc], w[:nocc])
+    dvpsi = st.dv_psi_dense(m, m, dvt, psi)
+    gaps = np.minimum(np.diff(w, prepend=-np.inf)[:nocc], np.diff(w)[:nocc])
+    picked = [j for j in range(nocc) if gaps[j] > 1e-3]
+    assert len(picked) >= 6
+    h = 1e-5
+    for j in picked:
+        vp = _continued_vector(H + h * M, j, psi[j])
+        vm = _continued_vector(H - h * M, j, psi[j])
+        fd = st.project_conduction(psi, ((vp - vm) / (2 * h))[None, :])[0]
+        x = st.solve_dense(st.operator(H, psi, w[j], alpha), st.rhs(dvpsi[j], psi))
+        assert np.linalg.norm(fd - x) < 1e-6 * np.linalg.norm(x)
