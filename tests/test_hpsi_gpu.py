@@ -261,3 +261,30 @@ def test_device_flags_report_skipped_items_and_wait_timeouts():
     with pytest.raises(pwk.PwkError):
         plan.set_wait_limit(-1)
     plan.close()
+
+
+def test_empty_and_invalid_requests():
+    """Degenerate requests through the C ABI: nb = 0 and an unknown precision are errors
+    (PWK_ERR_INVALID, nothing launched); an empty work list is a no-op that leaves the
+    output as it was."""
+    torch = torch_cuda()
+    from paper_2412_01695_gb300 import pwk
+    prob = synth.make_config(1, k_subset=[0, 3], nb=2)
+    plan = pwk.plan_from_problem(prob)
+    x = torch.from_numpy(prob.psi.copy()).cuda()
+    y = torch.full_like(x, 7.0 - 3.0j)
+    empty = torch.empty((prob.nk, 0, prob.npw_max), dtype=torch.complex128, device="cuda")
+    with pytest.raises(pwk.PwkError) as err:
+        pwk.hpsi_batched(plan, pwk.PWK_FP64, empty, empty, 0)
+    assert err.value.code == -1
+    with pytest.raises(pwk.PwkError) as err:
+        pwk.hpsi_batched(plan, 3, x, y, prob.nb)
+    assert err.value.code == -1
+    pwk.hpsi_items(plan, pwk.PWK_FP64, x, y, None, prob.nb)
+    torch.cuda.synchronize()
+    assert bool(torch.all(y == (7.0 - 3.0j)))
+    # the plan still works after the rejected calls
+    pwk.hpsi_batched(plan, pwk.PWK_FP64, x, y, prob.nb)
+    torch.cuda.synchronize()
+    assert max_rel_err(y.cpu().numpy(), oracle_hpsi(prob), prob) <= TOL64
+    plan.close()
