@@ -132,3 +132,12 @@ def test_full_size_cfg2_mixed_sampled():
     check_against_dense(prob, eig, psi, ks=synth.sample_k(prob.nk, 5, seed=3))
     # every k converged to eigenvalues in ascending order
     assert np.all(np.diff(eig, axis=1) >= -1e-12)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_single_band(mode):
+    """nb = 1 (reduced problems of order 1 to 4) on two k-points."""
+    prob = synth.make_config(1, k_subset=[0, 5], nb=1)
+    rc, eig, psi, iters, notc, napply = run_dav(prob, mode)
+    assert rc == 0 and notc.sum() == 0
+    check_against_dense(prob, eig, psi)

@@ -32,7 +32,7 @@ def check(H, S, eig, vec, nev, tol):
         assert np.max(np.linalg.norm(R, axis=0)) < 1e-9 * scale
 
 
-@pytest.mark.parametrize("n,nev", [(8, 8), (48, 12), (160, 40), (97, 31)])
+@pytest.mark.parametrize("n,nev", [(1, 1), (2, 1), (8, 8), (48, 12), (160, 40), (97, 31)])
 def test_random_pairs(n, nev):
     torch = torch_cuda()
     from paper_2412_01695_gb300 import pwk

@@ -147,3 +147,11 @@ def test_full_grid_4096k_sampled():
         assert np.all(x[i, n, nq:] == 0)
         assert np.linalg.norm(A @ xg - b) <= 1.5 * TOL * np.linalg.norm(b)
         assert np.linalg.norm(xg - xr) <= 1e-7 * np.linalg.norm(xr)
+
+
+def test_single_occupied_band():
+    """nocc = 1 (a rank-one valence projector) on two k-points."""
+    inp = make_inputs([3, 3000], nocc=1)
+    pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv = inp
+    rc, x, iters, resid = run_gpu(pk, pq, psi_k, psi_q, eps_k, alpha, dv, "fp64")
+    check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid)
