@@ -10,7 +10,8 @@ Readings of points the paper leaves open (listed with the design notes):
   * the preconditioner denominator x = H_GG - eps_i S_GG is clamped to sign(x) max(|x|, 1e-2 Ry);
   * a band is converged when |eps_i^(n+1) - eps_i^(n)| < eps_th; an optional residual
     bound ||H phi - eps S phi|| < res_tol may be required as well;
-  * a restart keeps the current Ritz vectors (the "restart with {phi^(n+1), eps^(n+1)}" step);
+  * a restart keeps the current Ritz vectors and eigenvalues as the new basis (the restart
+    step of Sec. 2.1);
   * when the preconditioned residual is numerically parallel to its Ritz vector
     (|cos| > 1 - 1e-6, which happens when H is diagonal in the plane-wave basis and the
     diagonal preconditioner is exact), or when the band's previous correction was left out
