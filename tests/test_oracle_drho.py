@@ -103,3 +103,38 @@ def test_linear_in_du_and_antilinear_in_u():
     base = dr.drho(pk, pq, u_k, u_kq, du)
     np.testing.assert_allclose(dr.drho(pk, pq, u_k, u_kq, a * du), a * base, atol=1e-12)
     np.testing.assert_allclose(dr.drho(pk, pq, a * u_k, u_kq, du), np.conj(a) * base, atol=1e-12)
+
+
+def test_first_order_density_change():
+    """At q = 0 with a real dv, the real part of Eq. drho for one k (w = 1) built from the
+    Sternheimer solutions equals d/d delta of the density 2 sum_n |u_n(r)|^2 of the lowest
+    states of H + delta dV (central difference of dense eigenvectors, gauge-free).  The
+    valence-valence and phase terms of d u_n cancel in the sum, which is why P_c du is enough."""
+    from oracle import hamiltonian as ham
+    from oracle import sternheimer as st
+    pk = synth.make_config(4, k_subset=[6], with_psi=False)
+    n = pk.npw[0]
+    m = pk.miller[0, :n]
+    H = ham.problem_h(pk, 0)
+    dvt = ham.grid_coefficients(np.real(synth.dv_for(4)))
+    M = ham.local_matrix(m, m, dvt)
+    w, V = np.linalg.eigh(H)
+    nocc = 6
+    assert w[nocc] - w[nocc - 1] > 1e-2          # the occupied manifold is separated
+    u = V[:, :nocc].T
+    alpha = st.alpha_pv(w[:nocc], w[:nocc])
+    dvpsi = st.dv_psi_dense(m, m, dvt, u)
+    du = np.array([st.solve_dense(st.operator(H, u, w[j], alpha), st.rhs(dvpsi[j], u))
+                   for j in range(nocc)])
+    out = dr.drho(pk, pk, u[None], u[None], du[None], weights=[1.0])
+    E = ham.phase_matrix(m, pk.N)
+    h = 1e-5
+
+    def density(sign):
+        X = np.linalg.eigh(H + sign * h * M)[1][:, :nocc].T
+        return 2.0 * np.sum(np.abs(ham.to_real_space(X, E)) ** 2, axis=0)
+
+    fd = ((density(1) - density(-1)) / (2 * h)).reshape(out.shape)
+    scale = np.max(np.abs(fd))
+    assert scale > 1e-3
+    np.testing.assert_allclose(out.real, fd, rtol=0, atol=1e-6 * scale)
