@@ -27,6 +27,7 @@ def test_reference_arm_prints_the_contract_line():
     assert res["value"] > 0 and res["higher_is_better"] is True
     cb = res["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == res["value"] and cb["cores"] >= 1 and cb["sample"]
+    assert 0 < cb["cores_busy"] <= cb["cores"] + 0.5
     e2e = res["e2e"]
     assert e2e["value"] == res["value"] and e2e["unit"] == res["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
@@ -35,3 +36,14 @@ def test_reference_arm_prints_the_contract_line():
 
 def test_reference_arm_other_ranks_print_nothing():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_cpu_baseline_leg_measures_busy_cores():
+    """The oracle leg of the GPU arm (run here on a small cell, no GPU output to check)."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    from paper_2412_01695_gb300 import synth
+    res, errs = bench.cpu_baseline(synth.make_config(1), None, budget_s=0.5)
+    assert res["kind"] == "oracle" and res["value"] > 0 and errs == []
+    assert 0 < res["cores_busy"] <= res["cores"] + 0.5
