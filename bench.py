@@ -639,6 +639,8 @@ def main():
                                              quick=args.quick)
         if not args.no_serving:
             res["serving"] = run_serving(n_jobs=20 if args.quick else 40)
+    # the CPU-baseline leg (rank 0, N = 1, after every timed region): the oracle timed on the
+    # host cores, and the same oracle checking samples of this run's GPU results
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         gpu_out = out32.cpu().numpy().astype(np.complex128)
         # the oracle runs on the same (FP32-rounded) input the GPU path saw
