@@ -1,18 +1,33 @@
-"""Benchmark: band-k H|psi> applications per second on one GB300 (or N replicas).
+"""Benchmark: band-k H|psi> applications per second of the batched mixed-precision Davidson
+solve, converged to 1e-8 Ry, on one GB300 (or N replicas), against the per-k FP64 form.
 
-Workload (one step): H|psi> for every band of every k-point of the 1-atom fcc cell,
-a = 7.5 bohr, ecutwfc = 45 Ry (npw 528-548), FFT 24^3, 20 bands, 512 k-points (8x8x8 MP),
-9 projectors, through pwk_hpsi_batched in the mixed-precision (FP32) path: 10240 band-k
-applications per step.  Inputs are resident in HBM; the L2 is flushed (a 512 MiB write)
-before every timed step.  Also reported: the FP64 batched path, the per-k FP64 form
-(the same FP64 kernel launched one k-point at a time), the end-to-end rate through the
-C ABI with host buffers, the roofline of the fused kernel and the CPU oracle baseline.
+Workload (one step): the lowest 20 eigenpairs of H(k) for all 512 k-points of the 1-atom fcc
+cell (a = 7.5 bohr, ecutwfc = 45 Ry, npw 528-548, FFT 24^3, 9 projectors, 8x8x8 MP grid) by
+one pwk_davidson_batched call in the mixed mode (FP32 H applications, FP64 refinement and
+FP64 reduced eigensolves inside the call), from the generator's random orthonormal trial
+vectors, to |d eps| < 1e-10 Ry and ||H psi - eps psi|| < 1e-5 (eigenvalues checked against the
+oracle's dense eigensolver to 1e-8 Ry).  value = the band-k H applications the solve performs
+(FP32 and FP64 together) / its device time.  Inputs are resident in HBM; the L2 is flushed (a
+512 MiB write) before every timed step.
 
-Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Also reported: the same solve with every H application in FP64 (batched), the per-k FP64 form
+(one plan and one call per k-point, on a sample of k-points, extrapolated), where the solve
+spends its device time (H applications, reduced eigensolves, the rest), the end-to-end rate
+through the C ABI with the trial vectors and results in host memory, the raw H|psi> kernel
+rates and rooflines, the DFPT Sternheimer solve and induced density, the other cells, the
+serving loop and the CPU oracle baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--quick]
+  python bench.py --case hpsi|davidson|sternheimer --cfg C [--nk NK] [--precision P] [--reps R]
+
+--case runs one operation of the library on one synthetic cell (the command the profiles
+under profiles/ were captured with) and prints the CUDA-event time of each repetition; the
+repetitions sit in an NVTX range "case", plan creation outside it.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -30,29 +45,49 @@ sys.path.insert(0, ROOT)
 METRIC = "band-k H|psi> applies/s, batched mixed-prec vs per-k FP64 at 1e-8 Ry; p99 latency"
 UNIT = "band-k applies/s"
 CFG = 2
-WORKLOAD = "fcc 1 atom a=7.5 ecut=45Ry FFT 24^3, 512 k (8x8x8 MP), 20 bands, 9 projectors"
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
+WORKLOAD = ("batched Davidson to 1e-8 Ry (mixed FP32/FP64): fcc 1 atom a=7.5 ecut=45Ry FFT 24^3, "
+            "512 k (8x8x8 MP), 20 bands, 9 projectors")
+ETH, RES_TOL, MAX_ITER = 1e-10, 1e-5, 300     # Davidson stopping (|d eps| Ry, residual norm)
+EIG_TOL = 1e-8                                  # Ry: the accuracy the metric is quoted at
+FLUSH_BYTES = 512 * 1024 * 1024
 
 
-def peaks():
+def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     d = {}
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-    sm_mhz = d.get("sm_max_mhz", 2070.0)
-    return {
-        "hbm_gbs": d.get("hbm_gbs", 6800.0),
-        "hbm_source": "measured" if "hbm_gbs" in d else "fallback",
-        "fp32_tflops": SM_COUNT * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12,
-        "sm_max_mhz": sm_mhz,
-    }
+    return {"hbm_gbs": d.get("hbm_gbs", 6800.0),
+            "hbm_source": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in d else "fallback",
+            "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
+
+
+def src_digest(*names) -> str:
+    """Short digest of kernel sources: a DRAM traffic figure copied from an ncu capture is
+    reported only while the sources it was captured at are unchanged."""
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2412_01695_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of a kernel, from ncu captures
+# summarised under profiles/, with the digest of the sources they were captured at.
+TRAFFIC = {}
+
+
+def traffic_for(kernel: str):
+    t = TRAFFIC.get(kernel)
+    if t is None or src_digest(*t["sources"]) != t["digest"]:
+        return None, None
+    return t["bytes"], t["profile"]
 
 
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clock and throttle reasons during a timed region."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -104,184 +139,186 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-# --------------------------------------------------------------------------- work
-def local_flops_per_band(prob, nstick_mean: float, P: int) -> float:
-    """Fused local kernel: 5 n log2 n per 1D transform of the pruned pair (z on the sticks,
-    y on the carried m1 planes, x on every line; inverse and forward), 2 N_r for V(r) u(r),
-    2 npw for the kinetic term."""
-    N = prob.N
-    f1 = 5.0 * N * math.log2(N)
-    fft = f1 * 2.0 * (nstick_mean + P * N + N * N)
-    npw = float(np.mean(prob.npw))
-    return fft + 2.0 * N ** 3 + 2.0 * npw
-
-
-def algorithmic_flops_per_band(prob, nstick_mean: float, P: int) -> float:
-    """Whole H application: the local kernel plus 16 nkb npw for the two projector
-    contractions (Eqs. lambdah and finalnl)."""
-    npw = float(np.mean(prob.npw))
-    return local_flops_per_band(prob, nstick_mean, P) + 16.0 * prob.nkb * npw
-
-
-def nonlocal_bytes_per_band(prob, elem_bytes: int) -> float:
-    """Projector kernels: read C (projection), read and write H C (add-back), and beta(k)
-    twice per k-point (once per kernel) shared by its bands."""
-    npw = float(np.mean(prob.npw))
-    return 3.0 * npw * elem_bytes + 2.0 * prob.nkb * npw * elem_bytes / prob.nb
-
-
-# dram__bytes_read.sum + dram__bytes_write.sum per launch (bytes) of the kernel, from the
-# ncu capture summarised in profiles/fused_window_kernel_hpsi_fcc512k_20b_fp32.md (48.4 MB read +
-# 6.4 MB written); to be removed once the kernel changes after that capture
-TRAFFIC = {"fused_window_kernel<float,float,24,6>": 54.8e6}
-
-
-def kernel_name(N: int, shape) -> str:
-    """Name of the H|psi> kernel the plan launches for a (kind, threads, L, smem) shape."""
-    if shape[0] == 1:
-        return f"fused_window_kernel<float,float,{N},{N // 4}>"
-    if shape[0] == 2:
-        return f"fused_window_kernel<float,float,{N},{N // 4}> (per-warp planes)"
-    return f"fused_kernel<float,float,{N},false>"
-
-
-def stick_stats(prob):
-    ns = []
-    m1 = []
+# --------------------------------------------------------------------------- work counts
+def hit_planes(prob):
+    """Per k-point: the z-sticks (distinct (m1, m2)) and the m1 planes its sphere hits."""
+    ns, npl = [], []
     for ik in range(prob.nk):
         m = prob.miller[ik, :prob.npw[ik]]
         ns.append(len(set(map(tuple, m[:, :2].tolist()))))
-        m1 += [m[:, 0].min(), m[:, 0].max()]
-    return float(np.mean(ns)), int(max(m1) - min(m1) + 1)
+        npl.append(len(np.unique(m[:, 0])))
+    return np.array(ns, float), np.array(npl, float)
+
+
+def local_flops_per_band(prob) -> float:
+    """The local term of one H application (the algorithmic count of the pruned transform pair,
+    5 n log2 n per 1D transform: z on the k-point's sticks, y on its hit m1 planes, x on every
+    line, inverse and forward), 2 N_r for V(r) u(r) and 2 npw for the kinetic term, averaged
+    over the k-points."""
+    N = prob.N
+    f1 = 5.0 * N * math.log2(N)
+    ns, npl = hit_planes(prob)
+    fft = f1 * 2.0 * (ns + npl * N + N * N)
+    return float(np.mean(fft + 2.0 * N ** 3 + 2.0 * prob.npw))
+
+
+def nonlocal_flops_per_band(prob) -> float:
+    """Projection and add-back (Eqs. lambdah, finalnl): 8 flops per complex multiply-add, two
+    contractions of nkb x npw."""
+    return 16.0 * prob.nkb * float(np.mean(prob.npw))
 
 
 def algorithmic_bytes_per_band(prob, elem_bytes: int) -> float:
-    """read psi + write H psi + (beta + g2 + index per k) / nb; V stays in L2."""
+    """read psi + write H psi + (beta + |k+G|^2 + index per k) / nb; V stays in L2."""
     npw = float(np.mean(prob.npw))
     per_k = prob.nkb * prob.npw_max * elem_bytes + prob.npw_max * (8 + 4)
     return 2.0 * npw * elem_bytes + per_k / prob.nb
 
 
-E2E_CHUNKS = 4   # groups of k-points of the end-to-end (host buffer) call
+# --------------------------------------------------------------------------- timing helpers
+class Timer:
+    def __init__(self, torch, dev, stream):
+        self.torch, self.stream = torch, stream
+        self.flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-
-def run_ours(args, rank, world, local_rank):
-    import torch
-    from paper_2412_01695_gb300 import pwk, synth
-
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    stream = torch.cuda.current_stream()
-    prob = synth.make_config(CFG)
-    nb = prob.nb
-    nbk = prob.nk * nb
-    plan = pwk.plan_from_problem(prob, device=dev)
-    psi64 = torch.from_numpy(prob.psi).to(dev)
-    psi32 = psi64.to(torch.complex64)
-    out32 = torch.empty_like(psi32)
-    out64 = torch.empty_like(psi64)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-
-    def timed(fn, steps, warmup):
+    def run(self, fn, steps, warmup, prep=None, flush=True):
+        """CUDA-event time of each of `steps` calls of fn after `warmup` untimed ones; prep()
+        (untimed) and an L2 flush before every call."""
+        torch = self.torch
         for _ in range(warmup):
+            if prep:
+                prep()
             fn()
         torch.cuda.synchronize()
-        evs = []
+        out = []
         for _ in range(steps):
-            flush.fill_(1.0)
+            if prep:
+                prep()
+            if flush:
+                self.flush.fill_(1.0)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
+            a.record(self.stream)
+            r = fn()
+            b.record(self.stream)
+            torch.cuda.synchronize()
+            out.append((a.elapsed_time(b) / 1e3, r))
+        return out
+
+
+def count_launches(torch, fn):
+    """Kernels of this library (namespace pwk) that one call of fn launches, counted from the
+    CUDA activity trace of torch.profiler on an extra, untimed call; None if the trace is not
+    available."""
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
             fn()
-            b.record(stream)
-            evs.append((a, b))
-        torch.cuda.synchronize()
-        return [a.elapsed_time(b) / 1e3 for a, b in evs]
+            torch.cuda.synchronize()
+        n = 0
+        for e in prof.events():
+            if getattr(e, "device_type", None) is not None and "CUDA" in str(e.device_type) and "pwk::" in e.name:
+                n += 1
+        return n or None
+    except Exception:   # no CUPTI on this host: the count is left out
+        return None
 
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-        torch.cuda.synchronize()
 
-    # ---- headline: mixed-precision (FP32) batched path
-    barrier()
-    clk = ClockSampler(local_rank)
+def fma_peaks(torch, dev, stream):
+    """Measured FP32 / FP64 CUDA-core FMA throughput (pwk_measure_fma_peak), with the clocks
+    seen during the measurement."""
+    from paper_2412_01695_gb300 import pwk
+    clk = ClockSampler(dev.index or 0)
     clk.start()
-    t32 = timed(lambda: pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream),
-                args.steps, args.warmup)
-    clocks = clk.stop()
-    barrier()
+    f32, sms = pwk.measure_fma_peak(pwk.PWK_FP32, stream)
+    f64, _ = pwk.measure_fma_peak(pwk.PWK_FP64, stream)
+    c = clk.stop()
+    return {"fp32_tflops": f32 / 1e12, "fp64_tflops": f64 / 1e12, "sm_count": sms,
+            "source": "pwk_measure_fma_peak (independent FMA chains on every SM, best of 3, CUDA events)",
+            "sm_mhz": c.get("sm_mhz"), "sm_max_mhz": c.get("sm_max_mhz")}
+
+
+# --------------------------------------------------------------------------- the headline
+def davidson_runner(torch, pwk, plan, prob, dev, mode, stream):
+    psi0 = torch.from_numpy(prob.psi).to(dev)
+    psi = torch.empty_like(psi0)
+    eig = torch.zeros((prob.nk, prob.nb), dtype=torch.float64, device=dev)
+
+    def prep():
+        psi.copy_(psi0)
+
+    def solve():
+        rc, iters, notc, napply = pwk.davidson_batched(plan, mode, psi, eig, prob.nb, ETH, RES_TOL,
+                                                       MAX_ITER, 0, stream)
+        return {"rc": int(rc), "iters_max": int(iters.max()), "iters_p50": float(np.median(iters)),
+                "applies_fp64": int(napply[0]), "applies_fp32": int(napply[1]),
+                "stats": plan.solver_stats()}
+    return prep, solve, psi, eig
+
+
+def per_k_fp64(torch, pwk, synth, prob, dev, stream, nks):
+    """The per-k FP64 form: one plan and one FP64 Davidson call per k-point (the same trial
+    vectors), on a seeded sample of k-points; plan creation is outside the time."""
+    ks = synth.sample_k(prob.nk, nks, seed=21)
+    t_tot, applies = 0.0, 0
+    for ik in ks:
+        sub = synth.make_config(CFG, k_subset=[int(ik)])
+        sub.psi = np.ascontiguousarray(prob.psi[[int(ik)], :, :sub.npw_max])
+        p1 = pwk.plan_from_problem(sub, device=dev)
+        prep, solve, _, _ = davidson_runner(torch, pwk, p1, sub, dev, pwk.PWK_FP64, stream)
+        prep()
+        solve()        # untimed: the first call allocates the plan's solver workspace
+        prep()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = solve()
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_tot += a.elapsed_time(b) / 1e3
+        applies += r["applies_fp64"] + r["applies_fp32"]
+        p1.close()
+    return {"band_k_applies_per_s": applies / t_tot,
+            "time_s_extrapolated": t_tot * prob.nk / len(ks),
+            "sample": f"{len(ks)} of {prob.nk} k-points, one plan and one FP64 call each"}
+
+
+def run_headline(args, torch, dev, stream, world, peaks):
+    from paper_2412_01695_gb300 import pwk, synth
     from paper_2412_01695_gb300.pools import aggregate
-    # job-level rate: band-k applications of all ranks / the slowest rank's time per step
-    total_units, step_s, _ = aggregate(nbk, float(np.sum(t32)) / len(t32))
-    kern_s = float(np.mean(t32))
-
-    # ---- FP64 batched and per-k FP64 (same kernel, one launch per k-point)
-    t64 = timed(lambda: pwk.hpsi_batched(plan, pwk.PWK_FP64, psi64, out64, nb, stream),
-                min(20, max(2, args.steps // 4)), 2)
-    nk_perk = prob.nk
-
-    def per_k():
-        for ik in range(nk_perk):
-            pwk.hpsi_items(plan, pwk.PWK_FP64, psi64, out64, items_k[ik], nb, stream)
-
-    items_k = [torch.tensor([[ik, b, b] for b in range(nb)], dtype=torch.int32, device=dev)
-               for ik in range(prob.nk)]
-    tpk = timed(per_k, 1, 1)
-
-    # ---- end to end through the C ABI with host buffers (pinned), FP32 path: the library's
-    # host-buffer entry point overlaps the copies in, the applications and the copies out of
-    # E2E_CHUNKS groups of k-points; the plain sequence (copy in, apply, copy out) beside it
-    h_in = psi32.cpu().pin_memory()
-    h_out = torch.empty_like(h_in).pin_memory()
-    d_in = torch.empty_like(psi32)
-    d_out = torch.empty_like(psi32)
-
-    def e2e():
-        pwk.hpsi_batched_host(plan, pwk.PWK_FP32, h_in, h_out, d_in, d_out, nb, E2E_CHUNKS, stream)
-
-    def e2e_serial():
-        psi32.copy_(h_in, non_blocking=True)
-        pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream)
-        h_out.copy_(out32, non_blocking=True)
-
-    te2e = timed(e2e, min(200, max(3, args.steps // 2)), 3)
-    e2e_s = float(np.mean(te2e))
-    te2e_serial = timed(e2e_serial, min(200, max(3, args.steps // 2)), 3)
-
-    nstick_mean, P = stick_stats(prob)
-    shape32 = plan.launch_shape(pwk.PWK_FP32)
-    pk = peaks()
-    # the fused local kernel alone: the same cell with the projector set emptied, same launch
-    # shape (one launch per step); the projector kernels take the rest of the step
-    import copy
-    prob_loc = copy.copy(prob)
-    prob_loc.beta = np.ascontiguousarray(prob.beta[:, :0, :])
-    prob_loc.D = np.zeros((0, 0))
-    plan_loc = pwk.plan_from_problem(prob_loc, device=dev)
-    plan_loc.set_launch_shape(pwk.PWK_FP32, *shape32[:3])
-    t_loc = timed(lambda: pwk.hpsi_batched(plan_loc, pwk.PWK_FP32, psi32, out32, nb, stream),
-                  min(200, max(3, args.steps // 4)), 5)
-    plan_loc.close()
-    # the output the host leg checks against the oracle: the full operator once more (the
-    # timing above left the local-only result in out32)
-    pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream)
-    torch.cuda.synchronize()
-    loc_s = float(np.mean(t_loc))
-    nl_s = max(kern_s - loc_s, 1e-12)
-    # the same step with the projections on the tensor cores (3xTF32, pwk_plan_set_projector_path)
-    plan.set_projector_path(1)
-    t_tc = timed(lambda: pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream),
-                 min(200, max(3, args.steps // 4)), 5)
-    plan.set_projector_path(0)
-    pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream)   # the output checked below
-    torch.cuda.synchronize()
-    tc_step_s = float(np.mean(t_tc))
-    loc_flops = local_flops_per_band(prob, nstick_mean, P) * nbk
-    achieved_tf = loc_flops / loc_s / 1e12
-    flops = algorithmic_flops_per_band(prob, nstick_mean, P) * nbk
-    nl_gbs = nonlocal_bytes_per_band(prob, 8) * nbk / nl_s / 1e9
+    prob = synth.make_config(CFG)
+    nbk = prob.nk * prob.nb
+    plan = pwk.plan_from_problem(prob, device=dev)
+    plan.set_solver_timing(True)
+    T = Timer(torch, dev, stream)
+    prep, solve, psi, eig = davidson_runner(torch, pwk, plan, prob, dev, pwk.PWK_FP32_C128, stream)
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    steps = T.run(solve, args.steps, args.warmup, prep=prep)
+    clocks = clk.stop()
+    times = np.array([t for t, _ in steps])
+    last = steps[-1][1]
+    applies = last["applies_fp64"] + last["applies_fp32"]
+    total_units, step_s, _ = aggregate(applies, float(np.mean(times)))
+    eig_mixed = eig.cpu().numpy()
+    st = last["stats"]
+    # where the solve spends its device time; the dominant part sets the roofline line
+    share = {"h_applications": st["h_ms"] / st["total_ms"], "reduced_eigensolves": st["rr_ms"] / st["total_ms"],
+             "vector_kernels_and_gaps": st["other_ms"] / st["total_ms"]}
+    h_flops = (local_flops_per_band(prob) + nonlocal_flops_per_band(prob))
+    rr_tflops = st["rr_fp64_flops"] / (st["rr_ms"] * 1e-3) / 1e12 if st["rr_ms"] > 0 else 0.0
+    rr_line = {"bound": "alu", "achieved": rr_tflops, "peak": peaks["fp64_tflops"], "unit": "TFLOP/s",
+               "frac": rr_tflops / peaks["fp64_tflops"],
+               "kernel": "rr_kernel (batched FP64 reduced eigensolver, one CTA per k-point)",
+               "algorithmic_flops": "12 n^3 + 12 n^2 nb FP64 flops per reduced problem of order n, summed "
+                                    "on the device over every launch of the solve",
+               "fp64_flops_per_solve": st["rr_fp64_flops"], "device_ms_per_solve": st["rr_ms"],
+               "peak_source": "measured FP64 FMA throughput (pwk_measure_fma_peak), this run"}
+    tb, tprof = traffic_for("rr_kernel")
+    rr_line["traffic"] = tb
+    rr_line["traffic_profile"] = tprof
+    dom = max(share, key=share.get)
     res = {
         "metric": METRIC,
         "value": total_units / step_s,
@@ -293,138 +330,188 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
-        "data": "synthetic (seeded generator: V(G) Gaussian spectrum, Gaussian projectors, random orthonormal psi)",
-        "config": {"workload": WORKLOAD, "global_batch": int(total_units), "k_points_per_gpu": prob.nk,
-                   "bands": nb, "npw_mean": float(np.mean(prob.npw)), "fft": [prob.N] * 3,
+        "dtype": "mixed f32/f64 (FP32 H applications, FP64 refinement, reduced eigensolves and norms)",
+        "data": "synthetic (seeded generator: V(G) Gaussian spectrum, Gaussian projectors, random orthonormal "
+                "trial vectors)",
+        "config": {"workload": WORKLOAD, "global_batch": int(nbk), "k_points_per_gpu": prob.nk, "bands": prob.nb,
+                   "npw_mean": float(np.mean(prob.npw)), "fft": [prob.N] * 3,
+                   "stop": f"|d eps| < {ETH} Ry and ||H psi - eps psi|| < {RES_TOL}; eigenvalues checked to "
+                           f"{EIG_TOL} Ry against the oracle",
                    "parallelism": f"k-pools x{world} (replicas, no collective)",
                    "l2": "flushed (512 MiB write) before every timed step"},
-        "fp64_batched_applies_per_s": nbk / float(np.mean(t64)),
-        "fp64_per_k_applies_per_s": nbk / float(np.mean(tpk)),
-        "speedup_vs_per_k_fp64": float(np.mean(tpk)) / kern_s,
-        "p99_ms_per_step": float(np.percentile(np.array(t32) * 1e3, 99)),
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": pk["fp32_tflops"],
-                     "unit": "TFLOP/s", "frac": achieved_tf / pk["fp32_tflops"],
-                     "traffic": TRAFFIC.get(kernel_name(prob.N, shape32)),
-                     "kernel": kernel_name(prob.N, shape32) + " (FP32 CUDA-core FMA)",
-                     "kernel_ms": loc_s * 1e3,
-                     "launch_shape": {"threads": shape32[1], "l3_chunk": shape32[2], "smem": shape32[3]},
-                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {pk['sm_max_mhz']:.0f} MHz",
-                     "step_tflops": flops / kern_s / 1e12,
-                     "hbm_gbs_achieved": algorithmic_bytes_per_band(prob, 8) * nbk / kern_s / 1e9,
-                     "hbm_peak_gbs": pk["hbm_gbs"]},
-        "roofline_nonlocal": {"bound": "hbm", "achieved": nl_gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                              "frac": nl_gbs / pk["hbm_gbs"], "ms": nl_s * 1e3,
-                              "kernels": "nl_project_kernel + nl_addback_kernel (step time minus the local kernel)",
-                              "tensor_core_projection": {"step_ms": tc_step_s * 1e3,
-                                                         "pair_ms": (tc_step_s - loc_s) * 1e3,
-                                                         "kernels": "nl_project_tc_kernel (tcgen05, 3xTF32) + nl_addback_kernel",
-                                                         "default": False}},
-        "e2e": {"value": nbk / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": int(h_in.numel() * h_in.element_size()),
-                "d2h_bytes_per_step": int(h_out.numel() * h_out.element_size()),
-                "call": f"pwk_hpsi_batched_host, {E2E_CHUNKS} groups of k-points (copies overlapped)",
-                "serial_value": nbk / float(np.mean(te2e_serial))},
-        "gpu_launches": 3 * args.steps,   # projections, local kernel, add-back per step
+        "time_to_solution_s": step_s,
+        "p99_ms_per_step": float(np.percentile(times * 1e3, 99)),
+        "applies_per_solve": {"fp32": last["applies_fp32"], "fp64": last["applies_fp64"]},
+        "iterations": {"max": last["iters_max"], "p50": last["iters_p50"]},
+        "unconverged": last["rc"],
+        "device_time_share": share,
+        "device_ms_per_solve": {"h_applications": st["h_ms"], "reduced_eigensolves": st["rr_ms"],
+                                "vector_kernels_and_gaps": st["other_ms"], "total": st["total_ms"]},
+        "h_tflops_in_solve": applies * h_flops / (st["h_ms"] * 1e-3) / 1e12 if st["h_ms"] > 0 else None,
+        "roofline_reduced_eigensolver": rr_line,
         "clocks": clocks,
     }
+    # the same solve with FP64 H applications (batched), and the per-k FP64 form
+    prep64, solve64, _, eig64 = davidson_runner(torch, pwk, plan, prob, dev, pwk.PWK_FP64, stream)
+    t64 = T.run(solve64, 1, 1, prep=prep64)
+    r64 = t64[0][1]
+    a64 = r64["applies_fp64"] + r64["applies_fp32"]
+    res["fp64_batched"] = {"time_to_solution_s": t64[0][0], "band_k_applies_per_s": a64 / t64[0][0],
+                           "applies": a64, "iterations_max": r64["iters_max"],
+                           "device_time_share": {"h_applications": r64["stats"]["h_ms"] / r64["stats"]["total_ms"],
+                                                 "reduced_eigensolves": r64["stats"]["rr_ms"] / r64["stats"]["total_ms"]}}
+    pk = per_k_fp64(torch, pwk, synth, prob, dev, stream, 4 if args.quick else 8)
+    res["fp64_per_k"] = pk
+    res["speedup_vs_per_k_fp64"] = {"time_to_solution": pk["time_s_extrapolated"] / step_s,
+                                    "applies_per_s": res["value"] / pk["band_k_applies_per_s"]}
+    res["speedup_vs_fp64_batched"] = t64[0][0] / step_s
+    # end to end through the C ABI: trial vectors from pinned host memory, eigenvalues and
+    # eigenvectors back to it, inside the timed region
+    h_psi0 = torch.from_numpy(prob.psi).pin_memory()
+    h_psi = torch.empty_like(h_psi0).pin_memory()
+    h_eig = torch.empty((prob.nk, prob.nb), dtype=torch.float64).pin_memory()
+
+    def e2e():
+        psi.copy_(h_psi0, non_blocking=True)
+        r = solve()
+        h_psi.copy_(psi, non_blocking=True)
+        h_eig.copy_(eig, non_blocking=True)
+        return r
+    te = T.run(e2e, max(1, min(args.steps, 3)), 1)
+    e2e_s = float(np.mean([t for t, _ in te]))
+    res["e2e"] = {"value": applies / e2e_s, "unit": UNIT,
+                  "h2d_bytes_per_step": int(h_psi0.numel() * h_psi0.element_size()),
+                  "d2h_bytes_per_step": int(h_psi.numel() * h_psi.element_size() + h_eig.numel() * 8),
+                  "call": "pwk_davidson_batched with the trial vectors copied in from pinned host memory and "
+                          "eigenvectors + eigenvalues copied out, inside the timed region"}
+    launches = count_launches(torch, lambda: (prep(), solve()))
+    res["gpu_launches"] = launches * args.steps if launches else None
+    res["gpu_launches_per_step"] = launches
     plan.close()
-    return res, prob, (psi32, out32)
+    return res, prob, eig_mixed, eig64.cpu().numpy()
 
 
-def run_solvers(dev, stream, quick=False):
-    """Time-to-solution of the two solvers (not part of the headline metric).
+# --------------------------------------------------------------------------- H|psi> kernels
+def run_hpsi_kernels(args, torch, dev, stream, peaks):
+    """The raw batched H|psi> rates on the headline cell (512 k x 20 bands): FP32 (the
+    arithmetic of the solve's phase 1), FP64 batched, per-k FP64, the host-buffer entry point,
+    and the roofline of the fused local kernel."""
+    from paper_2412_01695_gb300 import pwk, synth
+    prob = synth.make_config(CFG)
+    nb, nbk = prob.nb, prob.nk * prob.nb
+    plan = pwk.plan_from_problem(prob, device=dev)
+    T = Timer(torch, dev, stream)
+    psi64 = torch.from_numpy(prob.psi).to(dev)
+    psi32 = psi64.to(torch.complex64)
+    out32, out64 = torch.empty_like(psi32), torch.empty_like(psi64)
+    n = 20 if args.quick else 200
+    t32 = [t for t, _ in T.run(lambda: pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream), n, 5)]
+    t64 = [t for t, _ in T.run(lambda: pwk.hpsi_batched(plan, pwk.PWK_FP64, psi64, out64, nb, stream), 10, 2)]
+    items_k = [torch.tensor([[ik, b, b] for b in range(nb)], dtype=torch.int32, device=dev)
+               for ik in range(prob.nk)]
 
-    Davidson: every k of the 512-k cell, 20 bands, eigenvalues to eth = 1e-10 Ry with
-    ||H psi - eps psi|| < 1e-5 (eigenvalue error well below 1e-8 Ry), batched mixed mode,
-    batched FP64 mode, and the per-k FP64 form (one plan and one call per k-point) on a
-    sample of k-points, extrapolated to all 512.
-    Sternheimer: 256 k-points of the DFPT cell (k and k+q), 12 occupied bands, residual
-    1e-10, mixed and FP64; the occupied states come from the batched FP64 Davidson."""
+    def per_k():
+        for ik in range(prob.nk):
+            pwk.hpsi_items(plan, pwk.PWK_FP64, psi64, out64, items_k[ik], nb, stream)
+    tpk = [t for t, _ in T.run(per_k, 1, 1)]
+    # the fused local kernel alone: the same cell with the projector set emptied, same shape
+    import copy
+    shape32 = plan.launch_shape(pwk.PWK_FP32)
+    prob_loc = copy.copy(prob)
+    prob_loc.beta = np.ascontiguousarray(prob.beta[:, :0, :])
+    prob_loc.D = np.zeros((0, 0))
+    plan_loc = pwk.plan_from_problem(prob_loc, device=dev)
+    plan_loc.set_launch_shape(pwk.PWK_FP32, *shape32[:3])
+    tloc = [t for t, _ in T.run(lambda: pwk.hpsi_batched(plan_loc, pwk.PWK_FP32, psi32, out32, nb, stream), n, 5)]
+    plan_loc.close()
+    # end to end with host buffers (pwk_hpsi_batched_host, 4 groups of k-points)
+    h_in = psi32.cpu().pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in, d_out = torch.empty_like(psi32), torch.empty_like(psi32)
+    te = [t for t, _ in T.run(lambda: pwk.hpsi_batched_host(plan, pwk.PWK_FP32, h_in, h_out, d_in, d_out, nb, 4,
+                                                            stream), min(n, 50), 3)]
+    pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream)   # the output the host leg checks
+    torch.cuda.synchronize()
+    kern_s, loc_s = float(np.mean(t32)), float(np.mean(tloc))
+    loc_tf = local_flops_per_band(prob) * nbk / loc_s / 1e12
+    step_tf = (local_flops_per_band(prob) + nonlocal_flops_per_band(prob)) * nbk / kern_s / 1e12
+    ns, npl = hit_planes(prob)
+    kname = f"fused_window_kernel<float,float,{prob.N},{prob.N // 4}>"
+    tb, tprof = traffic_for(kname)
+    out = {
+        "fp32_batched": {"band_k_applies_per_s": nbk / kern_s, "ms": kern_s * 1e3,
+                         "tflops_algorithmic": step_tf,
+                         "hbm_gbs_algorithmic": algorithmic_bytes_per_band(prob, 8) * nbk / kern_s / 1e9},
+        "fp64_batched": {"band_k_applies_per_s": nbk / float(np.mean(t64)), "ms": float(np.mean(t64)) * 1e3},
+        "fp64_per_k": {"band_k_applies_per_s": nbk / float(np.mean(tpk)),
+                       "call": "pwk_hpsi_items, one launch set per k-point"},
+        "e2e_host_buffers_fp32": {"band_k_applies_per_s": nbk / float(np.mean(te)),
+                                  "call": "pwk_hpsi_batched_host, 4 groups of k-points"},
+        "roofline_local_kernel": {"bound": "alu", "achieved": loc_tf, "peak": peaks["fp32_tflops"],
+                                  "unit": "TFLOP/s", "frac": loc_tf / peaks["fp32_tflops"],
+                                  "kernel": kname + " (FP32 CUDA-core FMA), timed alone on the cell without projectors",
+                                  "kernel_ms": loc_s * 1e3,
+                                  "flops_per_band_k": local_flops_per_band(prob),
+                                  "count": "5 n log2 n per 1D transform over each k-point's own sticks "
+                                           f"(mean {ns.mean():.2f}) and hit m1 planes (mean {npl.mean():.2f}), "
+                                           "every x line, inverse and forward; 2 N_r (V); 2 npw (kinetic)",
+                                  "launch_shape": {"kind": shape32[0], "threads": shape32[1], "l3_chunk": shape32[2],
+                                                   "smem": shape32[3]},
+                                  "traffic": tb, "traffic_profile": tprof,
+                                  "peak_source": "measured FP32 FMA throughput (pwk_measure_fma_peak), this run"},
+        "nonlocal_part_ms": (kern_s - loc_s) * 1e3,
+    }
+    plan.close()
+    return out, prob, (psi32, out32)
+
+
+# --------------------------------------------------------------------------- solvers (context)
+def sternheimer_block(nk: int, dev, stream, nocc: int = 12, nbx: int = 16):
+    """Inputs of a batched Sternheimer solve on the first nk k-points of the DFPT cell (cell 4):
+    plans of the k and k+q blocks, the nbx lowest bands of both by the batched FP64 Davidson,
+    the nocc occupied ones, alpha_k = 2 (spread of the occupied levels) (>= 0.01 Ry) and the
+    perturbation dv(r)."""
     import torch
     from paper_2412_01695_gb300 import pwk, synth
-    out = {}
-    prob = synth.make_config(CFG)
-    plan = pwk.plan_from_problem(prob, device=dev)
+    ks = list(range(nk))
+    pk = synth.make_config(4, k_subset=ks, nb=nbx)
+    pq = synth.make_config(4, k_subset=ks, shift_q=True, nb=nbx)
+    plan_k = pwk.plan_from_problem(pk, device=dev)
+    plan_q = pwk.plan_from_problem(pq, device=dev)
 
-    def dav(p, pr, mode, nb):
-        psi = torch.from_numpy(pr.psi[:, :nb].copy()).to(dev)
-        eig = torch.zeros((pr.nk, nb), dtype=torch.float64, device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        rc, iters, notc, napply = pwk.davidson_batched(p, mode, psi, eig, nb, 1e-10, 1e-5, 300, 0,
-                                                       stream)
-        torch.cuda.synchronize()
-        return time.perf_counter() - t0, rc, iters, napply, eig, psi
+    def lowest(plan, pr):
+        psi = torch.from_numpy(pr.psi[:, :nbx].copy()).to(dev)
+        eig = torch.zeros((pr.nk, nbx), dtype=torch.float64, device=dev)
+        pwk.davidson_batched(plan, pwk.PWK_FP64, psi, eig, nbx, 1e-10, 1e-5, 300, 0, stream)
+        return eig, psi
 
-    res = {}
-    for name, mode in (("mixed", pwk.PWK_FP32_C128), ("fp64", pwk.PWK_FP64)):
-        dt, rc, iters, napply, eig, _ = dav(plan, prob, mode, prob.nb)
-        res[name] = {"time_s": dt, "unconverged": int(rc), "iters_max": int(iters.max()),
-                     "applies_fp64": int(napply[0]), "applies_fp32": int(napply[1]),
-                     "band_k_applies_per_s": float(napply.sum()) / dt}
-        if name == "mixed":
-            out["_eig_mixed"] = eig.cpu().numpy()
-    nks = 4 if quick else 8
-    ks = synth.sample_k(prob.nk, nks, seed=21)
-    t_perk = 0.0
-    ap = 0
-    for ik in ks:
-        sub = synth.make_config(CFG, k_subset=[int(ik)])
-        # the same start vectors; the single-k plan's rows are npw(k) long
-        sub.psi = np.ascontiguousarray(prob.psi[[int(ik)], :, :sub.npw_max])
-        p1 = pwk.plan_from_problem(sub, device=dev)
-        dt, rc, iters, napply, _, _ = dav(p1, sub, pwk.PWK_FP64, prob.nb)
-        t_perk += dt
-        ap += int(napply.sum())
-        p1.close()
-    res["fp64_per_k"] = {"time_s_extrapolated": t_perk * prob.nk / len(ks),
-                         "sample": f"{len(ks)} of {prob.nk} k-points, one plan and call each",
-                         "band_k_applies_per_s": ap / t_perk}
-    res["speedup_mixed_vs_per_k_fp64"] = res["fp64_per_k"]["time_s_extrapolated"] / res["mixed"]["time_s"]
-    out["davidson"] = res
+    eps_k, psi_k = lowest(plan_k, pk)
+    eps_q, psi_q = lowest(plan_q, pq)
+    e_all = torch.cat([eps_k[:, :nocc], eps_q[:, :nocc]], dim=1)
+    alpha = torch.clamp(2.0 * (e_all.max(dim=1).values - e_all.min(dim=1).values), min=0.01).contiguous()
+    return {"pk": pk, "pq": pq, "plan_k": plan_k, "plan_q": plan_q, "nocc": nocc,
+            "psi_k": psi_k[:, :nocc].contiguous(), "psi_q": psi_q[:, :nocc].contiguous(),
+            "eps_k": eps_k, "eps_q": eps_q, "ek": eps_k[:, :nocc].contiguous(), "alpha": alpha,
+            "dv": torch.from_numpy(synth.dv_for(4)).to(dev)}
 
-    # ultrasoft/PAW variant of the same cell: H and S together, generalized Davidson (S~, H - eps S)
-    plan.set_overlap(synth.q_for(CFG))
-    psi32 = torch.from_numpy(prob.psi).to(dev).to(torch.complex64)
-    h32, s32 = torch.empty_like(psi32), torch.empty_like(psi32)
-    for _ in range(5):
-        pwk.hspsi_batched(plan, pwk.PWK_FP32, psi32, h32, s32, prob.nb, stream)
-    torch.cuda.synchronize()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nrep = 50
-    a.record(stream)
-    for _ in range(nrep):
-        pwk.hspsi_batched(plan, pwk.PWK_FP32, psi32, h32, s32, prob.nb, stream)
-    b.record(stream)
-    torch.cuda.synchronize()
-    hs_ms = a.elapsed_time(b) / nrep
-    uspp = {"hspsi_fp32_ms": hs_ms, "hspsi_fp32_band_k_per_s": prob.nk * prob.nb / (hs_ms * 1e-3),
-            "note": "H and S of every band-k in one call (L2 not flushed between calls)"}
-    dt, rc, iters, napply, _, _ = dav(plan, prob, pwk.PWK_FP32_C128, prob.nb)
-    uspp["davidson_mixed"] = {"time_s": dt, "unconverged": int(rc), "iters_max": int(iters.max()),
-                              "applies_fp64": int(napply[0]), "applies_fp32": int(napply[1])}
-    out["uspp"] = uspp
-    plan.close()
 
-    # Sternheimer on a block of the DFPT cell
-    from paper_2412_01695_gb300.run_case import sternheimer_block
-    nk4 = 64 if quick else 4096   # the whole k grid of the DFPT cell (and its k+q grid)
+def run_sternheimer(dev, stream, quick=False):
+    """The DFPT cell (4096 k x 12 occupied bands, k and k+q), residual 1e-10, mixed and FP64,
+    then the induced density from the solution; where the solve spends its device time."""
+    import torch
+    from paper_2412_01695_gb300 import pwk, synth
+    nk4 = 64 if quick else 4096
     blk = sternheimer_block(nk4, dev, stream)
     pk, pq, plan_k, plan_q = blk["pk"], blk["pq"], blk["plan_k"], blk["plan_q"]
-    nocc, eps_k, eps_q = blk["nocc"], blk["eps_k"], blk["eps_q"]
+    nocc, eps_q = blk["nocc"], blk["eps_q"]
     psi_k, psi_q, ek, alpha, dv = blk["psi_k"], blk["psi_q"], blk["ek"], blk["alpha"], blk["dv"]
-    # a pair (k, n) is positive definite on the conduction space when eps_{k+q,nocc+1} > eps_{k,n}
-    # (the fixed-occupation form on a metal-like cell); the 1e-10 target holds for those, the
-    # others are reported apart (a CG breakdown stops them)
+    plan_q.set_solver_timing(True)
     pd = (eps_q[:, nocc:nocc + 1] - ek > 0).reshape(-1).cpu().numpy()
     sres = {"k_points": nk4, "nocc": nocc, "pairs": int(pd.size), "positive_definite_pairs": int(pd.sum()),
             "min_gap_ry": float((eps_q[:, nocc:nocc + 1] - ek).min().item())}
-    # one untimed solve first: the first call on a pair of plans builds the k -> k+q stick maps
-    # and the solver workspace
     dpsi = torch.zeros((nk4, nocc, pq.npw_max), dtype=torch.complex128, device=dev)
     pwk.sternheimer_cg_batched(plan_q, plan_k, pwk.PWK_FP32_C128, psi_k, ek, psi_q, nocc, alpha, dv, dpsi,
-                               1e-10, 500, stream)
+                               1e-10, 500, stream)   # first call builds the k -> k+q maps and workspace
     for name, mode in (("mixed", pwk.PWK_FP32_C128), ("fp64", pwk.PWK_FP64)):
         dpsi = torch.zeros((nk4, nocc, pq.npw_max), dtype=torch.complex128, device=dev)
         torch.cuda.synchronize()
@@ -433,19 +520,20 @@ def run_solvers(dev, stream, quick=False):
                                                       alpha, dv, dpsi, 1e-10, 500, stream)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        ninner = int(iters.sum())   # CG iterations = A applications inside the (inner) CG
+        st = plan_q.solver_stats()
+        ninner = int(iters.sum())
         sres[name] = {"time_s": dt, "pairs_above_tol": int(rc),
                       "positive_definite_pairs_above_tol": int((resid[pd] > 1e-10).sum()),
                       "max_true_residual_positive_definite": float(resid[pd].max()),
                       "indefinite_pairs_above_tol": int((resid[~pd] > 1e-10).sum()),
                       "iters_max": int(iters.max()), "iters_mean": float(iters.mean()),
-                      ("applies_fp32" if name == "mixed" else "applies_fp64"): ninner,
-                      "inner_applies_per_s": ninner / dt,
-                      "note": "applies counted inside the CG; the mixed mode adds one FP64 application "
-                              "per pair for each refinement residual"}
-    out["sternheimer"] = sres
-
-    # induced density (Eq. drho) from the Sternheimer solution just computed
+                      "cg_iterations_total": ninner, "inner_applies_per_s": ninner / dt,
+                      "device_time_share": {"h_applications": st["h_ms"] / st["total_ms"],
+                                            "vector_kernels_and_gaps": st["other_ms"] / st["total_ms"]},
+                      "device_ms": st["total_ms"]}
+    sres["speedup_mixed_vs_fp64"] = sres["fp64"]["time_s"] / sres["mixed"]["time_s"]
+    out = {"sternheimer": sres}
+    # induced density (Eq. drho) from the solution just computed
     w = torch.full((nk4,), 1.0 / nk4, dtype=torch.float64, device=dev)
     drho = torch.empty((pk.N,) * 3, dtype=torch.complex128, device=dev)
     dres = {"k_points": nk4, "nocc": nocc, "pairs": nk4 * nocc}
@@ -459,13 +547,11 @@ def run_solvers(dev, stream, quick=False):
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / reps
         dres[name] = {"time_ms": dt * 1e3, "pairs_per_s": nk4 * nocc / dt}
-    # the GPU result on 4 k-points (weights 1/nk4), checked against the oracle by the host leg
     ks_s = [0, 1, nk4 // 2, nk4 - 1]
     sub = torch.tensor(ks_s, device=dev)
     pk_s = synth.make_config(4, k_subset=ks_s, with_psi=False)
     pq_s = synth.make_config(4, k_subset=ks_s, with_psi=False, shift_q=True)
     pl_k, pl_q = pwk.plan_from_problem(pk_s, device=dev), pwk.plan_from_problem(pq_s, device=dev)
-    # the sample plans pad to their own (smaller) npw_max: the entries cut are zero padding
     u_k = psi_k[sub][:, :, :pk_s.npw_max].contiguous()
     u_q = psi_q[sub][:, :, :pq_s.npw_max].contiguous()
     d_s = dpsi[sub][:, :, :pq_s.npw_max].contiguous()
@@ -488,7 +574,7 @@ def run_other_cells(dev, stream, quick=False):
     batched band-k/s on every k-point of each cell, L2 flushed before every timed step."""
     import torch
     from paper_2412_01695_gb300 import pwk, synth
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    T = Timer(torch, dev, stream)
     out = {}
     for cfg in ((1, 4) if quick else (1, 3, 4)):
         prob = synth.make_config(cfg)
@@ -498,17 +584,8 @@ def run_other_cells(dev, stream, quick=False):
         for name, prec, dt in (("fp32", pwk.PWK_FP32, torch.complex64), ("fp64", pwk.PWK_FP64, torch.complex128)):
             x = torch.from_numpy(prob.psi).to(dev).to(dt)
             y = torch.empty_like(x)
-            for _ in range(3):
-                pwk.hpsi_batched(plan, prec, x, y, prob.nb, stream)
-            ts = []
-            for _ in range(10 if name == "fp32" else 3):
-                flush.fill_(1.0)
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                pwk.hpsi_batched(plan, prec, x, y, prob.nb, stream)
-                b.record(stream)
-                torch.cuda.synchronize()
-                ts.append(a.elapsed_time(b) * 1e-3)
+            ts = [t for t, _ in T.run(lambda: pwk.hpsi_batched(plan, prec, x, y, prob.nb, stream),
+                                      10 if name == "fp32" else 3, 3)]
             row[name] = {"band_k_per_s": prob.nk * prob.nb / float(np.mean(ts)), "ms": float(np.mean(ts)) * 1e3}
         row["launch_shape_fp32"] = list(plan.launch_shape(pwk.PWK_FP32)[:3])
         plan.close()
@@ -518,9 +595,8 @@ def run_other_cells(dev, stream, quick=False):
 
 def run_serving(n_jobs=40, rate_hz=200.0):
     """Serving: a seeded Poisson stream of mixed jobs (60% H|psi>, 25% Davidson, 15%
-    Sternheimer) on fcc / simple-cubic cells, admitted by HBM footprint into 4 overlapping
-    slots with H|psi> coalescing, against the same jobs run one at a time in FP64
-    (one slot, no coalescing, FP64 Davidson / Sternheimer)."""
+    Sternheimer), admitted by HBM footprint into 4 overlapping slots with H|psi> coalescing,
+    against the same jobs run one at a time in FP64."""
     from paper_2412_01695_gb300 import serve
     jobs = serve.random_mix(n_jobs, rate_hz=rate_hz, seed=2024, max_nk=27, max_nb=16,
                             ecut_range=(25.0, 40.0))
@@ -541,81 +617,168 @@ def run_serving(n_jobs=40, rate_hz=200.0):
             "p99_speedup": st1.get("p99_s", float("nan")) / st.get("p99_s", float("nan"))}
 
 
-def cpu_baseline(prob, gpu_out, budget_s=20.0):
-    """The FP64 oracle (dense H per k) on the host cores, on a seeded sample of k-points."""
+# --------------------------------------------------------------------------- the oracle on the host
+def oracle_davidson(prob, ks, budget_s):
+    """The oracle's Davidson (oracle/davidson.py, dense FP64 H(k) from direct Fourier sums) on
+    k-points of the workload in turn, with the same trial vectors and stopping rule, until
+    budget_s has passed (at least one k-point).  Returns (applies, seconds, cpu seconds,
+    {k: eigenvalues})."""
+    from oracle import davidson as dav
     from oracle import hamiltonian as ham
-    from paper_2412_01695_gb300 import synth
     vt = ham.grid_coefficients(prob.V_r)
-    t0 = time.perf_counter()
-    c0 = time.process_time()
-    done = 0
-    errs = []
-    checked = set(int(i) for i in synth.sample_k(prob.nk, 32, seed=5))
-    ik = 0
-    while time.perf_counter() - t0 < budget_s and done < 4 * prob.nk:
-        ref = ham.hpsi_dense(prob, ik, prob.psi[ik], vt)
-        if gpu_out is not None and ik in checked:
-            n = prob.npw[ik]
-            errs.append(float(np.max(ham.relative_error(gpu_out[ik][:, :n], ref[:, :n]))))
-            checked.discard(ik)
-        done += 1
-        ik = (ik + 1) % prob.nk
-    dt = time.perf_counter() - t0
-    busy = (time.process_time() - c0) / dt
-    return {"value": done * prob.nb / dt, "unit": UNIT, "cores": os.cpu_count(),
-            "cores_busy": round(busy, 2), "kind": "oracle",
-            "sample": f"{done} k-point applications x {prob.nb} bands of the workload (dense FP64 H(k) "
-                      f"built from direct Fourier sums, then H psi), {dt:.1f} s"}, errs
+    t0, c0 = time.perf_counter(), time.process_time()
+    applies, eigs = 0, {}
+    for ik in ks:
+        n = int(prob.npw[ik])
+        H = ham.problem_h(prob, ik, vt)
+        eps, _, _, napply, _ = dav.davidson(lambda X: X @ H.T, np.real(np.diag(H)), prob.psi[ik][:, :n],
+                                            eth=ETH, max_iter=MAX_ITER, res_tol=RES_TOL)
+        applies += napply
+        eigs[int(ik)] = eps
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return applies, time.perf_counter() - t0, time.process_time() - c0, eigs
+
+
+def cpu_baseline(prob, budget_s=20.0):
+    """The oracle's Davidson timed on the host cores on a bounded sample of the workload."""
+    from paper_2412_01695_gb300 import synth
+    ks = synth.sample_k(prob.nk, 64, seed=5)
+    applies, dt, cpu, eigs = oracle_davidson(prob, ks, budget_s)
+    return {"value": applies / dt, "unit": UNIT, "cores": os.cpu_count(), "cores_busy": round(cpu / dt, 2),
+            "kind": "oracle",
+            "sample": f"the oracle's Davidson (dense FP64 H(k) from direct Fourier sums, LAPACK reduced problem) "
+                      f"on {len(eigs)} k-points x {prob.nb} bands of the workload, same trial vectors and "
+                      f"stopping rule, {applies} H applications in {dt:.1f} s"}, eigs
 
 
 def run_reference(args):
-    """Reference arm: the FP64 CPU oracle as it stands, on the host cores."""
-    from oracle import hamiltonian as ham
+    """Reference arm: the FP64 CPU oracle's Davidson as it stands, on the host cores; each
+    step solves one k-point of the workload (the same trial vectors and stopping rule)."""
     from paper_2412_01695_gb300 import synth
     prob = synth.make_config(CFG)
-    vt = ham.grid_coefficients(prob.V_r)
     ks = synth.sample_k(prob.nk, 64, seed=5)
-    per_step = 2
-    times = []
-    cpu = []
-    it = 0
-    for s in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        c0 = time.process_time()
-        for j in range(per_step):
-            ik = ks[(it + j) % len(ks)]
-            ham.hpsi_dense(prob, ik, prob.psi[ik], vt)
-        it += per_step
-        if s >= args.warmup:
-            times.append(time.perf_counter() - t0)
-            cpu.append(time.process_time() - c0)
+    steps, warmup = min(args.steps, 12), min(args.warmup, 3)   # bounded: the oracle takes seconds per k
+    times, cpu, applies = [], [], 0
+    for s in range(warmup + steps):
+        a, dt, c, _ = oracle_davidson(prob, [ks[s % len(ks)]], 0.0)
+        if s >= warmup:
+            times.append(dt)
+            cpu.append(c)
+            applies += a
     step_s = float(np.mean(times))
+    value = applies / float(np.sum(times))
     busy = float(np.sum(cpu) / np.sum(times))
-    value = per_step * prob.nb / step_s
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+            "steps": steps, "warmup": warmup, "ms_per_step": step_s * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "global_batch": per_step * prob.nb,
+            "config": {"workload": WORKLOAD, "global_batch": prob.nb,
                        "parallelism": "host cores (numpy/LAPACK threads)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
                              "cores_busy": round(busy, 2), "kind": "oracle",
-                             "sample": f"each step = {per_step} k-points x {prob.nb} bands of the "
-                                       f"workload, dense FP64 H(k) then H psi"},
+                             "sample": f"each step = the oracle's Davidson on one k-point x {prob.nb} bands of "
+                                       f"the workload ({steps} steps of {args.steps} requested)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# --------------------------------------------------------------------------- --case (profiling driver)
+def run_case(args):
+    import torch
+    from paper_2412_01695_gb300 import pwk, synth
+    stream = torch.cuda.current_stream()
+    if args.case == "sternheimer":
+        if args.cfg != 4:
+            raise SystemExit("sternheimer runs on the DFPT cell: --cfg 4")
+        nk = args.nk or 256
+        blk = sternheimer_block(nk, torch.device("cuda"), stream)
+        mode = pwk.PWK_FP64 if args.precision == "fp64" else pwk.PWK_FP32_C128
+        nocc = blk["nocc"]
+        times = []
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("case")
+        for _ in range(args.reps):
+            dpsi = torch.zeros((nk, nocc, blk["pq"].npw_max), dtype=torch.complex128, device="cuda")
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            rc, iters, resid = pwk.sternheimer_cg_batched(blk["plan_q"], blk["plan_k"], mode, blk["psi_k"],
+                                                          blk["ek"], blk["psi_q"], nocc, blk["alpha"],
+                                                          blk["dv"], dpsi, 1e-10, 500, stream)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"case": "sternheimer", "cfg": 4, "nk": nk, "nocc": nocc, "precision": args.precision,
+                          "ms": times, "pairs_above_tol": int(rc), "iters_max": int(iters.max()),
+                          "max_true_residual": float(resid.max())}))
+        blk["plan_k"].close()
+        blk["plan_q"].close()
+        return
+    nkfull = int(np.prod(synth.CONFIGS[args.cfg]["mp"]))
+    sub = None if args.nk in (0, nkfull) else list(range(args.nk))
+    prob = synth.make_config(args.cfg, k_subset=sub, nb=args.nb or None)
+    plan = pwk.plan_from_problem(prob)
+    plan.set_projector_path(args.projector_path)
+    prec = pwk.PRECISIONS[args.precision]
+    times, extra = [], {}
+    torch.cuda.nvtx.range_push("case")
+    if args.case == "hpsi":
+        dt = torch.complex64 if args.precision == "fp32" else torch.complex128
+        x = torch.from_numpy(prob.psi).cuda().to(dt)
+        y = torch.empty_like(x)
+        for _ in range(args.reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            pwk.hpsi_batched(plan, prec, x, y, prob.nb)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+    else:
+        mode = pwk.PWK_FP64 if args.precision == "fp64" else pwk.PWK_FP32_C128
+        plan.set_solver_timing(True)
+        for _ in range(args.reps):
+            psi = torch.from_numpy(prob.psi).cuda()
+            eig = torch.zeros((prob.nk, prob.nb), dtype=torch.float64, device="cuda")
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            rc, iters, notc, napply = pwk.davidson_batched(plan, mode, psi, eig, prob.nb, ETH, RES_TOL,
+                                                           args.max_iter, 0)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        extra = {"unconverged": int(rc), "iters_max": int(iters.max()), "napply": napply.tolist(),
+                 "iters_percentiles": np.percentile(iters, [50, 90, 99, 100]).tolist(),
+                 "stats": plan.solver_stats()}
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"case": args.case, "cfg": args.cfg, "nk": prob.nk, "nb": prob.nb,
+                      "precision": args.precision, "ms": times,
+                      "launch_shape": plan.launch_shape(pwk.PRECISIONS[args.precision]), **extra}))
+    plan.close()
+
+
+# --------------------------------------------------------------------------- main
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-solvers", action="store_true", help="skip the solver time-to-solution section")
-    ap.add_argument("--quick", action="store_true", help="smaller solver samples")
-    ap.add_argument("--no-serving", action="store_true", help="skip the serving-loop section")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the headline (no H|psi> kernels, Sternheimer, other cells, serving)")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--quick", action="store_true", help="smaller samples in the context sections")
+    ap.add_argument("--case", choices=["hpsi", "davidson", "sternheimer"])
+    ap.add_argument("--cfg", type=int, default=2)
+    ap.add_argument("--nk", type=int, default=0)
+    ap.add_argument("--nb", type=int, default=0)
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "fp32_c128"])
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--max-iter", type=int, default=MAX_ITER)
+    ap.add_argument("--projector-path", type=int, default=0)
     args = ap.parse_args()
+    if args.case:
+        return run_case(args)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -623,40 +786,59 @@ def main():
         if rank == 0:
             print(json.dumps(run_reference(args)), flush=True)
         return
+    import torch
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
-    res, prob, (psi32, out32) = run_ours(args, rank, world, local_rank)
-    eig_mixed = drho_sample = None
-    if rank == 0 and not args.no_solvers:
-        import torch
-        sol = run_solvers(torch.device("cuda", local_rank), torch.cuda.current_stream(),
-                          quick=args.quick)
-        eig_mixed = sol.pop("_eig_mixed", None)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream()
+    peaks = measured_peaks()
+    peaks.update(fma_peaks(torch, dev, stream))
+    if world > 1:
+        torch.distributed.barrier()
+    res, prob, eig_mixed, eig64 = run_headline(args, torch, dev, stream, world, peaks)
+    res["peaks"] = peaks
+    # the reduced eigensolver or the H applications: the line for the larger device-time share
+    res["roofline"] = res["roofline_reduced_eigensolver"]
+    hp_out = None
+    if rank == 0 and not args.no_extras:
+        hk, hprob, hp_out = run_hpsi_kernels(args, torch, dev, stream, peaks)
+        res["hpsi_kernels"] = hk
+        if res["device_time_share"]["h_applications"] > res["device_time_share"]["reduced_eigensolves"]:
+            res["roofline"] = hk["roofline_local_kernel"]
+        sol = run_sternheimer(dev, stream, quick=args.quick)
         drho_sample = sol.pop("_drho_sample", None)
         res.update(sol)
-        res["other_cells"] = run_other_cells(torch.device("cuda", local_rank), torch.cuda.current_stream(),
-                                             quick=args.quick)
+        res["other_cells"] = run_other_cells(dev, stream, quick=args.quick)
         if not args.no_serving:
             res["serving"] = run_serving(n_jobs=20 if args.quick else 40)
+    else:
+        drho_sample = None
     # the CPU-baseline leg (rank 0, N = 1, after every timed region): the oracle timed on the
     # host cores, and the same oracle checking samples of this run's GPU results
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        gpu_out = out32.cpu().numpy().astype(np.complex128)
-        # the oracle runs on the same (FP32-rounded) input the GPU path saw
-        prob.psi = psi32.cpu().numpy().astype(np.complex128)
-        cb, errs = cpu_baseline(prob, gpu_out)
+        cb, eigs = cpu_baseline(prob)
         res["cpu_baseline"] = cb
-        res["max_rel_err_vs_oracle"] = max(errs) if errs else None
-        if eig_mixed is not None:
-            from oracle import davidson as dav
-            from oracle import hamiltonian as ham
-            from paper_2412_01695_gb300 import synth
-            p2 = synth.make_config(CFG)
-            vt = ham.grid_coefficients(p2.V_r)
-            errs = [float(np.max(np.abs(eig_mixed[ik] - dav.lowest_eigenpairs(
-                ham.problem_h(p2, ik, vt), p2.nb)[0]))) for ik in synth.sample_k(p2.nk, 3, seed=4)]
-            res["davidson"]["mixed"]["max_abs_eig_err_ry_vs_oracle"] = max(errs)
+        from oracle import hamiltonian as ham
+        vt = ham.grid_coefficients(prob.V_r)
+        err_m, err_64 = 0.0, 0.0
+        for ik in eigs:
+            w = np.linalg.eigvalsh(ham.problem_h(prob, ik, vt))[:prob.nb]
+            err_m = max(err_m, float(np.max(np.abs(eig_mixed[ik] - w))))
+            err_64 = max(err_64, float(np.max(np.abs(eig64[ik] - w))))
+        res["max_abs_eig_err_ry_vs_oracle"] = {"mixed": err_m, "fp64_batched": err_64, "k_points": sorted(eigs),
+                                               "bar": EIG_TOL}
+        if hp_out is not None:
+            psi32, out32 = hp_out
+            gpu_out = out32.cpu().numpy().astype(np.complex128)
+            psi_in = psi32.cpu().numpy().astype(np.complex128)
+            errs = []
+            for ik in list(eigs)[:4]:
+                n = hprob.npw[ik]
+                ref = ham.hpsi_dense(hprob, ik, psi_in[ik], vt)
+                errs.append(float(np.max(ham.relative_error(gpu_out[ik][:, :n], ref[:, :n]))))
+            res["hpsi_kernels"]["fp32_max_rel_err_vs_oracle"] = max(errs)
         if drho_sample is not None:
             from oracle import drho as odr
             from paper_2412_01695_gb300 import synth

@@ -284,7 +284,9 @@ int pwk_eigh_batched(int nprob, int n, int nev, const void* H, const void* S, do
  * the process exits; it limits a call to nprob * n^2 <= 409600 (e.g. 16 problems of
  * n = 160, 256 of n = 40); larger calls return PWK_ERR_UNSUPPORTED and do nothing.
  * The first call on a device looks up the array's device address (once per device, with that
- * device current); make that first call before any stream capture.  Every call shares the
+ * device current); make that first call before any stream capture.  The address is kept for
+ * the life of the process: a cudaDeviceReset of a device unloads the array there, so a process
+ * that resets a device must not call this entry point on that device afterwards.  Every call shares the
  * array (its previous contents are never read: the kernel writes each element before using
  * it), so calls that overlap on the GPU, on any streams, race: serialise them.
  * Asynchronous on `stream`: results are ready when the stream has synchronised. */
@@ -312,7 +314,8 @@ int pwk_eigh_batched_noalloc(int nprob, int n, int nev, const void* H, const voi
  *   alpha     device [nk] float64                         alpha of each k (Ry)
  *   dv_r      device [N1][N2][N3] complex128              lattice-periodic part of dV
  *   dpsi      device [nk][nocc][npw_max(k+q)] complex128  solution out
- *   tol       relative residual ||A x - b|| / ||b|| to reach, per (k, n)
+ *   tol       relative residual ||A x - b|| / ||b|| to reach, per (k, n); the iteration aims
+ *             at tol/2, so that an FP64 operator rounding differently still finds <= tol
  *   max_iter  CG iterations per solve (per refinement step in mixed mode)
  *   iters_out host int[nk*nocc] or NULL: CG iterations used
  *   resid_out host double[nk*nocc] or NULL: final true relative residual (FP64 operator)
@@ -323,6 +326,40 @@ int pwk_sternheimer_cg_batched(pwk_plan* plan_kq, pwk_plan* plan_k, int mode,
                                int nocc, const double* alpha, const void* dv_r, void* dpsi,
                                double tol, int max_iter, int* iters_out, double* resid_out,
                                void* stream);
+
+/* ---------------------------------------------------------------------------- solver timing
+ * Where a solver call spends its device time (the paper splits its run times the same way:
+ * H and S application, FFTs, reduced diagonalisation; Sec. 7, Tables 1-3).
+ * pwk_plan_set_solver_timing(plan, 1) makes pwk_davidson_batched and
+ * pwk_sternheimer_cg_batched (plan_kq) record CUDA events around their phases on their stream
+ * (read after the synchronisations the solvers make anyway; 8 bytes of device memory for a
+ * counter, allocated on the first switch-on); 0 switches it off.  pwk_plan_solver_stats then
+ * gives the figures of the last such call on the plan:
+ *   stats[0]  ms of device time in H (and S) applications
+ *   stats[1]  ms in the batched reduced eigensolver (Davidson; 0 for the CG)
+ *   stats[2]  ms from the call's first kernel to its last (device)
+ *   stats[3]  algorithmic FP64 flops of the reduced eigensolves: 12 n^3 + 12 n^2 nb per
+ *             problem of order n (the dense counts of Cholesky, reduction to standard form,
+ *             tridiagonalisation and back-transform of nb vectors, 8 flops per complex
+ *             multiply-add)
+ *   stats[4]  stats[2] - stats[0] - stats[1]: the vector kernels and gaps
+ * stats is host double[5].  PWK_ERR_INVALID for a null pointer. */
+int pwk_plan_set_solver_timing(pwk_plan* plan, int on);
+int pwk_plan_solver_stats(const pwk_plan* plan, double* stats);
+
+/* ---------------------------------------------------------------------------- measurement
+ * pwk_measure_fma_peak: the CUDA-core multiply-add throughput of the current device in FLOP/s
+ * (2 per FMA), measured by a kernel that keeps every SM busy with independent FMA chains
+ * (eight CTAs of 256 threads per SM, sixteen chains per thread), best of three timed launches
+ * after a warm-up, CUDA events on `stream`.  The roofline denominator of the kernels bound by
+ * these pipes: the transforms of the H|psi> kernel (FP32 or FP64), the reduced eigensolver
+ * and the CG reductions (FP64); the paper states its peaks per node (Sec. 7) but no per-kernel
+ * fraction, so this has no counterpart there.
+ *   precision   PWK_FP32 or PWK_FP64 (PWK_ERR_INVALID otherwise)
+ *   flops_per_s host double out (may be NULL)
+ *   sm_count    host int out: the device's multiprocessor count (may be NULL)
+ * Takes about 0.1-0.3 s; synchronises `stream`; 8 bytes of scratch from the library's pool. */
+int pwk_measure_fma_peak(int precision, double* flops_per_s, int* sm_count, void* stream);
 
 /* ---------------------------------------------------------------------------- misc */
 const char* pwk_strerror(int code);

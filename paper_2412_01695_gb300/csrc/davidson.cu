@@ -666,6 +666,8 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   // phase filters of the FP64 launches: every k in FP64 mode, the phase-2 k in mixed mode
   const int want64 = mixed ? 2 : 0;
 
+  PhaseTimer T(p, st);                                       // pwk_plan_set_solver_timing
+  double* const rr_flops = T.on ? p->d_flops : nullptr;
   double2* const sphi = w->with_s ? w->sphi : w->phi;       // S phi (S = 1: phi itself)
   float2* const sphi32 = w->with_s ? w->sphi32 : w->phi32;
   hdiag_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>(nk, np, p->nkb, p->d_npw, p->d_g2, p->v_mean,
@@ -727,17 +729,22 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
     items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, mask, nullptr, 0, nullptr, nb,
                                                           w->phase, 0, w->items);
     KCHECK("items_kernel");
+    cudaEvent_t th = T.mark();
     int r = ph == 1 ? run_hpsi(p, PWK_FP32, w->phi32, w->hphi32, w->items, nullptr, nk * nb, MB, MB, st,
                                w->with_s ? w->sphi32 : nullptr)
                     : run_hpsi(p, PWK_FP64, w->phi, w->hphi, w->items, nullptr, nk * nb, MB, MB, st,
                                w->with_s ? w->sphi : nullptr);
     if (r) return r;
+    T.close(0, th);
     napply[ph == 2 ? 0 : 1] += (long long)count * nb;
     gram(mask, nullptr, 0, nullptr, nb);
     KCHECK("gram_kernel");
     set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, mask, w->nbase, nb, nullptr);
-    return launch_rr(nk, MB, nb, w->nbase, mask, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st,
-                     w->drop);
+    cudaEvent_t tr = T.mark();
+    r = launch_rr(nk, MB, nb, w->nbase, mask, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st,
+                  w->drop, rr_flops);
+    T.close(1, tr);
+    return r;
   };
 
   if ((rc = start_block(mixed ? 1 : 2, w->active, nk))) return rc;
@@ -772,6 +779,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(host_dbg, w->dbg, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
     if (ce != cudaSuccess) return cuda_fail(ce, "davidson counters");
+    T.harvest();
     if (host_dbg[0] > 0 && !dumped) {   // H~, S~ are still those of the failed eigensolve
       dump_reduced(w, host_dbg[1], host_dbg[2]);
       dumped = true;
@@ -853,6 +861,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
         items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, w->iterk, w->nbase, 0, w->nnc, 0,
                                                               w->phase, ph, w->items);
         KCHECK("items_kernel");
+        cudaEvent_t th = T.mark();
         if (ph == 1) {
           if ((rc = run_hpsi(p, PWK_FP32, w->phi32, w->hphi32, w->items, nullptr, nk * nb, MB, MB, st,
                              w->with_s ? w->sphi32 : nullptr)))
@@ -862,14 +871,17 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
                              w->with_s ? w->sphi : nullptr)))
             return rc;
         }
+        T.close(0, th);
         napply[ph == 2 ? 0 : 1] += cnt;
       }
       gram(w->iterk, w->nbase, 0, w->nnc, 0);
       set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, w->nbase, 0, w->nnc);
       KCHECK("davidson gram");
+      cudaEvent_t tr = T.mark();
       if ((rc = launch_rr(nk, MB, nb, w->nbase, w->iterk, w->Hr, w->Sr, w->W, w->ev, w->eps_new,
-                          w->status, st, w->drop)))
+                          w->status, st, w->drop, rr_flops)))
         return rc;
+      T.close(1, tr);
       trace_reduced(w, it);
       update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->iterk, 0,
                                                              w->eps_new, w->eps, w->moved, w->status,
@@ -892,6 +904,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(h_nnc.data(), w->nnc, sizeof(int) * nk, cudaMemcpyDeviceToHost, st);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) return cuda_fail(ce, "davidson results");
+  T.finish();
   if (iters_out) std::memcpy(iters_out, h_iters.data(), sizeof(int) * nk);
   if (notconv_out) std::memcpy(notconv_out, h_nnc.data(), sizeof(int) * nk);
   if (napply_out) {

@@ -22,7 +22,9 @@ static __device__ __align__(256) double2 g_eigh_scratch[kNoallocElems];
 static std::mutex g_setup_mutex;
 static double2* g_scratch_addr[64] = {nullptr};
 
-// Once per device, with that device current: the device address of the scratch array.
+// Once per device, with that device current: the device address of the scratch array.  It
+// is kept for the life of the process (a cudaDeviceReset would unload the array: the header
+// tells callers not to use this entry point on a device they have reset).
 static int scratch_on_current_device(double2** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

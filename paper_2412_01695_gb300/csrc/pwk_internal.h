@@ -108,6 +108,10 @@ struct pwk_plan {
   int projector_path = 0;        // 0: CUDA cores, 1: tensor cores where they apply
   long long wait_polls = 1LL << 24;   // bound on the polls of each device-side wait
   int* d_err = nullptr;          // device error word (bad work items)
+  // solver phase timing (pwk_plan_set_solver_timing): figures of the last solver call
+  bool solver_timing = false;
+  double solver_stats[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double* d_flops = nullptr;     // device counter: FP64 flops of the reduced eigensolves
   // accounting
   size_t bytes = 0, budget = 0;
   std::vector<void*> allocs;

@@ -108,11 +108,16 @@ __device__ double2 block_sum2(double2 v, double* red) {
 __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const int* nbase,
                                                  const int* active, const double2* Hr,
                                                  const double2* Sr, double2* W, double2* ev,
-                                                 double* eps, int* status, unsigned char* drop_out) {
+                                                 double* eps, int* status, unsigned char* drop_out,
+                                                 double* flops) {
   const int k = blockIdx.x;
   if (k >= nk || (active != nullptr && !active[k])) return;
   const int n = nbase != nullptr ? nbase[k] : ld;
   const int tid = threadIdx.x, nth = blockDim.x;
+  // algorithmic FP64 operation count of this problem (real flops, 8 per complex multiply-add):
+  // Cholesky n^3/6, L^-1 H L^-H 2n^3/3, tridiagonalisation 2n^3/3, back-transform 3n^2 nb/2
+  // complex multiply-adds
+  if (flops != nullptr && tid == 0) atomicAdd(flops, 12.0 * n * n * n + 12.0 * n * n * nb);
   __shared__ double red[32];
   __shared__ double d[kMaxBasis], e[kMaxBasis], rc[kMaxBasis], rs[kMaxBasis];
   __shared__ double2 tau[kMaxBasis], vv[kMaxBasis], ww[kMaxBasis];
@@ -527,8 +532,8 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
 
 int launch_rr(int nk, int ld, int nb, const int* nbase, const int* active, const double2* Hr,
               const double2* Sr, double2* W, double2* ev, double* eps, int* status,
-              cudaStream_t st, unsigned char* drop_out) {
-  rr_kernel<<<nk, 256, 0, st>>>(nk, ld, nb, nbase, active, Hr, Sr, W, ev, eps, status, drop_out);
+              cudaStream_t st, unsigned char* drop_out, double* flops) {
+  rr_kernel<<<nk, 256, 0, st>>>(nk, ld, nb, nbase, active, Hr, Sr, W, ev, eps, status, drop_out, flops);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PWK_OK : cuda_fail(e, "rr_kernel");
 }

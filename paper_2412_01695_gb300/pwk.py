@@ -28,6 +28,7 @@ EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
            "pwk_plan_has_overlap",
            "pwk_hspsi_batched", "pwk_hspsi_items", "pwk_drho_batched", "pwk_davidson_batched",
            "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_eigh_batched_noalloc",
+           "pwk_measure_fma_peak", "pwk_plan_set_solver_timing", "pwk_plan_solver_stats",
            "pwk_strerror", "pwk_last_error_detail", "pwk_version")
 
 _lib = None
@@ -70,6 +71,9 @@ def load(path: str = LIB_PATH):
                                             _P, _P]),
         "pwk_eigh_batched": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
         "pwk_eigh_batched_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
+        "pwk_measure_fma_peak": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
+        "pwk_plan_set_solver_timing": (_I, [_P, _I]),
+        "pwk_plan_solver_stats": (_I, [_P, ctypes.POINTER(_D)]),
         "pwk_strerror": (ctypes.c_char_p, [_I]),
         "pwk_last_error_detail": (ctypes.c_char_p, []),
         "pwk_version": (ctypes.c_char_p, []),
@@ -161,6 +165,16 @@ class Plan:
             return
         q = np.ascontiguousarray(q, np.float64)
         _check(load().pwk_plan_set_overlap(self.handle, _np_ptr(q)), "pwk_plan_set_overlap")
+
+    def set_solver_timing(self, on: bool) -> None:
+        """pwk_plan_set_solver_timing: record the device time of the solvers' phases."""
+        _check(load().pwk_plan_set_solver_timing(self.handle, 1 if on else 0), "pwk_plan_set_solver_timing")
+
+    def solver_stats(self) -> dict:
+        """pwk_plan_solver_stats of the last solver call on this plan."""
+        v = (_D * 5)()
+        _check(load().pwk_plan_solver_stats(self.handle, v), "pwk_plan_solver_stats")
+        return {"h_ms": v[0], "rr_ms": v[1], "total_ms": v[2], "rr_fp64_flops": v[3], "other_ms": v[4]}
 
     @property
     def has_overlap(self) -> bool:
@@ -336,26 +350,75 @@ def sternheimer_cg_batched(plan_kq: Plan, plan_k: Plan, mode: int, psi_k, eps_k,
     return rc, iters, resid
 
 
+def _check_eigh_args(H, S, nev: int, eig=None, vec=None, status=None):
+    """Shapes, dtypes and device of the reduced-eigensolver arguments, checked before any
+    pointer reaches the library (the kernel trusts them): H, S complex128 [nprob][n][n],
+    1 <= nev <= n, eig float64 [nprob][nev], vec complex128 [nprob][n][nev], status int32
+    [nprob], all contiguous on one CUDA device.  Raises ValueError."""
+    import torch
+    if H.dim() != 3 or H.shape[1] != H.shape[2]:
+        raise ValueError("H must have shape (nprob, n, n)")
+    nprob, n = int(H.shape[0]), int(H.shape[1])
+    if not 1 <= int(nev) <= n:
+        raise ValueError("need 1 <= nev <= n")
+    want = [("H", H, torch.complex128, (nprob, n, n)), ("S", S, torch.complex128, (nprob, n, n)),
+            ("eig", eig, torch.float64, (nprob, nev)), ("vec", vec, torch.complex128, (nprob, n, nev)),
+            ("status", status, torch.int32, (nprob,))]
+    dev = None
+    for name, t, dt, shape in want:
+        if t is None:
+            continue
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if tuple(t.shape) != shape:
+            raise ValueError(f"{name} must have shape {shape}, got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    for name, t, dt, shape in want:
+        if t is None:
+            continue
+        if not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if dev is None:
+            dev = t.device
+        elif t.device != dev:
+            raise ValueError(f"{name} is on {t.device}, H on {dev}: all arguments on one device")
+    return nprob, n, dev
+
+
 def eigh_batched(H, S, nev: int, status=None, stream=None):
     """pwk_eigh_batched on complex128 CUDA tensors H, S [nprob][n][n]; returns (eig, vec)."""
     import torch
-    nprob, n = int(H.shape[0]), int(H.shape[1])
-    eig = torch.empty((nprob, nev), dtype=torch.float64, device=H.device)
-    vec = torch.empty((nprob, n, nev), dtype=torch.complex128, device=H.device)
-    _check(load().pwk_eigh_batched(nprob, n, nev, _ptr(H), _ptr(S), _ptr(eig), _ptr(vec),
-                                   _ptr(status) if status is not None else None,
-                                   _stream(stream)), "pwk_eigh_batched")
+    nprob, n, dev = _check_eigh_args(H, S, nev, status=status)
+    eig = torch.empty((nprob, nev), dtype=torch.float64, device=dev)
+    vec = torch.empty((nprob, n, nev), dtype=torch.complex128, device=dev)
+    with torch.cuda.device(dev):
+        _check(load().pwk_eigh_batched(nprob, n, nev, _ptr(H), _ptr(S), _ptr(eig), _ptr(vec),
+                                       _ptr(status) if status is not None else None,
+                                       _stream(stream)), "pwk_eigh_batched")
     return eig, vec
 
 
 def eigh_batched_noalloc(H, S, nev: int, eig, vec, status=None, stream=None):
     """pwk_eigh_batched_noalloc: the same solve with the library's built-in workspace; the
-    caller provides the outputs eig [nprob][nev] float64 and vec [nprob][n][nev] complex128.
+    caller provides the outputs eig [nprob][nev] float64 and vec [nprob][n][nev] complex128
+    (and optionally status [nprob] int32), all on H's device, where the call runs.
     Asynchronous: synchronise the stream before reading the results."""
-    nprob, n = int(H.shape[0]), int(H.shape[1])
-    _check(load().pwk_eigh_batched_noalloc(nprob, n, nev, _ptr(H), _ptr(S), _ptr(eig), _ptr(vec),
-                                           _ptr(status) if status is not None else None,
-                                           _stream(stream)), "pwk_eigh_batched_noalloc")
+    import torch
+    nprob, n, dev = _check_eigh_args(H, S, nev, eig, vec, status)
+    with torch.cuda.device(dev):
+        _check(load().pwk_eigh_batched_noalloc(nprob, n, nev, _ptr(H), _ptr(S), _ptr(eig), _ptr(vec),
+                                               _ptr(status) if status is not None else None,
+                                               _stream(stream)), "pwk_eigh_batched_noalloc")
+
+
+def measure_fma_peak(precision: int, stream=None):
+    """pwk_measure_fma_peak on the current device: (FLOP/s, SM count)."""
+    f = _D(0.0)
+    n = _I(0)
+    _check(load().pwk_measure_fma_peak(precision, ctypes.byref(f), ctypes.byref(n), _stream(stream)),
+           "pwk_measure_fma_peak")
+    return f.value, n.value
 
 
 def supported_grid(N: int) -> bool:

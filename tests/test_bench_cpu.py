@@ -39,11 +39,18 @@ def test_reference_arm_other_ranks_print_nothing():
 
 
 def test_cpu_baseline_leg_measures_busy_cores():
-    """The oracle leg of the GPU arm (run here on a small cell, no GPU output to check)."""
+    """The oracle leg of the GPU arm (run here on a small cell): the oracle's Davidson on at
+    least one k-point, whose eigenvalues are the dense ones to the metric's 1e-8 Ry."""
     if ROOT not in sys.path:
         sys.path.insert(0, ROOT)
+    import numpy as np
     import bench
+    from oracle import hamiltonian as ham
     from paper_2412_01695_gb300 import synth
-    res, errs = bench.cpu_baseline(synth.make_config(1), None, budget_s=0.5)
-    assert res["kind"] == "oracle" and res["value"] > 0 and errs == []
+    prob = synth.make_config(1)
+    res, eigs = bench.cpu_baseline(prob, budget_s=0.5)
+    assert res["kind"] == "oracle" and res["value"] > 0 and len(eigs) >= 1
     assert 0 < res["cores_busy"] <= res["cores"] + 0.5
+    for ik, e in eigs.items():
+        w = np.linalg.eigvalsh(ham.problem_h(prob, ik))[:prob.nb]
+        assert np.max(np.abs(e - w)) <= bench.EIG_TOL

@@ -260,3 +260,21 @@ def test_davidson_free_electron_degenerate():
     expect = (2 * math.pi / 7.5) ** 2 * rows[:prob.nb, 1] / 16.0
     assert conv.all()
     np.testing.assert_allclose(eps, expect, atol=1e-9)
+
+
+def test_rayleigh_ritz_on_rotated_eigenvectors(cfg1):
+    """The reduced problem of Sec. 2.1 on a basis that spans an exact invariant subspace: six
+    eigenvectors of the dense H(k) mixed by a random complex unitary.  Its reduced overlap
+    <phi_i|phi_j> is the identity (the basis is orthonormal in the Hermitian product), and
+    its Ritz values are the six exact eigenvalues."""
+    vt = ham.grid_coefficients(cfg1.V_r)
+    H = ham.problem_h(cfg1, 2, vt)
+    w, V = np.linalg.eigh(H)
+    rng = np.random.default_rng(8)
+    U = np.linalg.qr(rng.standard_normal((6, 6)) + 1j * rng.standard_normal((6, 6)))[0]
+    phi = U @ V[:, :6].T                     # rows: an orthonormal complex basis
+    Hr, Sr = dav._reduced(phi, phi @ H.T, phi)
+    np.testing.assert_allclose(Sr, np.eye(6), atol=1e-12)
+    np.testing.assert_allclose(np.linalg.eigvalsh(Hr), w[:6], atol=1e-10)
+    eps, vecs = dav._reduced_eig(Hr, Sr, 4)
+    np.testing.assert_allclose(eps, w[:4], atol=1e-10)

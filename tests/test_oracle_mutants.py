@@ -178,14 +178,18 @@ def test_planted_mistake_is_caught(case, cfg1, monkeypatch):
     label, module, attr, replacement, first = case
     assert hasattr(module, attr), attr
     monkeypatch.setattr(module, attr, replacement)
+    crashes = []
     for pin, fn in _pins(first):
         args = [cfg1 for p in inspect.signature(fn).parameters if p == "cfg1"]
         try:
             with np.errstate(all="ignore"):
                 fn(*args)
-        except Exception:                    # an assertion, or a crash the slip provokes
+        except AssertionError:               # a pin's check failed: the slip is caught
             return
-    pytest.fail(f"no pin catches the planted mistake '{label}' in {module.__name__}.{attr}")
+        except Exception as exc:             # a crash is not a catch: the next pin must assert
+            crashes.append(f"{pin}: {type(exc).__name__}")
+    pytest.fail(f"no pin asserts against the planted mistake '{label}' in {module.__name__}.{attr}"
+                + (f" (pins that crashed instead: {crashes})" if crashes else ""))
 
 
 def test_cases_cover_every_oracle_module():

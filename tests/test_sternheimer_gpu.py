@@ -5,7 +5,10 @@ eigenpairs of the dense FP64 H(k), H(k+q) (numpy eigh), alpha follows the oracle
 dv(r) comes from the seeded generator.  The bar: the true relative residual
 ||A x - b|| / ||b|| <= 1e-10 (recomputed here with the oracle's dense operator) for every
 (k, n) pair that is positive definite on the conduction space, and x within 1e-7 of the
-dense LU solution.
+dense LU solution.  Pairs that are not positive definite (the fixed-occupation form on a
+metal-like cell, where eps_{k+q,nocc+1} < eps_{k,n}) are checked apart: where the CG reached
+the target, x matches the dense LU solution; where it broke down or stopped above the target,
+the call counts the pair and reports its residual as the oracle recomputes it.
 """
 import numpy as np
 import pytest
@@ -64,10 +67,11 @@ def run_gpu(pk, pq, psi_k, psi_q, eps_k, alpha, dv, mode, tol=TOL, max_iter=400)
     return rc, out, iters, resid
 
 
-def check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid):
+def check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid, rc=None,
+          want_indefinite=False):
     dvt = ham.grid_coefficients(dv)
     nocc = psi_k.shape[1]
-    worst_res, worst_x, n_pd = 0.0, 0.0, 0
+    worst_res, worst_x, n_pd, n_ind, above = 0.0, 0.0, 0, 0, 0
     for i in range(pk.nk):
         nkk, nq = pk.npw[i], pq.npw[i]
         P = psi_q[i, :, :nq]
@@ -80,15 +84,24 @@ def check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid):
             assert np.all(x[i, n, nq:] == 0)
             rel = np.linalg.norm(A @ xg - b) / np.linalg.norm(b)
             pd = eps_q_all[i][nocc] - eps_k[i, n] > 0
+            # the GPU's own final residual agrees with the oracle's
+            assert abs(resid[i * nocc + n] - rel) < 1e-11 + 0.05 * rel
+            above += resid[i * nocc + n] > TOL
             if pd:
                 n_pd += 1
                 worst_res = max(worst_res, rel)
                 worst_x = max(worst_x, np.linalg.norm(xg - xr) / np.linalg.norm(xr))
-                # the GPU's own final residual agrees with the oracle's
-                assert abs(resid[i * nocc + n] - rel) < 1e-11 + 0.05 * rel
+            else:
+                n_ind += 1
+                if rel <= TOL:   # the CG converged on an indefinite pair: the LU solution
+                    assert np.linalg.norm(xg - xr) <= 1e-7 * np.linalg.norm(xr)
     assert n_pd > 0
-    assert worst_res <= 1.5 * TOL, worst_res
+    assert worst_res <= TOL, worst_res
     assert worst_x <= 1e-7, worst_x
+    if rc is not None:
+        assert rc == above, (rc, above)
+    if want_indefinite:
+        assert n_ind > 0
     return worst_res, worst_x
 
 
@@ -97,8 +110,24 @@ def test_cfg4_subset(mode):
     inp = make_inputs([0, 1, 1234, 4095])
     pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv = inp
     rc, x, iters, resid = run_gpu(pk, pq, psi_k, psi_q, eps_k, alpha, dv, mode)
-    check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid)
+    check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid, rc)
     assert np.all(iters > 0)
+
+
+# Three of the 14 k-points of the 16^3 DFPT grid where the highest occupied band n = 11 lies
+# above eps_{k+q,13} (gaps -0.019, -0.013, -0.0035 Ry), found by the oracle's dense eigensolver
+# over the whole grid; the test re-derives the sign of every gap from the oracle itself.
+INDEFINITE_K = [2282, 939, 410]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_indefinite_pairs_match_lu_or_are_reported(mode):
+    inp = make_inputs(INDEFINITE_K)
+    pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv = inp
+    rc, x, iters, resid = run_gpu(pk, pq, psi_k, psi_q, eps_k, alpha, dv, mode)
+    assert rc >= 0
+    check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid, rc,
+          want_indefinite=True)
 
 
 def test_rhs_zero_gives_zero():
@@ -115,7 +144,7 @@ def test_fewer_occupied_bands():
     inp = make_inputs([10, 2000], nocc=4)
     pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv = inp
     rc, x, iters, resid = run_gpu(pk, pq, psi_k, psi_q, eps_k, alpha, dv, "mixed")
-    check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid)
+    check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid, rc)
 
 
 def test_full_grid_4096k_sampled():
@@ -145,7 +174,7 @@ def test_full_grid_4096k_sampled():
         xr = st.solve_dense(A, b)
         xg = x[i, n, :nq]
         assert np.all(x[i, n, nq:] == 0)
-        assert np.linalg.norm(A @ xg - b) <= 1.5 * TOL * np.linalg.norm(b)
+        assert np.linalg.norm(A @ xg - b) <= TOL * np.linalg.norm(b)
         assert np.linalg.norm(xg - xr) <= 1e-7 * np.linalg.norm(xr)
 
 
@@ -154,4 +183,4 @@ def test_single_occupied_band():
     inp = make_inputs([3, 3000], nocc=1)
     pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv = inp
     rc, x, iters, resid = run_gpu(pk, pq, psi_k, psi_q, eps_k, alpha, dv, "fp64")
-    check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid)
+    check(pk, pq, psi_k, psi_q, eps_k, eps_q_all, Hq_all, alpha, dv, x, resid, rc)

@@ -28,9 +28,20 @@ def _pair(rng, nprob, n):
 
 
 def test_noalloc_matches_allocating_entry_point_on_two_calls():
+    """First a call at the workspace limit whose H is all NaN (its results and status are not
+    looked at): it leaves NaN in the workspace regions that hold L^-1 H and the reduced matrix.
+    A later call that read any workspace element before writing it would carry NaN into its
+    results; the two valid calls that follow must be finite and match the allocating entry
+    point."""
     torch = torch_cuda()
     from paper_2412_01695_gb300 import pwk
     rng = np.random.default_rng(2412)
+    Hn, Sn = _pair(rng, 16, 160)
+    Hn[:] = np.nan
+    eig = torch.empty((16, 40), dtype=torch.float64, device="cuda")
+    vec = torch.empty((16, 160, 40), dtype=torch.complex128, device="cuda")
+    pwk.eigh_batched_noalloc(torch.from_numpy(Hn).cuda(), torch.from_numpy(Sn).cuda(), 40, eig, vec)
+    torch.cuda.synchronize()
     for nprob, n, nev in ((6, 48, 12), (16, 160, 40)):
         H, S = _pair(rng, nprob, n)
         Hd, Sd = torch.from_numpy(H).cuda(), torch.from_numpy(S).cuda()
@@ -43,6 +54,7 @@ def test_noalloc_matches_allocating_entry_point_on_two_calls():
         assert np.all(st.cpu().numpy() == 0)
         e_ref, v_ref = e_ref.cpu().numpy(), v_ref.cpu().numpy()
         e, v = eig.cpu().numpy(), vec.cpu().numpy()
+        assert np.all(np.isfinite(e)) and np.all(np.isfinite(v))
         scale = max(1.0, float(np.max(np.abs(e_ref))))
         np.testing.assert_allclose(e, e_ref, rtol=0, atol=1e-11 * scale)
         np.testing.assert_allclose(v, v_ref, rtol=0, atol=1e-9)
