@@ -236,7 +236,7 @@ def fma_peaks(torch, dev, stream):
     c = clk.stop()
     return {"fp32_tflops": f32 / 1e12, "fp64_tflops": f64 / 1e12, "sm_count": sms,
             "source": "pwk_measure_fma_peak (independent FMA chains on every SM, best of 3, CUDA events)",
-            "sm_mhz": c.get("sm_mhz"), "sm_max_mhz": c.get("sm_max_mhz")}
+            "sm_mhz_during": c.get("sm_mhz")}
 
 
 # --------------------------------------------------------------------------- the headline
@@ -430,6 +430,14 @@ def run_hpsi_kernels(args, torch, dev, stream, peaks):
     d_in, d_out = torch.empty_like(psi32), torch.empty_like(psi32)
     te = [t for t, _ in T.run(lambda: pwk.hpsi_batched_host(plan, pwk.PWK_FP32, h_in, h_out, d_in, d_out, nb, 4,
                                                             stream), min(n, 50), 3)]
+    # each way of applying the projector terms (pwk_plan_set_projector_path), FP32 batched
+    paths = {"automatic_choice": "fused in the local kernel" if plan.projector_fused(pwk.PWK_FP32)
+             else "separate kernels"}
+    for path, name in ((2, "separate_cuda_core_kernels"), (3, "fused_in_local_kernel"), (1, "tensor_core_projection")):
+        plan.set_projector_path(path)
+        tp = [t for t, _ in T.run(lambda: pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream), n, 5)]
+        paths[name] = {"ms": float(np.mean(tp)) * 1e3, "band_k_applies_per_s": nbk / float(np.mean(tp))}
+    plan.set_projector_path(0)
     pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream)   # the output the host leg checks
     torch.cuda.synchronize()
     kern_s, loc_s = float(np.mean(t32)), float(np.mean(tloc))
@@ -460,6 +468,7 @@ def run_hpsi_kernels(args, torch, dev, stream, peaks):
                                   "traffic": tb, "traffic_profile": tprof,
                                   "peak_source": "measured FP32 FMA throughput (pwk_measure_fma_peak), this run"},
         "nonlocal_part_ms": (kern_s - loc_s) * 1e3,
+        "projector_paths_fp32": paths,
     }
     plan.close()
     return out, prob, (psi32, out32)
@@ -588,6 +597,14 @@ def run_other_cells(dev, stream, quick=False):
                                       10 if name == "fp32" else 3, 3)]
             row[name] = {"band_k_per_s": prob.nk * prob.nb / float(np.mean(ts)), "ms": float(np.mean(ts)) * 1e3}
         row["launch_shape_fp32"] = list(plan.launch_shape(pwk.PWK_FP32)[:3])
+        row["projectors_fused_fp32"] = plan.projector_fused(pwk.PWK_FP32)
+        for path in (2, 3):
+            plan.set_projector_path(path)
+            x = torch.from_numpy(prob.psi).to(dev).to(torch.complex64)
+            y = torch.empty_like(x)
+            ts = [t for t, _ in T.run(lambda: pwk.hpsi_batched(plan, pwk.PWK_FP32, x, y, prob.nb, stream), 10, 3)]
+            row[f"fp32_path{path}_ms"] = float(np.mean(ts)) * 1e3
+        plan.set_projector_path(0)
         plan.close()
         out[f"cell{cfg}"] = row
     return out

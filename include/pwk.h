@@ -99,15 +99,27 @@ int pwk_plan_launch_shape(const pwk_plan* plan, int precision, int* kind, int* t
  * memory or the window kernel does not apply to the plan (the shape is then unchanged). */
 int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threads, int l3_chunk);
 
-/* Path of the projections lambda = beta^H C (Eq. lambdah) in FP32 arithmetic:
- *   0 (default)  the CUDA-core kernel (as FP64 and work-list calls always use);
- *   1            the 5th-generation tensor cores wherever they apply (batched calls on whole
- *                k-points, nb + nkb <= 56, nkb <= 16): three TF32 products of a hi/lo split
- *                (FP32-level accuracy), FP32 accumulation in tensor memory.  On the 512-k
- *                cell it is slower than the CUDA-core kernel (about 0.07 against 0.048 ms), hence
- *                not the default.
- * The two paths round differently (both to FP32 accuracy).  PWK_ERR_INVALID for another value. */
+/* How the nonlocal projector terms (Eqs. lambdah, gamma, finalnl; with q also delta_eq,
+ * finals) are applied:
+ *   0 (default)  automatic: path 3 or path 2, whichever pwk_plan_create measured faster for
+ *                each precision on the plan's own k-points (pwk_plan_projector_fused tells);
+ *   1            separate kernels, the projections of FP32 batched calls on whole k-points on
+ *                the 5th-generation tensor cores where they apply (nb + nkb <= 56, nkb <= 16):
+ *                three TF32 products of a hi/lo split (FP32-level accuracy), FP32 accumulation
+ *                in tensor memory; the add-back a CUDA-core kernel;
+ *   2            separate CUDA-core kernels: projections before the local kernel, add-back
+ *                after it, beta(k) staged in shared memory for eight bands at a time;
+ *   3            inside the local kernel, so a band-k item makes one HBM round trip (read C,
+ *                write H C and S C): after the transforms, the local result and C are kept in
+ *                shared memory, beta(k) is staged into the freed buffers, and the projections,
+ *                gamma (delta) and the add-back run from there.
+ * Every path computes the same operator; they round differently (at FP32 or FP64 accuracy).
+ * Path 3 (and 0) falls back to 2 where beta(k) does not fit in shared memory, and the S-only
+ * application (drho) always uses 2.  PWK_ERR_INVALID for another value. */
 int pwk_plan_set_projector_path(pwk_plan* plan, int path);
+/* 1 if H|psi> of this precision applies the projector terms inside the local kernel (path 3,
+ * or path 0 where the plan chose it), else 0; -1 for a null plan or unknown precision. */
+int pwk_plan_projector_fused(const pwk_plan* plan, int precision);
 
 /* Device-side conditions the kernels of a plan recorded since the last clear (bit flags):
  *   PWK_FLAG_ITEM_SKIPPED  a work-list entry outside the plan was skipped (pwk_hpsi_items)

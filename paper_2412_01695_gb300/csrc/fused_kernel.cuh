@@ -26,6 +26,7 @@
 #include <type_traits>
 
 #include "fft_line.cuh"
+#include "nl_fused.cuh"
 #include "pwk_internal.h"
 
 namespace pwk {
@@ -63,7 +64,9 @@ __device__ __forceinline__ int plane_of_slot(int i, int m1lo) {
   return p < 0 ? p + N : (p >= N ? p - N : p);
 }
 
-template <typename T, typename TI, int N, bool CPLXV>
+// NL: the projector terms are applied as well (nl_fused.cuh: projections after the scatter
+// from the staged C, add-back in the gather, beta(k) read through L1/L2); compiled apart.
+template <typename T, typename TI, int N, bool CPLXV, bool NL>
 __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
   using V = c2_t<T>;
   using VI = c2_t<TI>;
@@ -111,7 +114,9 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
   }
   __syncthreads();
 
-  // ---- 1: scatter onto the sticks
+  // ---- 1: scatter onto the sticks; with projectors, lambda = beta^H C
+  constexpr bool nl = !CPLXV && NL;
+  V* nls = reinterpret_cast<V*>(smem_raw + a.nl_off);
   {
     const int* gin = a.gin + (size_t)k * a.npw_in_max;
     for (int g = tid; g < npi; g += nth) {
@@ -119,7 +124,10 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
       Z[(m >> 8) * zs + (m & 255)] = psis[g];
     }
   }
+  const V* nl_bk = nl ? static_cast<const V*>(a.beta) + (size_t)k * a.nkb * a.npw_beta : nullptr;
+  if (nl) nl_fused_project<T>(a, nl_bk, a.npw_beta, psis, npi, nls);
   __syncthreads();
+  if (nl) nl_fused_coef<T>(a, nls);   // read after the barriers that follow
 
   // ---- 2: inverse z transforms on the sticks
   for (int s = tid; s < ns; s += nth) {
@@ -211,6 +219,8 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
     const int* gout = a.gout + (size_t)k * a.npw_out_max;
     const T sc = T(a.scale);
     const double* g2k = a.g2 != nullptr ? a.g2 + (size_t)k * a.npw_out_max : nullptr;
+    const bool with_s = nl && a.sout != nullptr;
+    VI* sout = with_s ? static_cast<VI*>(a.sout) + ((size_t)k * a.nvec_out + vout) * a.npw_out_max : nullptr;
     for (int g = tid; g < npo; g += nth) {
       const int m = gout[g];
       const V z = Z[(m >> 8) * zs + (m & 255)];
@@ -221,20 +231,33 @@ __global__ void __launch_bounds__(256) fused_kernel(FusedArgs a) {
           acc.x += t2 * psis[g].x;
           acc.y += t2 * psis[g].y;
         }
+        if (nl) {   // the in and out spheres are the same here (npi == npo)
+          V h, sv;
+          nl_fused_addback<T>(a, nl_bk, a.npw_beta, g, nls, with_s && a.qm != nullptr, h, sv);
+          acc.x += h.x;
+          acc.y += h.y;
+          if (with_s) {
+            const VI cv = pin[g];
+            sout[g] = a.qm != nullptr ? VI{cv.x + TI(sv.x), cv.y + TI(sv.y)} : cv;
+          }
+        }
       }
       pout[g] = VI{TI(acc.x), TI(acc.y)};
     }
-    for (int g = npo + tid; g < a.npw_out_max; g += nth) pout[g] = VI{TI(0), TI(0)};
+    for (int g = npo + tid; g < a.npw_out_max; g += nth) {
+      pout[g] = VI{TI(0), TI(0)};
+      if (with_s) sout[g] = VI{TI(0), TI(0)};
+    }
   }
 }
 
-template <typename T, typename TI, bool CPLXV>
+template <typename T, typename TI, bool CPLXV, bool NL>
 int launch_fused(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {
   if (nblocks <= 0) return PWK_OK;
   switch (N) {
 #define PWK_CASE(n)                                                                             \
   case n: {                                                                                     \
-    auto kern = fused_kernel<T, TI, n, CPLXV>;                                                  \
+    auto kern = fused_kernel<T, TI, n, CPLXV, NL>;                                                  \
     cudaError_t e = allow_full_smem(kern);                                                      \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");                   \
     kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \

@@ -16,6 +16,7 @@
 
 #include "fft_line.cuh"
 #include "fused_kernel.cuh"
+#include "nl_fused.cuh"
 #include "pwk_internal.h"
 
 namespace pwk {
@@ -39,7 +40,9 @@ struct OutOfWin {
 //         nwarps L) through the y, x and y passes with warp-level synchronisation only; block
 //         barriers remain only around the z passes.  The arithmetic of every line is the same
 //         in both modes (the results are bitwise equal); only the thread mapping differs.
-template <typename T, typename TI, int N, int W, int MODE>
+// NL: the nonlocal projector terms are applied in the epilogue (nl_fused.cuh); the kernel
+//     without them (NL false) is compiled apart, so the projector code costs it nothing.
+template <typename T, typename TI, int N, int W, int MODE, bool NL>
 __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
   using V = c2_t<T>;
   using VI = c2_t<TI>;
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
   __syncthreads();
 
   // ---- 5: gather with 1/N_r; kinetic term
-  {
+  if constexpr (!NL) {
     const int* gout = a.gout + (size_t)k * a.npw_out_max;
     const T sc = T(a.scale);
     const double* g2k = a.g2 + (size_t)k * a.npw_out_max;
@@ -241,20 +244,62 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
       pout[g] = VI{TI(acc.x), TI(acc.y)};
     }
     for (int g = np + tid; g < a.npw_out_max; g += nth) pout[g] = VI{TI(0), TI(0)};
+  } else {
+    // With projectors (nl_fused.cuh): the local result and C go to shared memory past the
+    // stick square; once the square is read, beta(k) is staged over it, and the projections,
+    // gamma (delta) and the add-back (S C) run from shared memory.
+    const int* gout = a.gout + (size_t)k * a.npw_out_max;
+    const T sc = T(a.scale);
+    const double* g2k = a.g2 + (size_t)k * a.npw_out_max;
+    V* LOC = reinterpret_cast<V*>(smem_raw + a.loc_off);   // [npw_out_max] local + kinetic
+    V* Cs = LOC + a.npw_out_max;                             // [npw_out_max] C in T
+    V* nls = reinterpret_cast<V*>(smem_raw + a.nl_off);
+    for (int g = tid; g < np; g += nth) {
+      const int m = gout[g];
+      const V z = Z[(m >> 8) * zs + (m & 255)];
+      const T t2 = T(g2k[g]);
+      const VI cv = pin[g];
+      LOC[g] = V{z.x * sc + t2 * T(cv.x), z.y * sc + t2 * T(cv.y)};
+      Cs[g] = V{T(cv.x), T(cv.y)};
+    }
+    __syncthreads();
+    V* Bs = reinterpret_cast<V*>(smem_raw);                  // [nkb][npw_beta]
+    nl_stage_beta<T>(a, k, Bs);
+    nl_fused_project<T>(a, Bs, a.npw_beta, Cs, np, nls);
+    __syncthreads();
+    nl_fused_coef<T>(a, nls);
+    __syncthreads();
+    const bool with_s = a.sout != nullptr;
+    const bool with_q = with_s && a.qm != nullptr;
+    VI* sout = with_s ? static_cast<VI*>(a.sout) + ((size_t)k * a.nvec_out + vout) * a.npw_out_max : nullptr;
+    for (int g = tid; g < np; g += nth) {
+      V h, sv;
+      nl_fused_addback<T>(a, Bs, a.npw_beta, g, nls, with_q, h, sv);
+      const V l = LOC[g];
+      pout[g] = VI{TI(l.x + h.x), TI(l.y + h.y)};
+      if (with_s) {
+        const VI cv = pin[g];
+        sout[g] = a.qm != nullptr ? VI{cv.x + TI(sv.x), cv.y + TI(sv.y)} : cv;
+      }
+    }
+    for (int g = np + tid; g < a.npw_out_max; g += nth) {
+      pout[g] = VI{TI(0), TI(0)};
+      if (with_s) sout[g] = VI{TI(0), TI(0)};
+    }
   }
 }
 
 // window half-width instantiated for a grid of size N
 __host__ __device__ constexpr int window_of(int N) { return N / 4; }
 
-template <typename T, typename TI>
+template <typename T, typename TI, bool NL>
 int launch_window(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {
   if (nblocks <= 0) return PWK_OK;
   switch (N) {
 #define PWK_WCASE(n)                                                                            \
   case n: {                                                                                     \
-    auto kern = s.kind == 2 ? fused_window_kernel<T, TI, n, window_of(n), 1>                    \
-                            : fused_window_kernel<T, TI, n, window_of(n), 0>;                   \
+    auto kern = s.kind == 2 ? fused_window_kernel<T, TI, n, window_of(n), 1, NL>                \
+                            : fused_window_kernel<T, TI, n, window_of(n), 0, NL>;               \
     cudaError_t e = allow_full_smem(kern);                                                      \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(window)");                  \
     kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \

@@ -3,6 +3,6 @@
 
 namespace pwk {
 int launch_fused_xfer(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {
-  return launch_fused<double, double, true>(N, a, nblocks, s, st);
+  return launch_fused<double, double, true, false>(N, a, nblocks, s, st);
 }
 }  // namespace pwk

@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kNlThreads, sizeof(T) == 4 ? 3 : 2) nl_addback
             const int g = t * kNlTile + lane + 32 * u;
             if (g < np) {
               if (pout != nullptr) pout[g] = VI{TI(T(hv[u].x) + ah[u].x), TI(T(hv[u].y) + ah[u].y)};
-              if (with_s) sout[g] = VI{TI(T(cv[u].x) + as[u].x), TI(T(cv[u].y) + as[u].y)};
+              if (with_s) sout[g] = VI{cv[u].x + TI(as[u].x), cv[u].y + TI(as[u].y)};
             }
           }
         }

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "fft_line.cuh"
+#include "nl_fused.cuh"
 #include "pwk_internal.h"
 #include "solvers.h"
 
@@ -319,19 +320,77 @@ LaunchShape choose_shape(int N, int elem_bytes, const SphereMap& sm, int ctas_pe
   return s;
 }
 
+static NlArgs nl_args(const pwk_plan* p, int precision, const void* in, void* out, void* sout,
+                      const int* items, const int* d_count, int nblocks, int nvec_in, int nvec_out,
+                      int k0);
+
+// Shared-memory layout of the local kernel with the projector terms fused in: the kernel's
+// own buffers, then (window kernels) the gathered local result and C, placed past the stick
+// square; beta(k) is staged at offset 0 once the square has been read; the coefficients
+// (lambda, gamma, delta) last.  Returns the bytes the launch needs; *nl_off, *loc_off get the
+// offsets.
+static size_t fused_layout(const pwk_plan* p, int precision, const LaunchShape& s, int* nl_off, int* loc_off) {
+  const size_t V = precision == PWK_FP64 ? 16 : 8;
+  auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+  size_t R = r16(s.smem);
+  size_t loc = 0;
+  if (s.kind >= 1) {
+    const int N = p->N, NW = 2 * (N / 4) + 1;
+    int zs = 0, yps = 0;
+    window_strides(N, s.L, &zs, &yps);
+    const size_t zb = r16((size_t)NW * NW * zs * V);
+    const size_t lc = r16(2 * (size_t)p->npw_max * V);
+    const size_t bb = r16((size_t)p->nkb * p->npw_max * V);
+    R = std::max(R, std::max(bb, zb) + lc);
+    loc = R - lc;
+  }
+  if (nl_off) *nl_off = (int)R;
+  if (loc_off) *loc_off = (int)loc;
+  return R + nl_fused_bytes(p->nkb, (int)V);
+}
+
+// Whether the projector terms of this precision run inside the local kernel: the plan's
+// choice (set by the autotuner, or forced by pwk_plan_set_projector_path) and room in shared
+// memory.
+static bool nl_fused_fits(const pwk_plan* p, int precision, const LaunchShape& s) {
+  return p->nkb > 0 && fused_layout(p, precision, s, nullptr, nullptr) <= 227 * 1024;
+}
+static bool nl_fused_for(const pwk_plan* p, int precision, const LaunchShape& s) {
+  if (p->projector_path == 3) return nl_fused_fits(p, precision, s);
+  if (p->projector_path != 0) return false;
+  return p->nl_fused[precision] && nl_fused_fits(p, precision, s);
+}
+
+// Point the kernel arguments at the plan's projectors (the precision's copies of beta, D, q)
+// and the shared-memory layout of the fused kernel.
+static void set_fused_nl(const pwk_plan* p, int precision, FusedArgs& a, void* sout, const LaunchShape& s) {
+  const bool f64 = precision == PWK_FP64;
+  a.beta = f64 ? static_cast<const void*>(p->d_beta) : static_cast<const void*>(p->d_beta32);
+  a.Dm = f64 ? static_cast<const void*>(p->d_D) : static_cast<const void*>(p->d_D32);
+  a.qm = f64 ? static_cast<const void*>(p->d_q) : static_cast<const void*>(p->d_q32);
+  a.sout = sout;
+  a.nkb = p->nkb;
+  a.npw_beta = p->npw_max;
+  fused_layout(p, precision, s, &a.nl_off, &a.loc_off);
+}
+
 static int launch_variant(int precision, int N, const FusedArgs& a, int nblocks,
-                          const LaunchShape& s, cudaStream_t st) {
+                          const LaunchShape& s0, cudaStream_t st) {
+  LaunchShape s = s0;
+  if (a.beta != nullptr) s.smem = (size_t)a.nl_off + nl_fused_bytes(a.nkb, precision == PWK_FP64 ? 16 : 8);
+  const bool nl = a.beta != nullptr;
   if (s.kind >= 1) {
     switch (precision) {
-      case PWK_FP64: return launch_window_f64(N, a, nblocks, s, st);
-      case PWK_FP32: return launch_window_f32(N, a, nblocks, s, st);
-      default: return launch_window_f32c128(N, a, nblocks, s, st);
+      case PWK_FP64: return nl ? launch_window_f64_nl(N, a, nblocks, s, st) : launch_window_f64(N, a, nblocks, s, st);
+      case PWK_FP32: return nl ? launch_window_f32_nl(N, a, nblocks, s, st) : launch_window_f32(N, a, nblocks, s, st);
+      default:
+        return nl ? launch_window_f32c128_nl(N, a, nblocks, s, st) : launch_window_f32c128(N, a, nblocks, s, st);
     }
   }
   switch (precision) {
-    case PWK_FP64: return launch_fused_f64(N, a, nblocks, s, st);
-    case PWK_FP32: return launch_fused_f32(N, a, nblocks, s, st);
-    default: return launch_fused_f32c128(N, a, nblocks, s, st);
+    case PWK_FP64: return nl ? launch_fused_f64_nl(N, a, nblocks, s, st) : launch_fused_f64(N, a, nblocks, s, st);
+    case PWK_FP32: return nl ? launch_fused_f32_nl(N, a, nblocks, s, st) : launch_fused_f32(N, a, nblocks, s, st);
+    default: return nl ? launch_fused_f32c128_nl(N, a, nblocks, s, st) : launch_fused_f32c128(N, a, nblocks, s, st);
   }
 }
 
@@ -350,10 +409,12 @@ static void use_kind(const pwk_plan* p, FusedArgs& a, int kind) {
   }
 }
 
-// Pick the launch shape (threads per CTA, l3 chunk L) of one precision by timing the fused
-// kernel on a sample of the plan's k-points (8 zero vectors per k; the work of the kernel
-// does not depend on the values).  Every candidate gives bitwise the same result: the
-// arithmetic of each line and the order of every reduction do not depend on the shape.
+// Pick the launch shape (kernel kind, threads per CTA, l3 chunk L) of one precision, and
+// whether the projector terms run inside the local kernel or in separate kernels, by timing
+// them on a sample of the plan's k-points (8 zero vectors per k, up to 512 k-points in FP32
+// and 96 in FP64; the work of the kernels does not depend on the values).  Every shape of a
+// kind gives bitwise the same result: the arithmetic of each line and the order of every
+// reduction do not depend on the shape.
 int autotune_shape(pwk_plan* p, int precision) {
   const int N = p->N;
   const int elem = precision == PWK_FP64 ? 16 : 8;
@@ -376,7 +437,7 @@ int autotune_shape(pwk_plan* p, int precision) {
         if (c.smem <= 227 * 1024) cands.push_back(c);
       }
   if (cands.empty()) return PWK_OK;   // the default shape stands (plan creation checked it)
-  const int nv = 8, nkt = std::min(p->nk, precision == PWK_FP64 ? 64 : 192);
+  const int nv = 8, nkt = std::min(p->nk, precision == PWK_FP64 ? 96 : 512);
   const size_t bytes = (size_t)nkt * nv * p->npw_max * io_elem;
   void *in = nullptr, *out = nullptr;
   if (cudaMalloc(&in, bytes) != cudaSuccess || cudaMalloc(&out, bytes) != cudaSuccess) {
@@ -390,43 +451,99 @@ int autotune_shape(pwk_plan* p, int precision) {
   cudaEventCreate(&e1);
   FusedArgs a = hpsi_args(p, precision, in, out);
   a.nvec_in = a.nvec_out = nv;
-  // two interleaved rounds over the candidates, the faster of each candidate's two timings
-  // counts (a clock ramp or another process's burst during one timing does not decide)
-  std::vector<float> tbest(cands.size(), 1e30f);
+  // time of one call (after one untimed launch), ms; 1e30 if it fails
+  auto time_it = [&](auto&& run) -> float {
+    if (run() != PWK_OK) {
+      cudaGetLastError();
+      return 1e30f;
+    }
+    cudaEventRecord(e0, 0);
+    for (int r = 0; r < 3; ++r) run();
+    cudaEventRecord(e1, 0);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      cudaGetLastError();
+      return 1e30f;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms;
+  };
+  // Two interleaved rounds over the candidates, the faster of each candidate's two timings
+  // counts (a clock ramp or another process's burst during one timing does not decide).  Each
+  // candidate is timed without the projector terms and, where they fit, with them fused in.
+  std::vector<float> tplain(cands.size(), 1e30f), tfused(cands.size(), 1e30f);
   for (int round = 0; round < 2; ++round) {
     for (size_t ci = 0; ci < cands.size(); ++ci) {
       const LaunchShape& c = cands[ci];
       a.L = c.L;
       use_kind(p, a, c.kind);
-      if (launch_variant(precision, N, a, nkt * nv, c, 0) != PWK_OK) {
-        cudaGetLastError();
-        continue;
+      a.beta = nullptr;
+      tplain[ci] = std::min(tplain[ci], time_it([&] { return launch_variant(precision, N, a, nkt * nv, c, 0); }));
+      if (nl_fused_fits(p, precision, c)) {
+        set_fused_nl(p, precision, a, nullptr, c);
+        tfused[ci] = std::min(tfused[ci], time_it([&] { return launch_variant(precision, N, a, nkt * nv, c, 0); }));
+        a.beta = nullptr;
       }
-      cudaEventRecord(e0, 0);
-      for (int r = 0; r < 3; ++r) launch_variant(precision, N, a, nkt * nv, c, 0);
-      cudaEventRecord(e1, 0);
-      if (cudaEventSynchronize(e1) != cudaSuccess) {
-        cudaGetLastError();
-        continue;
-      }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      tbest[ci] = std::min(tbest[ci], ms);
     }
   }
-  float best = 1e30f;
-  LaunchShape pick = p->shape[precision];
+  size_t bp = 0, bf = 0;
   for (size_t ci = 0; ci < cands.size(); ++ci) {
-    if (tbest[ci] < best) {
-      best = tbest[ci];
-      pick = cands[ci];
+    if (tplain[ci] < tplain[bp]) bp = ci;
+    if (tfused[ci] < tfused[bf]) bf = ci;
+  }
+  cudaFree(in);
+  cudaFree(out);
+  in = out = nullptr;
+  // The projector terms inside the best fused shape against the separate kernels around the
+  // best plain shape (projections, local kernel, add-back), timed as whole H applications on
+  // a larger sample (at least about 16 waves of CTAs), where launch overheads and partial last
+  // waves no longer decide.
+  bool fused = false;
+  if (p->nkb > 0 && tfused[bf] < 1e29f && tplain[bp] < 1e29f) {
+    const int nk2 = std::min(p->nk, precision == PWK_FP64 ? 256 : 1536);
+    const size_t bytes2 = (size_t)nk2 * nv * p->npw_max * io_elem;
+    void* coef = nullptr;
+    if (cudaMalloc(&in, bytes2) == cudaSuccess && cudaMalloc(&out, bytes2) == cudaSuccess &&
+        cudaMalloc(&coef, (size_t)nk2 * nv * 2 * p->nkb * elem) == cudaSuccess) {
+      cudaMemset(in, 0, bytes2);
+      FusedArgs b = hpsi_args(p, precision, in, out);
+      b.nvec_in = b.nvec_out = nv;
+      NlArgs n = nl_args(p, precision, in, out, nullptr, nullptr, nullptr, nk2 * nv, nv, nv, 0);
+      n.tensor_cores = false;
+      n.coef = coef;
+      float tf = 1e30f, ts = 1e30f;
+      for (int round = 0; round < 2; ++round) {
+        const LaunchShape& cf = cands[bf];
+        b.L = cf.L;
+        use_kind(p, b, cf.kind);
+        set_fused_nl(p, precision, b, nullptr, cf);
+        tf = std::min(tf, time_it([&] { return launch_variant(precision, N, b, nk2 * nv, cf, 0); }));
+        const LaunchShape& cp = cands[bp];
+        b.L = cp.L;
+        use_kind(p, b, cp.kind);
+        b.beta = nullptr;
+        ts = std::min(ts, time_it([&] {
+          n.phase = 0;
+          int r = launch_nl(precision, n, 0);
+          if (r == PWK_OK) r = launch_variant(precision, N, b, nk2 * nv, cp, 0);
+          n.phase = 1;
+          return r ? r : launch_nl(precision, n, 0);
+        }));
+      }
+      fused = tf <= ts;
+    } else {
+      cudaGetLastError();
     }
+    cudaFree(coef);
+    cudaFree(in);
+    cudaFree(out);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaFree(in);
-  cudaFree(out);
-  p->shape[precision] = pick;
+  if (tplain[bp] < 1e29f || fused) {
+    p->shape[precision] = fused ? cands[bf] : cands[bp];
+    p->nl_fused[precision] = fused;
+  }
   return PWK_OK;
 }
 
@@ -488,6 +605,34 @@ cudaError_t scratch_alloc(void** ptr, size_t bytes, cudaStream_t st) {
   return e;
 }
 
+// Arguments of the separate projector kernels for a launch of run_hpsi (coef left null).
+static NlArgs nl_args(const pwk_plan* p, int precision, const void* in, void* out, void* sout,
+                      const int* items, const int* d_count, int nblocks, int nvec_in, int nvec_out,
+                      int k0) {
+  NlArgs n;
+  n.in = in;
+  n.out = out;
+  n.sout = sout;
+  n.items = items;
+  n.d_count = d_count;
+  n.k0 = k0;
+  n.err = p->d_err;
+  n.tensor_cores = p->projector_path == 1;
+  n.wait_polls = p->wait_polls;
+  n.nitems = nblocks;
+  n.nvec_in = nvec_in;
+  n.nvec_out = nvec_out;
+  n.nk = p->nk;
+  n.npw_max = p->npw_max;
+  n.npw = p->d_npw;
+  n.nkb = p->nkb;
+  const bool f64 = precision == PWK_FP64;
+  n.beta = f64 ? static_cast<const void*>(p->d_beta) : static_cast<const void*>(p->d_beta32);
+  n.D = f64 ? static_cast<const void*>(p->d_D) : static_cast<const void*>(p->d_D32);
+  n.q = f64 ? static_cast<const void*>(p->d_q) : static_cast<const void*>(p->d_q32);
+  return n;
+}
+
 int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* items,
              const int* d_count, int nblocks, int nvec_in, int nvec_out, cudaStream_t st,
              void* sout, int k0) {
@@ -496,31 +641,26 @@ int run_hpsi(pwk_plan* p, int precision, const void* in, void* out, const int* i
     return PWK_ERR_INVALID;
   }
   if (nblocks <= 0) return PWK_OK;
-  // projector coefficients gamma, delta of every item: scratch from a stream-ordered pool,
-  // so concurrent calls on other streams never share it
+  const LaunchShape& shape = p->shape[precision];
+  if (out != nullptr && nl_fused_for(p, precision, shape)) {
+    // one kernel: projections, local and kinetic terms, add-back (and S C)
+    FusedArgs a = hpsi_args(p, precision, in, out);
+    a.items = items;
+    a.d_count = d_count;
+    a.k0 = k0;
+    a.nvec_in = nvec_in;
+    a.nvec_out = nvec_out;
+    use_kind(p, a, shape.kind);
+    set_fused_nl(p, precision, a, sout, shape);
+    return launch_variant(precision, p->N, a, nblocks, shape, st);
+  }
+  // separate projector kernels: coefficients gamma, delta of every item in scratch from a
+  // stream-ordered pool, so concurrent calls on other streams never share it
   NlArgs n;
   const bool nl = p->nkb > 0 || sout != nullptr;   // with no projectors S C = C (phase 1 copies)
   if (nl) {
-    n.in = in;
-    n.out = out;
-    n.sout = sout;
-    n.items = items;
-    n.d_count = d_count;
-    n.k0 = k0;
-    n.err = p->d_err;
-    n.tensor_cores = p->projector_path == 1;
-    n.wait_polls = p->wait_polls;
-    n.nitems = nblocks;
-    n.nvec_in = nvec_in;
-    n.nvec_out = nvec_out;
-    n.nk = p->nk;
-    n.npw_max = p->npw_max;
-    n.npw = p->d_npw;
-    n.nkb = p->nkb;
+    n = nl_args(p, precision, in, out, sout, items, d_count, nblocks, nvec_in, nvec_out, k0);
     const bool f64 = precision == PWK_FP64;
-    n.beta = f64 ? static_cast<const void*>(p->d_beta) : static_cast<const void*>(p->d_beta32);
-    n.D = f64 ? static_cast<const void*>(p->d_D) : static_cast<const void*>(p->d_D32);
-    n.q = f64 ? static_cast<const void*>(p->d_q) : static_cast<const void*>(p->d_q32);
     const size_t cbytes = (size_t)nblocks * 2 * p->nkb * (f64 ? 16 : 8);
     if (cbytes > 0) {
       cudaError_t e = scratch_alloc(&n.coef, cbytes, st);
@@ -608,12 +748,17 @@ int pwk_plan_errors(pwk_plan* p, int* flags, int clear) {
 }
 
 int pwk_plan_set_projector_path(pwk_plan* p, int path) {
-  if (p == nullptr || path < 0 || path > 1) {
-    set_error("null plan or path not 0/1");
+  if (p == nullptr || path < 0 || path > 3) {
+    set_error("null plan or path not 0..3");
     return PWK_ERR_INVALID;
   }
   p->projector_path = path;
   return PWK_OK;
+}
+
+int pwk_plan_projector_fused(const pwk_plan* p, int precision) {
+  if (p == nullptr || precision < 0 || precision > 2) return -1;
+  return nl_fused_for(p, precision, p->shape[precision]) ? 1 : 0;
 }
 
 int pwk_plan_set_launch_shape(pwk_plan* p, int precision, int kind, int threads, int l3_chunk) {

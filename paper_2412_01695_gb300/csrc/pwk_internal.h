@@ -105,7 +105,8 @@ struct pwk_plan {
   const pwk_plan* xfer_src = nullptr;
   pwk::LaunchShape shape[3];     // per precision
   pwk::LaunchShape xshape;       // transfer kernel (complex dv, FP64)
-  int projector_path = 0;        // 0: CUDA cores, 1: tensor cores where they apply
+  int projector_path = 0;        // 0 automatic, 1 tensor cores, 2 separate kernels, 3 fused
+  bool nl_fused[3] = {false, false, false};   // automatic choice per precision (autotuner)
   long long wait_polls = 1LL << 24;   // bound on the polls of each device-side wait
   int* d_err = nullptr;          // device error word (bad work items)
   // solver phase timing (pwk_plan_set_solver_timing): figures of the last solver call
@@ -150,6 +151,14 @@ struct FusedArgs {
   const void* V = nullptr;         // real [N^3] of the arithmetic type, or complex128 dv
   double scale = 1.0;              // 1/N_r
   int* err = nullptr;
+  // nonlocal projector terms fused into the kernel (nl_fused.cuh); beta == null: none
+  const void* beta = nullptr;      // [nk][nkb][npw_beta] complex of the arithmetic type
+  const void* Dm = nullptr;        // [nkb][nkb] real of the arithmetic type
+  const void* qm = nullptr;        // [nkb][nkb] or null (S = 1)
+  void* sout = nullptr;            // S C output (io type) or null
+  int nkb = 0, npw_beta = 0;
+  int nl_off = 0;                  // byte offset of the coefficients in dynamic shared memory
+  int loc_off = 0;                 // window kernel: byte offset of the gathered local result and C
 };
 
 size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int npw_in_max);
@@ -192,6 +201,13 @@ int launch_fused_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchSha
                          cudaStream_t st);
 int launch_fused_xfer(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
 int launch_window_f64(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+// the same kernels with the projector terms inside (a.beta set), defined in hpsi_*_nl.cu
+int launch_fused_f64_nl(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_fused_f32_nl(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_fused_f32c128_nl(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_window_f64_nl(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_window_f32_nl(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+int launch_window_f32c128_nl(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
 int launch_window_f32(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
 int launch_window_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchShape& s,
                           cudaStream_t st);

@@ -22,7 +22,7 @@ PWK_FLAG_ITEM_SKIPPED, PWK_FLAG_WAIT_TIMEOUT = 1, 2
 # every symbol declared in include/pwk.h
 EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
            "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_plan_set_projector_path",
-           "pwk_plan_errors", "pwk_plan_set_wait_limit",
+           "pwk_plan_errors", "pwk_plan_set_wait_limit", "pwk_plan_projector_fused",
            "pwk_supported_grid",
            "pwk_hpsi_batched", "pwk_hpsi_batched_host", "pwk_hpsi_items", "pwk_plan_set_overlap",
            "pwk_plan_has_overlap",
@@ -55,6 +55,7 @@ def load(path: str = LIB_PATH):
         "pwk_plan_launch_shape": (_I, [_P, _I, _P, _P, _P, _P]),
         "pwk_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
         "pwk_plan_set_projector_path": (_I, [_P, _I]),
+        "pwk_plan_projector_fused": (_I, [_P, _I]),
         "pwk_plan_errors": (_I, [_P, ctypes.POINTER(_I), _I]),
         "pwk_plan_set_wait_limit": (_I, [_P, ctypes.c_longlong]),
         "pwk_supported_grid": (_I, [_I]),
@@ -145,8 +146,14 @@ class Plan:
                "pwk_plan_set_launch_shape")
 
     def set_projector_path(self, path: int) -> None:
-        """pwk_plan_set_projector_path: 0 CUDA cores (default), 1 tensor cores where they apply."""
+        """pwk_plan_set_projector_path: 0 automatic (default), 1 tensor-core projections,
+        2 separate CUDA-core kernels, 3 fused into the local kernel."""
         _check(load().pwk_plan_set_projector_path(self.handle, path), "pwk_plan_set_projector_path")
+
+    def projector_fused(self, precision: int) -> bool:
+        """pwk_plan_projector_fused: whether H|psi> of this precision runs the projector terms
+        inside the local kernel."""
+        return load().pwk_plan_projector_fused(self.handle, precision) == 1
 
     def errors(self, clear: bool = True) -> int:
         """pwk_plan_errors: the device-side flags (PWK_FLAG_*) recorded since the last clear."""

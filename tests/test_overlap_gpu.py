@@ -19,10 +19,11 @@ TOL64 = 1e-12
 TOL32 = 5e-6
 
 
-def run_hs(prob, q, precision="fp64", items=None, nvec=None):
+def run_hs(prob, q, precision="fp64", items=None, nvec=None, path=0):
     torch = torch_cuda()
     from paper_2412_01695_gb300 import pwk
     plan = pwk.plan_from_problem(prob)
+    plan.set_projector_path(path)
     plan.set_overlap(q)
     assert plan.has_overlap == (q is not None and prob.nkb > 0)
     prec = pwk.PRECISIONS[precision]
@@ -115,3 +116,31 @@ def test_aliasing_rejected():
     with pytest.raises(pwk.PwkError):
         pwk.hspsi_batched(plan, pwk.PWK_FP64, x, y, x, prob.nb)
     plan.close()
+
+
+@pytest.mark.parametrize("path", [2, 3])
+@pytest.mark.parametrize("precision", ["fp64", "fp32_c128"])
+@pytest.mark.parametrize("cfg,nks", [(1, 8), (2, 4), (4, 3)])
+def test_hs_each_projector_path(path, precision, cfg, nks):
+    """H and S together with the projector terms in separate kernels (path 2) and inside the
+    local kernel (path 3), batched and on a work list, against the oracle; without q, S psi is
+    psi bit for bit on both paths."""
+    nkfull = int(np.prod(synth.CONFIGS[cfg]["mp"]))
+    prob = synth.make_config(cfg, k_subset=synth.sample_k(nkfull, nks), nb=4)
+    q = synth.q_for(cfg)
+    tol = TOL64 if precision == "fp64" else TOL32
+    h, s = run_hs(prob, q, precision, path=path)
+    assert max_rel_err(h, oracle_hpsi(prob), prob) <= tol
+    assert max_rel_err(s, oracle_spsi(prob, q), prob) <= tol
+    items = [(0, 0, 3), (prob.nk - 1, 2, 1), (-1, 0, 0), (0, 1, 0)]
+    h, s = run_hs(prob, q, precision, items=items, path=path)
+    ref_h, ref_s = oracle_hpsi(prob), oracle_spsi(prob, q)
+    for k, vi, vo in items:
+        if k < 0:
+            continue
+        n = prob.npw[k]
+        assert ham.relative_error(h[k][vo, :n], ref_h[k][vi, :n]) <= tol
+        assert ham.relative_error(s[k][vo, :n], ref_s[k][vi, :n]) <= tol
+        assert np.all(s[k][vo, n:] == 0) and np.all(h[k][vo, n:] == 0)
+    h, s = run_hs(prob, None, precision, path=path)
+    np.testing.assert_array_equal(s, prob.psi)
