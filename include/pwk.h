@@ -191,6 +191,32 @@ int pwk_hpsi_batched_host(pwk_plan* plan, int precision, const void* h_psi, void
 int pwk_hpsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, const int* items,
                    int nitems, int nvec_per_k, void* stream);
 
+/* pwk_hpsi_multi: H|psi> on one work list whose entries belong to several plans -- cells with
+ * their own atoms and projector sets (nkb may differ, 0 included), D, V(r), spheres and
+ * k-points -- applied in a single launch (the paper batches the k-points of one cell, Sec. 4;
+ * this extends the batch across cells that share an FFT grid, so uneven projector sets do
+ * not split the work into one launch per cell).
+ *   nplans      number of plans (>= 1); plans[i] the plan of cell i; all on one device with
+ *               the same grid N, and every sphere within |m_i| <= N/4 (the window kernel)
+ *   precision   PWK_FP64, PWK_FP32 or PWK_FP32_C128
+ *   psi, hpsi   host arrays of nplans device pointers: psi[i], hpsi[i] are plan i's vectors
+ *               [nk_i][nvec_per_k[i]][npw_max_i] of the precision's complex type
+ *   nvec_per_k  host int[nplans]
+ *   items       device int[nitems][4]: (plan, k, in_slot, out_slot): hpsi[plan][k][out_slot]
+ *               = H_plan(k) psi[plan][k][in_slot].  plan = -1 marks an empty slot; an entry
+ *               outside the plans, the plan's k-points or its slots is skipped (its output left
+ *               unchanged) and flags PWK_FLAG_ITEM_SKIPPED on plans[0]
+ *   nitems      number of entries (0: nothing is launched)
+ * The projector terms run inside the kernel (one HBM round trip per item); the launch shape
+ * is plans[0]'s window shape for the precision.  Two entries must not write the same output
+ * vector, and no output may be an input of another entry (in place, hpsi[i] == psi[i], is
+ * allowed).  The plans' arguments (a few hundred bytes each) take scratch from the library's
+ * stream-ordered pool.  PWK_ERR_INVALID for mismatched plans or bad pointers,
+ * PWK_ERR_UNSUPPORTED when a plan's spheres or projectors do not fit the window kernel.
+ * Asynchronous on `stream`. */
+int pwk_hpsi_multi(int nplans, pwk_plan* const* plans, int precision, const void* const* psi,
+                   void* const* hpsi, const int* nvec_per_k, const int* items, int nitems, void* stream);
+
 /* ---------------------------------------------------------------------------- overlap S
  * Ultrasoft / PAW overlap (paper Sec. 2.2):
  *   S C = C + sum_{I,mn} q^I_mn beta^I_m <beta^I_n|C>  (Eqs. lambdah, delta_eq, finals),

@@ -431,6 +431,7 @@ __global__ void __launch_bounds__(256) resid_kernel(int nb, int MB, int np, cons
 
 // Which bands still need a correction, per k-point and its phase (1: FP32 H, 2: FP64 H).
 // counters[0] += bands to correct this step, counters[5] += those of phase-2 k-points,
+// counters[6] += k-points that take a correction step,
 // counters[4] += k-points switching from phase 1 to phase 2 this step (their FP32 floor is
 // reached or their phase-1 iterations are used up), counters[1] += bands of k-points given up
 // after repeated reduced-problem failures (counters[2], [3]: the first such k and its status).
@@ -477,6 +478,7 @@ __global__ void select_kernel(int nk, int nb, int MB, double rt1, double rt2, in
   } else {
     iters[k] += 1;
     iterk[k] = 1;
+    atomicAdd(&counters[6], 1);
   }
   atomicAdd(&counters[0], c);
   if (phase[k] == 2) atomicAdd(&counters[5], c);

@@ -40,33 +40,18 @@ struct OutOfWin {
 //         nwarps L) through the y, x and y passes with warp-level synchronisation only; block
 //         barriers remain only around the z passes.  The arithmetic of every line is the same
 //         in both modes (the results are bitwise equal); only the thread mapping differs.
-// NL: the nonlocal projector terms are applied in the epilogue (nl_fused.cuh); the kernel
-//     without them (NL false) is compiled apart, so the projector code costs it nothing.
+// The work of one band-k item (k, input slot vin, output slot vout) of the plan described
+// by `a`; the kernels below decode the item and call it.
+// NL: the nonlocal projector terms are applied in the epilogue (nl_fused.cuh) when the plan
+//     has projectors (a.nkb > 0); the kernel without them (NL false) is compiled apart, so the
+//     projector code costs it nothing.
 template <typename T, typename TI, int N, int W, int MODE, bool NL>
-__global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
+__device__ __forceinline__ void window_body(const FusedArgs& a, int k, int vin, int vout) {
   using V = c2_t<T>;
   using VI = c2_t<TI>;
   using Wn = Win<N, W>;
   constexpr int NW = Wn::NW;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-
-  const int item = blockIdx.x;
-  if (a.d_count != nullptr && item >= *a.d_count) return;
-  int k, vin, vout;
-  if (a.items != nullptr) {
-    k = a.items[3 * item];
-    vin = a.items[3 * item + 1];
-    vout = a.items[3 * item + 2];
-    if (k == -1) return;
-    if (k < 0 || k >= a.nk || vin < 0 || vin >= a.nvec_in || vout < 0 || vout >= a.nvec_out) {
-      if (threadIdx.x == 0 && a.err != nullptr) atomicOr(a.err, 1);
-      return;
-    }
-  } else {
-    const int kr = item / a.nvec_in;
-    vin = vout = item - kr * a.nvec_in;
-    k = a.k0 + kr;
-  }
   const int tid = threadIdx.x, nth = blockDim.x;
   const int np = a.npw_in[k];
   const int ns = a.nstick[k];
@@ -231,7 +216,7 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
   __syncthreads();
 
   // ---- 5: gather with 1/N_r; kinetic term
-  if constexpr (!NL) {
+  if (!NL || a.nkb == 0) {
     const int* gout = a.gout + (size_t)k * a.npw_out_max;
     const T sc = T(a.scale);
     const double* g2k = a.g2 + (size_t)k * a.npw_out_max;
@@ -244,7 +229,7 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
       pout[g] = VI{TI(acc.x), TI(acc.y)};
     }
     for (int g = np + tid; g < a.npw_out_max; g += nth) pout[g] = VI{TI(0), TI(0)};
-  } else {
+  } else if constexpr (NL) {
     // With projectors (nl_fused.cuh): the local result and C go to shared memory past the
     // stick square; once the square is read, beta(k) is staged over it, and the projections,
     // gamma (delta) and the add-back (S C) run from shared memory.
@@ -289,8 +274,78 @@ __global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
   }
 }
 
+// One CTA per work item of one plan: item = (k - k0) * nvec + band of a batched call, or the
+// (k, in_slot, out_slot) entry of a work list.
+template <typename T, typename TI, int N, int W, int MODE, bool NL>
+__global__ void __launch_bounds__(256) fused_window_kernel(FusedArgs a) {
+  const int item = blockIdx.x;
+  if (a.d_count != nullptr && item >= *a.d_count) return;
+  int k, vin, vout;
+  if (a.items != nullptr) {
+    k = a.items[3 * item];
+    vin = a.items[3 * item + 1];
+    vout = a.items[3 * item + 2];
+    if (k == -1) return;
+    if (k < 0 || k >= a.nk || vin < 0 || vin >= a.nvec_in || vout < 0 || vout >= a.nvec_out) {
+      if (threadIdx.x == 0 && a.err != nullptr) atomicOr(a.err, 1);
+      return;
+    }
+  } else {
+    const int kr = item / a.nvec_in;
+    vin = vout = item - kr * a.nvec_in;
+    k = a.k0 + kr;
+  }
+  window_body<T, TI, N, W, MODE, NL>(a, k, vin, vout);
+}
+
+// One CTA per work item of a list that spans several plans of the same grid (cells with their
+// own atoms, projectors, V(r), spheres and k-points): entry (plan, k, in_slot, out_slot) of
+// a.items, the plan's arguments at a.multi[plan] (in device memory).  An entry with plan = -1
+// is an empty slot; one outside the plans or the plan's k-points and slots is skipped and
+// flagged in the first plan's error word.
+template <typename T, typename TI, int N, int W, int MODE>
+__global__ void __launch_bounds__(256) fused_window_multi_kernel(FusedArgs a0) {
+  const int item = blockIdx.x;
+  const int* it = a0.items + 4 * (size_t)item;
+  const int p = it[0], k = it[1], vin = it[2], vout = it[3];
+  if (p == -1) return;
+  if (p < 0 || p >= a0.nmulti) {
+    if (threadIdx.x == 0 && a0.err != nullptr) atomicOr(a0.err, 1);
+    return;
+  }
+  const FusedArgs& a = a0.multi[p];
+  if (k < 0 || k >= a.nk || vin < 0 || vin >= a.nvec_in || vout < 0 || vout >= a.nvec_out) {
+    if (threadIdx.x == 0 && a0.err != nullptr) atomicOr(a0.err, 1);
+    return;
+  }
+  window_body<T, TI, N, W, MODE, true>(a, k, vin, vout);
+}
+
 // window half-width instantiated for a grid of size N
 __host__ __device__ constexpr int window_of(int N) { return N / 4; }
+
+template <typename T, typename TI>
+int launch_window_multi(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {
+  if (nblocks <= 0) return PWK_OK;
+  switch (N) {
+#define PWK_WMCASE(n)                                                                           \
+  case n: {                                                                                     \
+    auto kern = s.kind == 2 ? fused_window_multi_kernel<T, TI, n, window_of(n), 1>              \
+                            : fused_window_multi_kernel<T, TI, n, window_of(n), 0>;             \
+    cudaError_t e = allow_full_smem(kern);                                                      \
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(window multi)");            \
+    kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \
+    e = cudaGetLastError();                                                                     \
+    if (e != cudaSuccess) return cuda_fail(e, "window multi kernel launch");                    \
+    return PWK_OK;                                                                              \
+  }
+    PWK_FOR_EACH_N(PWK_WMCASE)
+#undef PWK_WMCASE
+    default:
+      set_error("unsupported grid size");
+      return PWK_ERR_UNSUPPORTED;
+  }
+}
 
 template <typename T, typename TI, bool NL>
 int launch_window(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st) {

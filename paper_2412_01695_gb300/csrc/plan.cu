@@ -1146,6 +1146,86 @@ int pwk_hspsi_items(pwk_plan* p, int precision, const void* psi, void* hpsi, voi
                   static_cast<cudaStream_t>(stream), spsi);
 }
 
+int pwk_hpsi_multi(int nplans, pwk_plan* const* plans, int precision, const void* const* psi,
+                   void* const* hpsi, const int* nvec_per_k, const int* items, int nitems, void* stream) {
+  if (nplans < 1 || plans == nullptr || psi == nullptr || hpsi == nullptr || nvec_per_k == nullptr ||
+      nitems < 0 || (nitems > 0 && items == nullptr)) {
+    set_error("null pointer, nplans < 1 or nitems < 0");
+    return PWK_ERR_INVALID;
+  }
+  if (precision < 0 || precision > 2) {
+    set_error("unknown precision");
+    return PWK_ERR_INVALID;
+  }
+  const pwk_plan* p0 = plans[0];
+  for (int i = 0; i < nplans; ++i) {
+    const pwk_plan* p = plans[i];
+    if (p == nullptr || psi[i] == nullptr || hpsi[i] == nullptr || nvec_per_k[i] < 1) {
+      set_error("null plan or vector array, or nvec_per_k < 1");
+      return PWK_ERR_INVALID;
+    }
+    if (p->N != p0->N || p->device != p0->device) {
+      set_error("the plans of one call must share the grid and the device");
+      return PWK_ERR_INVALID;
+    }
+    if (!p->window_ok) {
+      set_error("pwk_hpsi_multi needs spheres within the window kernel's |m_i| <= N/4");
+      return PWK_ERR_UNSUPPORTED;
+    }
+  }
+  if (nitems == 0) return PWK_OK;
+  // one launch shape for every plan: the first plan's window shape of this precision (or the
+  // kernel's default chunk), shared memory for the largest stick set and fused layout
+  LaunchShape s;
+  s.kind = p0->shape[precision].kind >= 1 ? p0->shape[precision].kind : 1;
+  s.threads = p0->shape[precision].kind >= 1 ? p0->shape[precision].threads : 128;
+  s.L = p0->shape[precision].kind >= 1 ? p0->shape[precision].L : std::max(1, p0->N / 3);
+  if (s.kind == 2) s.L = std::min(s.L, 2);
+  const int elem = precision == PWK_FP64 ? 16 : 8;
+  int nst = 0;
+  for (int i = 0; i < nplans; ++i) nst = std::max(nst, plans[i]->self.nstick_max);
+  s.smem = window_smem_bytes(p0->N, elem, s.L, nst, s.kind == 2 ? s.threads / 32 : 1);
+  std::vector<FusedArgs> d(nplans);
+  size_t need = s.smem;
+  for (int i = 0; i < nplans; ++i) {
+    pwk_plan* p = plans[i];
+    FusedArgs a = hpsi_args(p, precision, psi[i], hpsi[i]);
+    a.nvec_in = a.nvec_out = nvec_per_k[i];
+    a.L = s.L;
+    use_kind(p, a, s.kind);
+    if (p->nkb > 0) {
+      const size_t b = fused_layout(p, precision, s, nullptr, nullptr);
+      if (b > 227 * 1024) {
+        set_error("a plan's projectors do not fit in shared memory next to the kernel's buffers");
+        return PWK_ERR_UNSUPPORTED;
+      }
+      set_fused_nl(p, precision, a, nullptr, s);
+      need = std::max(need, b);
+    }
+    d[i] = a;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  void* dd = nullptr;
+  cudaError_t e = scratch_alloc(&dd, sizeof(FusedArgs) * nplans, st);
+  if (e != cudaSuccess) return cuda_fail(e, "scratch_alloc(plan arguments)");
+  e = cudaMemcpyAsync(dd, d.data(), sizeof(FusedArgs) * nplans, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(dd, st);
+    return cuda_fail(e, "cudaMemcpyAsync(plan arguments)");
+  }
+  FusedArgs a0 = d[0];
+  a0.items = items;
+  a0.multi = static_cast<const FusedArgs*>(dd);
+  a0.nmulti = nplans;
+  a0.err = p0->d_err;
+  LaunchShape sl = s;
+  sl.smem = need;
+  int rc = launch_window_multi_prec(precision, p0->N, a0, nitems, sl, st);
+  e = cudaFreeAsync(dd, st);
+  if (rc == PWK_OK && e != cudaSuccess) rc = cuda_fail(e, "cudaFreeAsync(plan arguments)");
+  return rc;
+}
+
 int pwk_hpsi_items(pwk_plan* p, int precision, const void* psi, void* hpsi, const int* items,
                    int nitems, int nvec_per_k, void* stream) {
   if (p == nullptr || psi == nullptr || hpsi == nullptr || (nitems > 0 && items == nullptr) ||

@@ -159,6 +159,10 @@ struct FusedArgs {
   int nkb = 0, npw_beta = 0;
   int nl_off = 0;                  // byte offset of the coefficients in dynamic shared memory
   int loc_off = 0;                 // window kernel: byte offset of the gathered local result and C
+  // work lists over several plans (pwk_hpsi_multi): items are (plan, k, in, out) and the
+  // plans' own arguments are multi[0 .. nmulti) in device memory
+  const FusedArgs* multi = nullptr;
+  int nmulti = 0;
 };
 
 size_t fused_smem_bytes(int N, int elem_bytes, int nstick_max, int P, int L, int npw_in_max);
@@ -208,6 +212,9 @@ int launch_fused_f32c128_nl(int N, const FusedArgs& a, int nblocks, const Launch
 int launch_window_f64_nl(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
 int launch_window_f32_nl(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
 int launch_window_f32c128_nl(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
+// work lists over several plans of one grid (pwk_hpsi_multi), defined in hpsi_multi.cu
+int launch_window_multi_prec(int precision, int N, const FusedArgs& a, int nblocks, const LaunchShape& s,
+                             cudaStream_t st);
 int launch_window_f32(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, cudaStream_t st);
 int launch_window_f32c128(int N, const FusedArgs& a, int nblocks, const LaunchShape& s,
                           cudaStream_t st);

@@ -24,7 +24,8 @@ EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
            "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_plan_set_projector_path",
            "pwk_plan_errors", "pwk_plan_set_wait_limit", "pwk_plan_projector_fused",
            "pwk_supported_grid",
-           "pwk_hpsi_batched", "pwk_hpsi_batched_host", "pwk_hpsi_items", "pwk_plan_set_overlap",
+           "pwk_hpsi_batched", "pwk_hpsi_batched_host", "pwk_hpsi_items", "pwk_hpsi_multi",
+           "pwk_plan_set_overlap",
            "pwk_plan_has_overlap",
            "pwk_hspsi_batched", "pwk_hspsi_items", "pwk_drho_batched", "pwk_davidson_batched",
            "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_eigh_batched_noalloc",
@@ -62,6 +63,7 @@ def load(path: str = LIB_PATH):
         "pwk_hpsi_batched": (_I, [_P, _I, _P, _P, _I, _P]),
         "pwk_hpsi_batched_host": (_I, [_P, _I, _P, _P, _P, _P, _I, _I, _P]),
         "pwk_hpsi_items": (_I, [_P, _I, _P, _P, _P, _I, _I, _P]),
+        "pwk_hpsi_multi": (_I, [_I, _P, _I, _P, _P, _P, _P, _I, _P]),
         "pwk_plan_set_overlap": (_I, [_P, _P]),
         "pwk_plan_has_overlap": (_I, [_P]),
         "pwk_hspsi_batched": (_I, [_P, _I, _P, _P, _P, _I, _P]),
@@ -275,6 +277,34 @@ def hpsi_items(plan: Plan, precision: int, psi, hpsi, items, nvec_per_k: int, st
     _check(load().pwk_hpsi_items(plan.handle, precision, _ptr(psi), _ptr(hpsi),
                                  _ptr(items) if n else None, n, nvec_per_k, _stream(stream)),
            "pwk_hpsi_items")
+
+
+def hpsi_multi(plans, precision: int, psis, hpsis, items, stream=None):
+    """pwk_hpsi_multi: one work list over several plans of one grid.  plans, psis, hpsis are
+    lists (one entry per plan; psis[i] [nk_i][nvec_i][npw_max_i]); items a device int32 tensor
+    [n][4] of (plan, k, in_slot, out_slot)."""
+    import torch
+    npl = len(plans)
+    if not (len(psis) == len(hpsis) == npl) or npl < 1:
+        raise ValueError("one psi and one hpsi per plan")
+    dt = torch.complex64 if precision == PWK_FP32 else torch.complex128
+    nvec = []
+    for p, x, y in zip(plans, psis, hpsis):
+        if x.dim() != 3:
+            raise ValueError("psi must be [nk][nvec][npw_max]")
+        shape = (p.nk, int(x.shape[1]), p.npw_max)
+        _need(x, shape, dt, "psi")
+        _need(y, shape, dt, "hpsi")
+        nvec.append(int(x.shape[1]))
+    n = 0 if items is None else int(items.shape[0])
+    if n:
+        _need(items, (n, 4), torch.int32, "items")
+    ph = (ctypes.c_void_p * npl)(*[p.handle for p in plans])
+    xs = (ctypes.c_void_p * npl)(*[_ptr(x) for x in psis])
+    ys = (ctypes.c_void_p * npl)(*[_ptr(y) for y in hpsis])
+    nv = (ctypes.c_int * npl)(*nvec)
+    _check(load().pwk_hpsi_multi(npl, ph, precision, xs, ys, nv, _ptr(items) if n else None, n,
+                                 _stream(stream)), "pwk_hpsi_multi")
 
 
 def hspsi_batched(plan: Plan, precision: int, psi, hpsi, spsi, nb: int, stream=None) -> None:
