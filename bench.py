@@ -610,28 +610,52 @@ def run_other_cells(dev, stream, quick=False):
     return out
 
 
-def run_serving(n_jobs=40, rate_hz=200.0):
-    """Serving: a seeded Poisson stream of mixed jobs (60% H|psi>, 25% Davidson, 15%
-    Sternheimer), admitted by HBM footprint into 4 overlapping slots with H|psi> coalescing,
-    against the same jobs run one at a time in FP64."""
+def run_serving(quick=False):
+    """Serving over the workload's ranges (serve.config5_mix: fcc/sc cells with 1-8 atoms,
+    25-60 Ry, 4-60 bands, 1-1728 k-points; 60% H|psi> in the mixed path, 25% Davidson, 15%
+    Sternheimer), plans and solver workspaces resident before the clock: (1) Poisson arrivals
+    at 200 Hz into 4 overlapping slots with H|psi> coalescing and HBM-footprint admission;
+    (2) the same jobs at a sustainable rate (70% of the throughput (1) reached); (3) the plain
+    baseline at the arrivals of (2): one job at a time, FP64, H|psi> with one launch set per
+    k-point."""
     from paper_2412_01695_gb300 import serve
-    jobs = serve.random_mix(n_jobs, rate_hz=rate_hz, seed=2024, max_nk=27, max_nb=16,
-                            ecut_range=(25.0, 40.0))
-    copy = lambda js: [serve.Job(j.jid, j.kind, j.cell, j.nb, arrival=j.arrival) for j in js]  # noqa: E731
-    ex = serve.GpuExecutor(slots=4)
+    n_jobs = 24 if quick else 40
+    jobs = serve.config5_mix(n_jobs, rate_hz=200.0, seed=7)
+    t0 = time.perf_counter()
+    ex = serve.GpuExecutor(slots=4, plan_cache_bytes=96 << 30)
     ex.prepare(jobs)
-    srv = serve.Server(ex, hbm_budget=32 << 30, slots=4, estimate=serve.estimate_for)
-    done = srv.run(copy(jobs), realtime=True)
-    st = serve.latency_stats(done)
-    ex1 = serve.GpuExecutor(slots=1)
-    ex1.prepare(jobs)
-    one = serve.Server(ex1, hbm_budget=32 << 30, slots=1, estimate=serve.estimate_for,
-                       coalesce=False).run(copy(jobs), realtime=True)
-    st1 = serve.latency_stats(one)
-    return {"jobs": n_jobs, "rate_hz": rate_hz,
-            "mix": {k: sum(j.kind == k for j in jobs) for k in ("hpsi", "davidson", "sternheimer")},
-            "continuous": st, "one_at_a_time": st1,
-            "p99_speedup": st1.get("p99_s", float("nan")) / st.get("p99_s", float("nan"))}
+    ex.warm(jobs)
+    warm_s = time.perf_counter() - t0
+    budget = 160 << 30
+
+    def run(js, slots, coalesce):
+        srv = serve.Server(ex, hbm_budget=budget, slots=slots, estimate=serve.estimate_for, coalesce=coalesce)
+        return srv.run([j.fresh() for j in js], realtime=True)
+
+    d200 = run(jobs, 4, True)
+    st200 = serve.latency_stats(d200)
+    rate_s = 0.7 * st200["jobs_per_s"]
+    scale = 200.0 / rate_s
+    jobs_s = [serve.Job(j.jid, j.kind, j.cell, j.nb, arrival=j.arrival * scale, precision=j.precision)
+              for j in jobs]
+    ds = run(jobs_s, 4, True)
+    sts = serve.latency_stats(ds)
+    ex.per_k = True
+    dplain = run(jobs_s, 1, False)
+    ex.per_k = False
+    stp = serve.latency_stats(dplain)
+    mix = {k: sum(j.kind == k for j in jobs) for k in ("hpsi", "davidson", "sternheimer")}
+    nks = sorted({j.cell.mp ** 3 for j in jobs})
+    return {"jobs": n_jobs, "mix": mix, "k_points_per_job": [nks[0], nks[-1]],
+            "bands_per_job": [min(j.nb for j in jobs), max(j.nb for j in jobs)],
+            "atoms_per_cell": [min(j.cell.nat for j in jobs), max(j.cell.nat for j in jobs)],
+            "ecut_ry": [min(j.cell.ecut for j in jobs), max(j.cell.ecut for j in jobs)],
+            "warm_up_s": warm_s,
+            "offered_200hz": {**st200, "note": "arrivals faster than service: latency is mostly queueing"},
+            "sustainable": {**sts, "offered_rate_hz": rate_s},
+            "plain_per_k_fp64_one_at_a_time": {**stp, "offered_rate_hz": rate_s},
+            "p99_speedup_vs_plain": stp.get("p99_s", float("nan")) / sts.get("p99_s", float("nan")),
+            "p50_speedup_vs_plain": stp.get("p50_s", float("nan")) / sts.get("p50_s", float("nan"))}
 
 
 # --------------------------------------------------------------------------- the oracle on the host
@@ -829,7 +853,7 @@ def main():
         res.update(sol)
         res["other_cells"] = run_other_cells(dev, stream, quick=args.quick)
         if not args.no_serving:
-            res["serving"] = run_serving(n_jobs=20 if args.quick else 40)
+            res["serving"] = run_serving(quick=args.quick)
     else:
         drho_sample = None
     # the CPU-baseline leg (rank 0, N = 1, after every timed region): the oracle timed on the

@@ -32,7 +32,9 @@
 namespace pwk {
 
 struct DavWork {
-  int nk = 0, nb = 0, MB = 0, npw_max = 0;
+  int nk = 0, nb = 0, MB = 0, npw_max = 0;   // nb, MB: the current call's
+  int cap_nb = 0, cap_MB = 0;                // the allocated capacity
+  bool has_s = false, has32 = false;         // S phi arrays, FP32 arrays allocated
   bool with_s = false;   // overlap S (plan with q): S phi kept beside H phi
   double2 *phi = nullptr, *hphi = nullptr, *corr = nullptr, *tmp1 = nullptr, *tmp2 = nullptr;
   double2 *sphi = nullptr, *tmp3 = nullptr;
@@ -67,20 +69,44 @@ static int dalloc(pwk_plan* p, DavWork* w, T** ptr, size_t n) {
   return rc;
 }
 
+// The workspace only grows: a call whose nb and MB fit the allocated capacity (and whose
+// precision mode and overlap the allocated arrays cover) reuses it, so a plan that serves
+// solves of different sizes allocates (and synchronises the device) only for the largest.
+// The arrays are indexed with the call's nb and MB.
+static int alloc_dav_work(pwk_plan* p, int nb, int MB, bool mixed, bool with_s);
 static int ensure_dav_work(pwk_plan* p, int nb, int MB, bool mixed) {
   const bool with_s = p->d_q != nullptr;
-  if (p->dav && p->dav->nb == nb && p->dav->MB == MB && p->dav->with_s == with_s &&
-      p->dav->mixed == mixed)
-    return PWK_OK;
-  destroy_dav_work(p);
+  int cnb = nb, cMB = MB;
+  bool cs = with_s, c32 = mixed;
+  if (DavWork* w0 = p->dav) {
+    if (!(w0->cap_nb >= nb && w0->cap_MB >= MB && (w0->has_s || !with_s) && (w0->has32 || !mixed))) {
+      cnb = std::max(nb, w0->cap_nb);
+      cMB = std::max(MB, w0->cap_MB);
+      cs = with_s || w0->has_s;
+      c32 = mixed || w0->has32;
+      destroy_dav_work(p);
+    }
+  }
+  if (p->dav == nullptr) {
+    if (int rc = alloc_dav_work(p, cnb, cMB, c32, cs)) return rc;
+  }
+  DavWork* w = p->dav;
+  w->nb = nb;
+  w->MB = MB;
+  w->with_s = with_s;
+  w->mixed = mixed;
+  return PWK_OK;
+}
+
+static int alloc_dav_work(pwk_plan* p, int nb, int MB, bool mixed, bool with_s) {
   DavWork* w = new DavWork();
   p->dav = w;
   w->nk = p->nk;
-  w->nb = nb;
-  w->MB = MB;
+  w->cap_nb = nb;
+  w->cap_MB = MB;
   w->npw_max = p->npw_max;
-  w->with_s = with_s;
-  w->mixed = mixed;
+  w->has_s = with_s;
+  w->has32 = mixed;
   const size_t nk = p->nk, np = p->npw_max;
   int rc;
   if (mixed && ((rc = dalloc(p, w, &w->phi32, nk * MB * np)) || (rc = dalloc(p, w, &w->hphi32, nk * MB * np)) ||

@@ -56,16 +56,24 @@ static int calloc_(pwk_plan* p, CgWork* w, T** ptr, size_t n) {
   return rc;
 }
 
+// Grows only, like the Davidson workspace: a call with at most the allocated number of
+// occupied bands (and an overlap the arrays cover) reuses it; arrays are indexed with the
+// call's nocc.
 static int ensure_cg_work(pwk_plan* p, int nocc) {
-  const bool with_s = p->d_q != nullptr;
-  if (p->cg && p->cg->nocc == nocc && p->cg->with_s == with_s) return PWK_OK;
+  const bool want_s = p->d_q != nullptr;
+  if (p->cg && p->cg->nocc >= nocc && (p->cg->with_s || !want_s)) return PWK_OK;
+  bool with_s = want_s;
+  if (p->cg) {
+    nocc = std::max(nocc, p->cg->nocc);
+    with_s = with_s || p->cg->with_s;
+  }
   destroy_cg_work(p);
   CgWork* w = new CgWork();
   p->cg = w;
   w->nk = p->nk;
-  w->nocc = nocc;
+  w->nocc = nocc;   // capacity
   w->np = p->npw_max;
-  w->with_s = with_s;
+  w->with_s = with_s;   // S arrays allocated
   const size_t nv = (size_t)p->nk * nocc, nv2 = nv * p->npw_max;
   int rc;
   if (with_s && ((rc = calloc_(p, w, &w->su, nv2)) || (rc = calloc_(p, w, &w->sx, nv2)))) {
@@ -446,13 +454,14 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
   }
   // S psi_{k+q,v} (FP64) when the plan has q; the H output of that call is not used
   const double2* su = psi_kq;
-  if (w->with_s) {
+  const bool with_s = pq->d_q != nullptr;   // this call applies S (the workspace may hold more)
+  if (with_s) {
     cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
     if ((rc = run_hpsi(pq, PWK_FP64, psi_kq, w->r, w->items, nullptr, npairs, nocc, nocc, st, w->su)))
       return rc;
     su = w->su;
   }
-  double2* const sx = w->with_s ? w->sx : nullptr;   // S applied to the operand of A
+  double2* const sx = with_s ? w->sx : nullptr;   // S applied to the operand of A
   // one warp per valence vector for the projections mu_v (8 to 16 warps)
   const int pc_threads = 32 * std::min(std::max(nocc, 8), 16);
   proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, su, nullptr, w->t,
