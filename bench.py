@@ -598,7 +598,19 @@ def run_other_cells(dev, stream, quick=False):
             row[name] = {"band_k_per_s": prob.nk * prob.nb / float(np.mean(ts)), "ms": float(np.mean(ts)) * 1e3}
         row["launch_shape_fp32"] = list(plan.launch_shape(pwk.PWK_FP32)[:3])
         row["projectors_fused_fp32"] = plan.projector_fused(pwk.PWK_FP32)
-        for path in (2, 3):
+        # the local kernel alone (the cell without projectors, same launch shape)
+        import copy
+        pl = copy.copy(prob)
+        pl.beta = np.ascontiguousarray(prob.beta[:, :0, :])
+        pl.D = np.zeros((0, 0))
+        plan_loc = pwk.plan_from_problem(pl, device=dev)
+        plan_loc.set_launch_shape(pwk.PWK_FP32, *plan.launch_shape(pwk.PWK_FP32)[:3])
+        x = torch.from_numpy(prob.psi).to(dev).to(torch.complex64)
+        y = torch.empty_like(x)
+        ts = [t for t, _ in T.run(lambda: pwk.hpsi_batched(plan_loc, pwk.PWK_FP32, x, y, prob.nb, stream), 10, 3)]
+        row["fp32_local_only_ms"] = float(np.mean(ts)) * 1e3
+        plan_loc.close()
+        for path in (1, 2, 3):
             plan.set_projector_path(path)
             x = torch.from_numpy(prob.psi).to(dev).to(torch.complex64)
             y = torch.empty_like(x)

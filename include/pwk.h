@@ -103,10 +103,11 @@ int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threa
  * finals) are applied:
  *   0 (default)  automatic: path 3 or path 2, whichever pwk_plan_create measured faster for
  *                each precision on the plan's own k-points (pwk_plan_projector_fused tells);
- *   1            separate kernels, the projections of FP32 batched calls on whole k-points on
- *                the 5th-generation tensor cores where they apply (nb + nkb <= 56, nkb <= 16):
- *                three TF32 products of a hi/lo split (FP32-level accuracy), FP32 accumulation
- *                in tensor memory; the add-back a CUDA-core kernel;
+ *   1            separate kernels, both contractions of FP32 batched calls on whole k-points
+ *                on the 5th-generation tensor cores where they apply (2 nkb <= 128, nb <= 128,
+ *                tiles within shared memory; the S add-back stays on the CUDA cores): three
+ *                TF32 products of a hi/lo split (FP32-level accuracy), FP32 accumulation in
+ *                tensor memory; other calls fall back to path 2;
  *   2            separate CUDA-core kernels: projections before the local kernel, add-back
  *                after it, beta(k) staged in shared memory for eight bands at a time;
  *   3            inside the local kernel, so a band-k item makes one HBM round trip (read C,

@@ -394,7 +394,9 @@ size_t nl_shared_bytes(int nkb, int precision) {
 }
 
 int launch_nl(int precision, const NlArgs& a, cudaStream_t st) {
-  if (a.tensor_cores && nl_project_tc_applies(precision, a)) return launch_nl_project_tc(precision, a, st);
+  // both contractions on the tensor cores where they apply (the coefficient scratch has the
+  // same layout on either path, so a phase may run on the tensor cores and the other not)
+  if (a.tensor_cores && nl_tcw_applies(precision, a)) return launch_nl_tcw(precision, a, st);
   switch (precision) {
     case PWK_FP64: return launch_nl_typed<double, double>(a, st);
     case PWK_FP32: return launch_nl_typed<float, float>(a, st);

@@ -190,9 +190,9 @@ struct NlArgs {
   long long wait_polls = 1LL << 24;   // bound on the polls of each device-side wait
 };
 int launch_nl(int precision, const NlArgs& a, cudaStream_t st);
-// tensor-core projection (nonlocal_tc.cu): whether it applies to a launch, and the launch
-int nl_project_tc_applies(int precision, const NlArgs& a);
-int launch_nl_project_tc(int precision, const NlArgs& a, cudaStream_t st);
+// tensor-core projection and add-back for wide projector sets (nonlocal_tcw.cu)
+int nl_tcw_applies(int precision, const NlArgs& a);
+int launch_nl_tcw(int precision, const NlArgs& a, cudaStream_t st);
 // stream-ordered scratch from the library's per-device pool (memory returned with
 // cudaFreeAsync stays mapped in the pool for later calls)
 cudaError_t scratch_alloc(void** ptr, size_t bytes, cudaStream_t st);

@@ -201,11 +201,12 @@ def test_every_launch_shape_gives_identical_results(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_c128"])
-@pytest.mark.parametrize("cfg,nks,nb", [(2, 6, 20), (1, 8, 8), (4, 5, 12), (2, 3, 44)])
+@pytest.mark.parametrize("cfg,nks,nb", [(2, 6, 20), (1, 8, 8), (4, 5, 12), (2, 3, 44), (3, 2, 40), (3, 2, 7)])
 def test_tensor_core_projections_match_cuda_cores_and_oracle(precision, cfg, nks, nb):
-    """The FP32 projections on the tensor cores (three TF32 products of a hi/lo split) and on
-    the CUDA cores both meet the FP32 bound against the oracle, and agree with each other to
-    FP32 rounding (nb + nkb up to 53 of the 56 the tensor-core kernel takes)."""
+    """The FP32 projector contractions on the tensor cores (projection and add-back, three TF32
+    products of a hi/lo split each) and on the CUDA cores both meet the FP32 bound against the
+    oracle, and agree with each other to FP32 rounding: 4, 9 and 36 projectors (cell 3: four
+    atoms), 7 to 44 bands, one and several tiles of 128 plane waves, ragged last tiles."""
     torch = torch_cuda()
     from paper_2412_01695_gb300 import pwk
     nkfull = int(np.prod(synth.CONFIGS[cfg]["mp"]))
