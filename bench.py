@@ -73,6 +73,9 @@ def src_digest(*names) -> str:
     return h.hexdigest()[:12]
 
 
+# projector paths (pwk_plan_projector_choice)
+PATH_NAMES = {1: "separate tensor-core kernels", 2: "separate CUDA-core kernels", 3: "fused in the local kernel"}
+
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of a kernel, from ncu captures
 # summarised under profiles/, with the digest of the sources they were captured at.
 TRAFFIC = {}
@@ -183,7 +186,9 @@ class Timer:
 
     def run(self, fn, steps, warmup, prep=None, flush=True):
         """CUDA-event time of each of `steps` calls of fn after `warmup` untimed ones; prep()
-        (untimed) and an L2 flush before every call."""
+        (untimed) and an L2 flush before every call.  self.launches: the library's kernel
+        launches inside the timed calls (pwk_launch_count before and after each)."""
+        from paper_2412_01695_gb300 import pwk
         torch = self.torch
         for _ in range(warmup):
             if prep:
@@ -191,6 +196,7 @@ class Timer:
             fn()
         torch.cuda.synchronize()
         out = []
+        self.launches = 0
         for _ in range(steps):
             if prep:
                 prep()
@@ -198,31 +204,14 @@ class Timer:
                 self.flush.fill_(1.0)
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
+            c0 = pwk.launch_count()
             a.record(self.stream)
             r = fn()
             b.record(self.stream)
+            self.launches += pwk.launch_count() - c0
             torch.cuda.synchronize()
             out.append((a.elapsed_time(b) / 1e3, r))
         return out
-
-
-def count_launches(torch, fn):
-    """Kernels of this library (namespace pwk) that one call of fn launches, counted from the
-    CUDA activity trace of torch.profiler on an extra, untimed call; None if the trace is not
-    available."""
-    try:
-        from torch.profiler import ProfilerActivity, profile
-        torch.cuda.synchronize()
-        with profile(activities=[ProfilerActivity.CUDA]) as prof:
-            fn()
-            torch.cuda.synchronize()
-        n = 0
-        for e in prof.events():
-            if getattr(e, "device_type", None) is not None and "CUDA" in str(e.device_type) and "pwk::" in e.name:
-                n += 1
-        return n or None
-    except Exception:   # no CUPTI on this host: the count is left out
-        return None
 
 
 def fma_peaks(torch, dev, stream):
@@ -296,11 +285,13 @@ def run_headline(args, torch, dev, stream, world, peaks):
     clk = ClockSampler(dev.index or 0)
     clk.start()
     steps = T.run(solve, args.steps, args.warmup, prep=prep)
+    launches = T.launches
     clocks = clk.stop()
     times = np.array([t for t, _ in steps])
     last = steps[-1][1]
     applies = last["applies_fp64"] + last["applies_fp32"]
     total_units, step_s, _ = aggregate(applies, float(np.mean(times)))
+    launches = int(aggregate(launches, 0.0)[0])   # every rank's launches
     eig_mixed = eig.cpu().numpy()
     st = last["stats"]
     # where the solve spends its device time; the dominant part sets the roofline line
@@ -384,9 +375,8 @@ def run_headline(args, torch, dev, stream, world, peaks):
                   "d2h_bytes_per_step": int(h_psi.numel() * h_psi.element_size() + h_eig.numel() * 8),
                   "call": "pwk_davidson_batched with the trial vectors copied in from pinned host memory and "
                           "eigenvectors + eigenvalues copied out, inside the timed region"}
-    launches = count_launches(torch, lambda: (prep(), solve()))
-    res["gpu_launches"] = launches * args.steps if launches else None
-    res["gpu_launches_per_step"] = launches
+    res["gpu_launches"] = launches
+    res["gpu_launches_per_step"] = launches / args.steps
     plan.close()
     return res, prob, eig_mixed, eig64.cpu().numpy()
 
@@ -431,8 +421,7 @@ def run_hpsi_kernels(args, torch, dev, stream, peaks):
     te = [t for t, _ in T.run(lambda: pwk.hpsi_batched_host(plan, pwk.PWK_FP32, h_in, h_out, d_in, d_out, nb, 4,
                                                             stream), min(n, 50), 3)]
     # each way of applying the projector terms (pwk_plan_set_projector_path), FP32 batched
-    paths = {"automatic_choice": "fused in the local kernel" if plan.projector_fused(pwk.PWK_FP32)
-             else "separate kernels"}
+    paths = {"automatic_choice": PATH_NAMES.get(plan.projector_choice(pwk.PWK_FP32), "none")}
     for path, name in ((2, "separate_cuda_core_kernels"), (3, "fused_in_local_kernel"), (1, "tensor_core_projection")):
         plan.set_projector_path(path)
         tp = [t for t, _ in T.run(lambda: pwk.hpsi_batched(plan, pwk.PWK_FP32, psi32, out32, nb, stream), n, 5)]
@@ -597,7 +586,7 @@ def run_other_cells(dev, stream, quick=False):
                                       10 if name == "fp32" else 3, 3)]
             row[name] = {"band_k_per_s": prob.nk * prob.nb / float(np.mean(ts)), "ms": float(np.mean(ts)) * 1e3}
         row["launch_shape_fp32"] = list(plan.launch_shape(pwk.PWK_FP32)[:3])
-        row["projectors_fused_fp32"] = plan.projector_fused(pwk.PWK_FP32)
+        row["projector_path_fp32"] = PATH_NAMES.get(plan.projector_choice(pwk.PWK_FP32), "none")
         # the local kernel alone (the cell without projectors, same launch shape)
         import copy
         pl = copy.copy(prob)
@@ -795,7 +784,7 @@ def run_case(args):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
             rc, iters, notc, napply = pwk.davidson_batched(plan, mode, psi, eig, prob.nb, ETH, RES_TOL,
-                                                           args.max_iter, 0)
+                                                           args.max_iter, args.max_basis)
             b.record()
             torch.cuda.synchronize()
             times.append(a.elapsed_time(b))
@@ -829,6 +818,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--max-iter", type=int, default=MAX_ITER)
     ap.add_argument("--projector-path", type=int, default=0)
+    ap.add_argument("--max-basis", type=int, default=0, help="Davidson basis bound (0: 4 nb)")
     args = ap.parse_args()
     if args.case:
         return run_case(args)

@@ -1,7 +1,7 @@
 /* pwk.h - C ABI of the many-k plane-wave Kohn-Sham library for one GB300 (sm_103a).
  *
  * The library applies the Kohn-Sham Hamiltonian to the Bloch wave-functions of many
- * k-points and bands at once (Gong & Dal Corso, arXiv:2412.01695, Sec. 2.2 and Sec. 4),
+ * k-points and bands at once (Gong & Dal Corso, arXiv:2412.01695, Sec. 2.2 and Sec. 3),
  * drives a batched block-Davidson eigensolver (Sec. 2.1, Algorithm 2) and a batched DFPT
  * Sternheimer preconditioned CG (Sec. 2.3-2.4, Algorithm 4) on the device.
  *
@@ -12,7 +12,7 @@
  *   complex numbers are interleaved (re, im): complex128 = 2 x double, complex64 = 2 x float;
  *   wave-function arrays are [nk][nvec][npw_max], coefficient index fastest; entries
  *   beyond npw(k) are padding: they must be zero on input and are written as zero on output;
- *   real-space grids are [N1][N2][N3] with l3 fastest, r_l = sum_i (l_i/N_i) a_i (Sec. 5).
+ *   real-space grids are [N1][N2][N3] with l3 fastest, r_l = sum_i (l_i/N_i) a_i (Sec. 4).
  *   Miller indices (m1, m2, m3) give G = m1 b1 + m2 b2 + m3 b3 with a_i . b_j = 2 pi delta_ij.
  *
  * Ownership: every device array passed in is owned by the caller and must stay alive and
@@ -55,8 +55,8 @@ typedef struct pwk_plan pwk_plan; /* opaque */
 
 /* ---------------------------------------------------------------------------- plans
  * pwk_plan_create: describe one cell, one FFT grid and one set of nk k-points with their
- * plane-wave spheres and projectors (paper Sec. 4: the data loaded on the GPU for a block
- * of N_k k-points before the Davidson or CG starts; Sec. 5 for the grids).
+ * plane-wave spheres and projectors (paper Sec. 3: the data loaded on the GPU for a block
+ * of N_k k-points before the Davidson or CG starts; Sec. 4 for the grids).
  *   A        host [3][3]   lattice vectors a_i as rows (bohr)
  *   N1,N2,N3               FFT grid; N1 = N2 = N3 = N with N in pwk_supported_grid()
  *   nk                     number of k-points (>= 1)
@@ -101,8 +101,9 @@ int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threa
 
 /* How the nonlocal projector terms (Eqs. lambdah, gamma, finalnl; with q also delta_eq,
  * finals) are applied:
- *   0 (default)  automatic: path 3 or path 2, whichever pwk_plan_create measured faster for
- *                each precision on the plan's own k-points (pwk_plan_projector_fused tells);
+ *   0 (default)  automatic: path 3, path 2 or (FP32 arithmetic) path 1, whichever
+ *                pwk_plan_create measured fastest for each precision as whole H applications of
+ *                32 bands on the plan's own k-points (pwk_plan_projector_choice tells);
  *   1            separate kernels, both contractions of FP32 batched calls on whole k-points
  *                on the 5th-generation tensor cores where they apply (2 nkb <= 128, nb <= 128,
  *                tiles within shared memory; the S add-back stays on the CUDA cores): three
@@ -121,6 +122,11 @@ int pwk_plan_set_projector_path(pwk_plan* plan, int path);
 /* 1 if H|psi> of this precision applies the projector terms inside the local kernel (path 3,
  * or path 0 where the plan chose it), else 0; -1 for a null plan or unknown precision. */
 int pwk_plan_projector_fused(const pwk_plan* plan, int precision);
+/* The projector path H|psi> of this precision takes on whole-k-point batched calls under the
+ * plan's current setting: 3 (inside the local kernel), 1 (separate tensor-core kernels), 2
+ * (separate CUDA-core kernels), 0 if the plan has no projectors; -1 for a null plan or unknown
+ * precision.  (Calls outside the tensor-core kernels' limits take path 2 where this says 1.) */
+int pwk_plan_projector_choice(const pwk_plan* plan, int precision);
 
 /* Device-side conditions the kernels of a plan recorded since the last clear (bit flags):
  *   PWK_FLAG_ITEM_SKIPPED  a work-list entry outside the plan was skipped (pwk_hpsi_items)
@@ -141,9 +147,9 @@ int pwk_supported_grid(int N);
 
 /* ---------------------------------------------------------------------------- H|psi>
  * pwk_hpsi_batched: hpsi = H_KS psi for nb bands of every k of the plan (paper Sec. 2.2,
- * Sec. 4 "routine that applies H_KS ... for N_k k points"):
+ * Sec. 3 "routine that applies H_KS ... for N_k k points"):
  *   kinetic |k+G|^2 C (Sec. 2.2.1), local V_eff by scatter G->r, inverse 3D transform,
- *   V(r) u(r), forward 3D transform with 1/N_r and gather r->G (Sec. 2.2.2, Sec. 5),
+ *   V(r) u(r), forward 3D transform with 1/N_r and gather r->G (Sec. 2.2.2, Sec. 4),
  *   nonlocal lambda = sum_G beta* C (Eq. lambdah), gamma = D lambda (Eq. gamma),
  *   add-back sum gamma beta (Eq. finalnl).  S is not applied (pwk_hspsi_batched does).
  *   precision  PWK_FP64, PWK_FP32 or PWK_FP32_C128
@@ -194,7 +200,7 @@ int pwk_hpsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, c
 
 /* pwk_hpsi_multi: H|psi> on one work list whose entries belong to several plans -- cells with
  * their own atoms and projector sets (nkb may differ, 0 included), D, V(r), spheres and
- * k-points -- applied in a single launch (the paper batches the k-points of one cell, Sec. 4;
+ * k-points -- applied in a single launch (the paper batches the k-points of one cell, Sec. 3;
  * this extends the batch across cells that share an FFT grid, so uneven projector sets do
  * not split the work into one launch per cell).
  *   nplans      number of plans (>= 1); plans[i] the plan of cell i; all on one device with
@@ -246,7 +252,7 @@ int pwk_hspsi_items(pwk_plan* plan, int precision, const void* psi, void* hpsi, 
  * pwk_davidson_batched: lowest nb eigenpairs of H(k) for every k of the plan by the block
  * Davidson iteration of Sec. 2.1, run for all k at once (Algorithm 2):
  *   Rayleigh-Ritz on the basis (H~ = <phi|H|phi>, S~ = <phi|S|phi>, FP64 Cholesky of S~ and
- *   Hermitian eigensolve, Sec. 6), correction vectors (H_diag - eps S_diag)^-1 (H - eps S) phi,
+ *   Hermitian eigensolve, Sec. 5), correction vectors (H_diag - eps S_diag)^-1 (H - eps S) phi,
  *   normalisation, basis expansion, restart with the Ritz vectors when the basis would
  *   exceed max_basis, per-band test |eps^(n+1) - eps^(n)| > eth.
  *   mode     PWK_FP64: every H application in FP64.
@@ -296,7 +302,7 @@ int pwk_drho_batched(pwk_plan* plan_kq, pwk_plan* plan_k, int precision, const v
                      void* drho, void* stream);
 
 /* pwk_eigh_batched: the batched generalized Hermitian eigensolver of the Davidson reduced
- * problem as a stand-alone call (paper Sec. 6: ZHEGV for many k-points at once).  For each
+ * problem as a stand-alone call (paper Sec. 5: ZHEGV for many k-points at once).  For each
  * problem p < nprob: H_p v = eps S_p v, the nev lowest eigenpairs, FP64, one CTA per problem
  * (Cholesky of S, reduction to standard form, Householder tridiagonalisation, bisection and inverse iteration).
  *   H, S    device complex128 [nprob][n][n], row-major, full Hermitian; S positive definite
@@ -368,7 +374,7 @@ int pwk_sternheimer_cg_batched(pwk_plan* plan_kq, pwk_plan* plan_k, int mode,
 
 /* ---------------------------------------------------------------------------- solver timing
  * Where a solver call spends its device time (the paper splits its run times the same way:
- * H and S application, FFTs, reduced diagonalisation; Sec. 7, Tables 1-3).
+ * H and S application, FFTs, reduced diagonalisation; Sec. 6, Tables 1-3).
  * pwk_plan_set_solver_timing(plan, 1) makes pwk_davidson_batched and
  * pwk_sternheimer_cg_batched (plan_kq) record CUDA events around their phases on their stream
  * (read after the synchronisations the solvers make anyway; 8 bytes of device memory for a
@@ -392,13 +398,19 @@ int pwk_plan_solver_stats(const pwk_plan* plan, double* stats);
  * (eight CTAs of 256 threads per SM, sixteen chains per thread), best of three timed launches
  * after a warm-up, CUDA events on `stream`.  The roofline denominator of the kernels bound by
  * these pipes: the transforms of the H|psi> kernel (FP32 or FP64), the reduced eigensolver
- * and the CG reductions (FP64); the paper states its peaks per node (Sec. 7) but no per-kernel
+ * and the CG reductions (FP64); the paper states its peaks per node (Sec. 6) but no per-kernel
  * fraction, so this has no counterpart there.
  *   precision   PWK_FP32 or PWK_FP64 (PWK_ERR_INVALID otherwise)
  *   flops_per_s host double out (may be NULL)
  *   sm_count    host int out: the device's multiprocessor count (may be NULL)
  * Takes about 0.1-0.3 s; synchronises `stream`; 8 bytes of scratch from the library's pool. */
 int pwk_measure_fma_peak(int precision, double* flops_per_s, int* sm_count, void* stream);
+
+/* pwk_launch_count: how many kernels the library has launched in this process since it was
+ * loaded (every launch of every entry point, counted on the host as it is queued; all devices
+ * and threads together).  The difference of two readings around a region counts that region's
+ * launches.  Never fails. */
+long long pwk_launch_count(void);
 
 /* ---------------------------------------------------------------------------- misc */
 const char* pwk_strerror(int code);

@@ -7,7 +7,7 @@ maps) and uses no FFT library: every Fourier sum is written out as a direct sum.
 
 Modules
   hamiltonian  -- kinetic, local (dense convolution and direct Fourier sums),
-                  nonlocal projector terms; dense H(k); H|psi>  (paper Sec. 2.2, Sec. 5)
+                  nonlocal projector terms; dense H(k); H|psi>  (paper Sec. 2.2, Sec. 4)
   davidson     -- the block Davidson iteration of Sec. 2.1 and the dense reference
   sternheimer  -- right-hand side, operator, dense solve and the PCG of Sec. 2.4 (Eq. linear_system)
 

@@ -4,7 +4,7 @@ Follows the steps of paper Sec. 2.1 in order, in FP64, for one k at a time, with
 (norm-conserving projectors) unless an overlap operator S is passed (ultrasoft/PAW q_mn,
 Sec. 2.2; oracle/overlap.py builds it).  The reduced generalized problem (H~ - eps S~) v = 0
 is solved with LAPACK (scipy.linalg.eigh), which the paper also uses for this step
-(Sec. 6, ZHEGV/ZHEGVX).  ``lowest_eigenpairs`` is the exact result the iteration reaches.
+(Sec. 5, ZHEGV/ZHEGVX).  ``lowest_eigenpairs`` is the exact result the iteration reaches.
 
 Readings of points the paper leaves open (listed with the design notes):
   * the preconditioner denominator x = H_GG - eps_i S_GG is clamped to sign(x) max(|x|, 1e-2 Ry);

@@ -6,7 +6,7 @@ Everything is FP64.  Two independent routes are provided for the local term:
   * ``local_matrix``: the exact G-space definition reached by the FFT method, a circular
     convolution with the grid coefficients V~(m) = (1/N_r) sum_r V(r) e^{-2 pi i m.l/N};
   * ``hpsi_direct``: the paper's own route written as direct Fourier sums (Sec. 2.2.2,
-    u = sum_G C e^{iG.r}, u' = V u, C' = (1/N_r) sum_r u' e^{-iG.r}; Sec. 5, Eq. fwFFT),
+    u = sum_G C e^{iG.r}, u' = V u, C' = (1/N_r) sum_r u' e^{-iG.r}; Sec. 4, Eq. fwFFT),
     O(npw * N_r) per band, no FFT.
 
 Parity pins live in tests/test_oracle_*.py (free electrons, constant shift, single
@@ -18,7 +18,7 @@ import numpy as np
 
 
 def reciprocal(A: np.ndarray) -> np.ndarray:
-    """Rows b_i with a_i . b_j = 2 pi delta_ij (Sec. 5, the mesh G_{m1,m2,m3})."""
+    """Rows b_i with a_i . b_j = 2 pi delta_ij (Sec. 4, the mesh G_{m1,m2,m3})."""
     return 2.0 * np.pi * np.linalg.inv(A).T
 
 
@@ -34,7 +34,7 @@ def _dft_matrix(N: int, sign: int) -> np.ndarray:
 
 
 def grid_coefficients(f_r: np.ndarray) -> np.ndarray:
-    """f~(m) = (1/N_r) sum_l f(l) e^{-2 pi i m.l/N} for all m mod N (Sec. 5, Eq. fwFFT).
+    """f~(m) = (1/N_r) sum_l f(l) e^{-2 pi i m.l/N} for all m mod N (Sec. 4, Eq. fwFFT).
 
     Written as three separable direct sums over l3, l2, l1 (no FFT library)."""
     N1, N2, N3 = f_r.shape

@@ -12,7 +12,7 @@ both against closed forms.
 
 Generalized problems:
   * H x = eps S x (Eq. ks with S): ``lowest_generalized`` (LAPACK through scipy, as the
-    paper's ZHEGV step of Sec. 6);
+    paper's ZHEGV step of Sec. 5);
   * the DFPT system of Eq. linear_system with S (dS = 0, the perturbation being a local
     potential dv):  [H_{k+q} + alpha Q - eps S] dpsi = -P_c^dagger dV psi, with
     alpha Q = alpha sum_v S|u_v><u_v|S (Eq. projector) and P_c^dagger = 1 - S P_v,

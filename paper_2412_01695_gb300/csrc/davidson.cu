@@ -700,26 +700,26 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   float2* const sphi32 = w->with_s ? w->sphi32 : w->phi32;
   hdiag_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>(nk, np, p->nkb, p->d_npw, p->d_g2, p->v_mean,
                                                         p->d_beta, p->d_D, w->hdiag, p->d_q,
-                                                        w->with_s ? w->sdiag : nullptr);
+                                                        w->with_s ? w->sdiag : nullptr); note_launch();
   if (mixed) {
-    to_float_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>((size_t)nk * np, w->hdiag, w->hdiag32);
-    if (w->with_s) to_float_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>((size_t)nk * np, w->sdiag, w->sdiag32);
+    to_float_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>((size_t)nk * np, w->hdiag, w->hdiag32); note_launch();
+    if (w->with_s) { to_float_kernel<<<blocks((size_t)nk * np), 256, 0, st>>>((size_t)nk * np, w->sdiag, w->sdiag32); note_launch(); }
   }
   KCHECK("hdiag_kernel");
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, 1);
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iters, 0);
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->status, 0);
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, 0);
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->force, 0);
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->failcount, 0);
-  fill_int_kernel<<<1, 32, 0, st>>>(4, w->dbg, 0);
-  fill_int_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk * nb, w->lastrow, -1);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->active, 1); note_launch();
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iters, 0); note_launch();
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->status, 0); note_launch();
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, 0); note_launch();
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->force, 0); note_launch();
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->failcount, 0); note_launch();
+  fill_int_kernel<<<1, 32, 0, st>>>(4, w->dbg, 0); note_launch();
+  fill_int_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk * nb, w->lastrow, -1); note_launch();
   if (mixed)
-    copy_vecs_kernel<double, float><<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi32, MB, 0, nullptr,
-                                                             nullptr, 0);
+    { copy_vecs_kernel<double, float><<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi32, MB, 0, nullptr,
+                                                             nullptr, 0); note_launch(); }
   else
-    copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi, MB, 0, nullptr,
-                                                              nullptr, 0);
+    { copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, psi, nb, 0, w->phi, MB, 0, nullptr,
+                                                              nullptr, 0); note_launch(); }
   KCHECK("davidson init");
 
   // Phase 1 (mixed mode) stops at the FP32 noise floor: eigenvalues of the reduced problem
@@ -736,26 +736,26 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   // a k-point still short of the FP32 floor after 60 correction steps (a slow band next to a
   // small gap) finishes in FP64 instead of spending the rest of max_iter in FP32
   const int cap1 = std::max(1, std::min(max_iter / 2, 60));
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->phase, mixed ? 1 : 2);
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->switchk, 0);
-  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, 0);
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->phase, mixed ? 1 : 2); note_launch();
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->switchk, 0); note_launch();
+  fill_int_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, 0); note_launch();
 
   // new columns of H~, S~ for the k-points in mask, in the precision of their phase
   auto gram = [&](const int* mask, const int* base, int base_const, const int* cnt, int cnt_const) {
     if (mixed)
-      gram_kernel<float><<<nk * nb, 256, gram_smem / 2, st>>>(nb, MB, np, p->d_npw, mask, base, base_const, cnt,
+      { gram_kernel<float><<<nk * nb, 256, gram_smem / 2, st>>>(nb, MB, np, p->d_npw, mask, base, base_const, cnt,
                                                              cnt_const, w->phi32, w->hphi32, sphi32, w->Hr,
-                                                             w->Sr, w->phase, 1);
+                                                             w->Sr, w->phase, 1); note_launch(); }
     gram_kernel<double><<<nk * nb, 256, gram_smem, st>>>(nb, MB, np, p->d_npw, mask, base, base_const, cnt,
                                                          cnt_const, w->phi, w->hphi, sphi, w->Hr, w->Sr,
-                                                         w->phase, want64);
+                                                         w->phase, want64); note_launch();
   };
 
   // H on phi[0:nb] of the k-points in mask (all in phase ph), their nb x nb reduced matrices
   // and eigensolve
   auto start_block = [&](int ph, int* mask, int count) -> int {
     items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, mask, nullptr, 0, nullptr, nb,
-                                                          w->phase, 0, w->items);
+                                                          w->phase, 0, w->items); note_launch();
     KCHECK("items_kernel");
     cudaEvent_t th = T.mark();
     int r = ph == 1 ? run_hpsi(p, PWK_FP32, w->phi32, w->hphi32, w->items, nullptr, nk * nb, MB, MB, st,
@@ -767,7 +767,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
     napply[ph == 2 ? 0 : 1] += (long long)count * nb;
     gram(mask, nullptr, 0, nullptr, nb);
     KCHECK("gram_kernel");
-    set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, mask, w->nbase, nb, nullptr);
+    set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, mask, w->nbase, nb, nullptr); note_launch();
     cudaEvent_t tr = T.mark();
     r = launch_rr(nk, MB, nb, w->nbase, mask, w->Hr, w->Sr, w->W, w->ev, w->eps_new, w->status, st,
                   w->drop, rr_flops);
@@ -779,7 +779,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->active, 1,
                                                          w->eps_new, w->eps, w->moved, w->status,
                                                          nullptr, w->nbase, w->force, w->failcount,
-                                                         w->dbg);
+                                                         w->dbg); note_launch();
   KCHECK("update_kernel");
 
   int it = 0;
@@ -787,21 +787,21 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
   const int allb = (rt1 > 0 || res_tol > 0) ? 1 : 0;
   for (;;) {
     if (mixed)
-      resid_kernel<float><<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved, allb,
+      { resid_kernel<float><<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved, allb,
                                                    w->ev, w->eps, w->phi32, w->hphi32, sphi32, w->hdiag32,
                                                    w->with_s ? w->sdiag32 : nullptr, w->drop, w->lastrow,
-                                                   w->corr32, w->rnorm, w->phase, 1);
+                                                   w->corr32, w->rnorm, w->phase, 1); note_launch(); }
     resid_kernel<double><<<nk * nb, 256, 0, st>>>(nb, MB, np, p->d_npw, w->nbase, w->active, w->moved, allb,
                                                   w->ev, w->eps, w->phi, w->hphi, sphi, w->hdiag,
                                                   w->with_s ? w->sdiag : nullptr, w->drop, w->lastrow,
-                                                  w->corr, w->rnorm, w->phase, want64);
+                                                  w->corr, w->rnorm, w->phase, want64); note_launch();
     KCHECK("resid_kernel");
     cudaMemsetAsync(w->counters, 0, 8 * sizeof(int), st);
     cudaMemsetAsync(w->counters + 2, 0xff, sizeof(int), st);
     select_kernel<<<blocks(nk), 256, 0, st>>>(nk, nb, MB, rt1, res_tol, cap1, w->active, w->phase,
                                               w->moved, w->rnorm, w->nbase, w->todo, w->nnc,
                                               w->restart, w->iters, w->status, w->force,
-                                              w->failcount, w->switchk, w->iterk, w->counters);
+                                              w->failcount, w->switchk, w->iterk, w->counters); note_launch();
     KCHECK("select_kernel");
     cudaError_t ce = cudaMemcpyAsync(hc, w->counters, 8 * sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(host_dbg, w->dbg, 4 * sizeof(int), cudaMemcpyDeviceToHost, st);
@@ -829,65 +829,65 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       // FP64 refinement start of the k-points leaving phase 1: their Ritz vectors from the
       // FP32 basis, in FP64, then FP64 H on them
       rotate_kernel<float, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->switchk, w->ev, w->phi32,
-                                                            w->tmp1, nb, nullptr, 0);
+                                                            w->tmp1, nb, nullptr, 0); note_launch();
       copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0,
-                                                                w->switchk, nullptr, 0);
-      set_value_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->switchk, w->phase, 2);
+                                                                w->switchk, nullptr, 0); note_launch();
+      set_value_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->switchk, w->phase, 2); note_launch();
       KCHECK("phase switch");
       if ((rc = start_block(2, w->switchk, nswitch))) return rc;
       update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->switchk, 0,
                                                              w->eps_new, w->eps, w->moved, w->status,
                                                              nullptr, w->nbase, w->force, w->failcount,
-                                                             w->dbg);
+                                                             w->dbg); note_launch();
       KCHECK("update_kernel");
     }
     if (total > 0) {
       // restart the k-points whose basis would overflow
       if (mixed) {
         rotate_kernel<float, float><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->phi32,
-                                                             w->t32a, nb, w->phase, 1);
+                                                             w->t32a, nb, w->phase, 1); note_launch();
         rotate_kernel<float, float><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->hphi32,
-                                                             w->t32b, nb, w->phase, 1);
+                                                             w->t32b, nb, w->phase, 1); note_launch();
         copy_vecs_kernel<float, float><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->t32a, nb, 0, w->phi32, MB, 0,
-                                                                w->restart, w->phase, 1);
+                                                                w->restart, w->phase, 1); note_launch();
         copy_vecs_kernel<float, float><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->t32b, nb, 0, w->hphi32, MB, 0,
-                                                                w->restart, w->phase, 1);
+                                                                w->restart, w->phase, 1); note_launch();
         if (w->with_s) {
           rotate_kernel<float, float><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev,
-                                                               w->sphi32, w->t32c, nb, w->phase, 1);
+                                                               w->sphi32, w->t32c, nb, w->phase, 1); note_launch();
           copy_vecs_kernel<float, float><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->t32c, nb, 0, w->sphi32, MB, 0,
-                                                                  w->restart, w->phase, 1);
+                                                                  w->restart, w->phase, 1); note_launch();
         }
       }
       rotate_kernel<double, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->phi,
-                                                             w->tmp1, nb, w->phase, want64);
+                                                             w->tmp1, nb, w->phase, want64); note_launch();
       rotate_kernel<double, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev, w->hphi,
-                                                             w->tmp2, nb, w->phase, want64);
+                                                             w->tmp2, nb, w->phase, want64); note_launch();
       copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp1, nb, 0, w->phi, MB, 0,
-                                                                w->restart, w->phase, want64);
+                                                                w->restart, w->phase, want64); note_launch();
       copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp2, nb, 0, w->hphi, MB, 0,
-                                                                w->restart, w->phase, want64);
+                                                                w->restart, w->phase, want64); note_launch();
       if (w->with_s) {
         rotate_kernel<double, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, w->restart, w->ev,
-                                                               w->sphi, w->tmp3, nb, w->phase, want64);
+                                                               w->sphi, w->tmp3, nb, w->phase, want64); note_launch();
         copy_vecs_kernel<double, double><<<nk * nb, 256, 0, st>>>(nk, nb, np, w->tmp3, nb, 0, w->sphi, MB, 0,
-                                                                  w->restart, w->phase, want64);
+                                                                  w->restart, w->phase, want64); note_launch();
       }
       gram(w->restart, nullptr, 0, nullptr, nb);
-      set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, w->nbase, nb, nullptr);
+      set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->restart, w->nbase, nb, nullptr); note_launch();
       KCHECK("davidson restart");
       // append the corrections, apply H to them (FP32 for phase-1 k, FP64 for phase-2 k)
       if (mixed)
-        append_kernel<float><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->iterk, w->nbase, w->nnc, w->todo,
-                                                      w->corr32, w->phi32, w->lastrow, w->phase, 1);
+        { append_kernel<float><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->iterk, w->nbase, w->nnc, w->todo,
+                                                      w->corr32, w->phi32, w->lastrow, w->phase, 1); note_launch(); }
       append_kernel<double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->iterk, w->nbase, w->nnc, w->todo, w->corr,
-                                                     w->phi, w->lastrow, w->phase, want64);
+                                                     w->phi, w->lastrow, w->phase, want64); note_launch();
       KCHECK("davidson append");
       for (int ph = 1; ph <= 2; ++ph) {
         const int cnt = ph == 2 ? n64 : total - n64;
         if (cnt == 0) continue;
         items_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, w->iterk, w->nbase, 0, w->nnc, 0,
-                                                              w->phase, ph, w->items);
+                                                              w->phase, ph, w->items); note_launch();
         KCHECK("items_kernel");
         cudaEvent_t th = T.mark();
         if (ph == 1) {
@@ -903,7 +903,7 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
         napply[ph == 2 ? 0 : 1] += cnt;
       }
       gram(w->iterk, w->nbase, 0, w->nnc, 0);
-      set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, w->nbase, 0, w->nnc);
+      set_nbase_kernel<<<blocks(nk), 256, 0, st>>>(nk, w->iterk, w->nbase, 0, w->nnc); note_launch();
       KCHECK("davidson gram");
       cudaEvent_t tr = T.mark();
       if ((rc = launch_rr(nk, MB, nb, w->nbase, w->iterk, w->Hr, w->Sr, w->W, w->ev, w->eps_new,
@@ -914,17 +914,17 @@ extern "C" int pwk_davidson_batched(pwk_plan* p, int mode, void* psi_v, double* 
       update_kernel<<<blocks((size_t)nk * nb), 256, 0, st>>>(nk, nb, eth1, eth, w->phase, w->iterk, 0,
                                                              w->eps_new, w->eps, w->moved, w->status,
                                                              w->nnc, w->nbase, w->force, w->failcount,
-                                                             w->dbg);
+                                                             w->dbg); note_launch();
       KCHECK("update_kernel");
     }
   }
   // eigenvectors out: psi = phi v (from the FP32 basis for k-points still in phase 1);
   // eigenvalues out
   if (mixed)
-    rotate_kernel<float, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi32, psi,
-                                                          nb, w->phase, 1);
+    { rotate_kernel<float, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi32, psi,
+                                                          nb, w->phase, 1); note_launch(); }
   rotate_kernel<double, double><<<nk * nb, 256, 0, st>>>(nb, MB, np, w->nbase, nullptr, w->ev, w->phi, psi, nb,
-                                                         w->phase, want64);
+                                                         w->phase, want64); note_launch();
   KCHECK("final rotate");
   cudaError_t ce = cudaMemcpyAsync(eig, w->eps, sizeof(double) * nk * nb, cudaMemcpyDeviceToDevice, st);
   std::vector<int> h_iters(nk), h_nnc(nk);

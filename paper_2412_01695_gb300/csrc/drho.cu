@@ -7,7 +7,7 @@
 // sum_v u_{k+q,v} <S u_{k+q,v}|du> (S = 1 without q).  The augmentation term is not included
 // (the paper did not accelerate it).
 //
-// The paper keeps two full FFT grids per band in HBM for this step (Sec. 6).  Here one CTA
+// The paper keeps two full FFT grids per band in HBM for this step (Sec. 3).  Here one CTA
 // takes one (k, nu) pair at a time: both coefficient sets are scattered onto the union of the
 // two spheres' z-sticks in shared memory (the transfer maps of the k -> k+q pair), both are
 // transformed z on the sticks, y on the carried m1 planes, x on every line, and the product
@@ -225,7 +225,7 @@ int launch_drho_typed(int N, const DrhoArgs& a, int nparts, size_t smem, cudaStr
     auto kern = drho_kernel<T, n>;                                                               \
     cudaError_t e = allow_full_smem(kern);                                                       \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(drho)");                     \
-    kern<<<nparts, 256, smem, st>>>(a);                                                          \
+    kern<<<nparts, 256, smem, st>>>(a); note_launch();                                                          \
     e = cudaGetLastError();                                                                      \
     return e == cudaSuccess ? PWK_OK : cuda_fail(e, "drho_kernel");                              \
   }
@@ -294,7 +294,7 @@ extern "C" int pwk_drho_batched(pwk_plan* pq, pwk_plan* pk, int precision, const
   }
   const double2* suv = static_cast<const double2*>(psi_kq);
   if (pq->d_q != nullptr) {   // S u_{k+q,v}: the projector terms alone
-    pair_items_kernel<<<(npairs + 255) / 256, 256, 0, st>>>(npairs, nocc, items);
+    pair_items_kernel<<<(npairs + 255) / 256, 256, 0, st>>>(npairs, nocc, items); note_launch();
     e = cudaGetLastError();
     rc = e == cudaSuccess ? run_hpsi(pq, PWK_FP64, psi_kq, nullptr, items, nullptr, npairs, nocc, nocc, st, su)
                           : cuda_fail(e, "pair_items_kernel");
@@ -302,7 +302,7 @@ extern "C" int pwk_drho_batched(pwk_plan* pq, pwk_plan* pk, int precision, const
   }
   if (rc == PWK_OK) {
     conduction_kernel<<<npairs, 256, 0, st>>>(nocc, npq, pq->d_npw, static_cast<const double2*>(psi_kq), suv,
-                                              static_cast<const double2*>(dpsi), duc);
+                                              static_cast<const double2*>(dpsi), duc); note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "conduction_kernel");
   }
@@ -332,7 +332,7 @@ extern "C" int pwk_drho_batched(pwk_plan* pq, pwk_plan* pk, int precision, const
   }
   if (rc == PWK_OK) {
     drho_reduce_kernel<<<(int)((nr + 255) / 256), 256, 0, st>>>((int)nr, nparts, part,
-                                                                static_cast<double2*>(drho));
+                                                                static_cast<double2*>(drho)); note_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) rc = cuda_fail(e, "drho_reduce_kernel");
   }

@@ -1,6 +1,6 @@
 // Register-resident complex DFT of one line of compile-time length N (N = 2^a 3^b 5^c).
 //
-// Used for the one-dimensional passes of the 3D transform of paper Sec. 5
+// Used for the one-dimensional passes of the 3D transform of paper Sec. 4
 // (Eqs. zfft, yfft, xfft and fwFFT): every line is owned by one thread and lives in
 // registers.  The factorisation is a two-level Cooley-Tukey split N = R * M applied
 // recursively (R = 4, 2, 3 or 5), with explicit radix-2/3/4/5 butterflies.  Every index

@@ -3,8 +3,8 @@
 // The nonlocal projector terms run as separate kernels around it (nonlocal.cu): their
 // projections over all bands of a k-point share one staged copy of beta(k).
 //
-// Per work item (paper Sec. 2.2 and Sec. 5, Fig. 2 flow, here fused into one kernel):
-//   1. load C(G) and scatter it onto the z-sticks held in shared memory (Sec. 4 "sets the
+// Per work item (paper Sec. 2.2 and Sec. 4, Fig. 2 flow, here fused into one kernel):
+//   1. load C(G) and scatter it onto the z-sticks held in shared memory (Sec. 3 "sets the
 //      non zero elements of this grid");
 //   2. inverse z transforms, only on the sticks (m1, m2) that carry coefficients (Eq. zfft);
 //   3. for each chunk of L planes l3: inverse y transforms on the m1 planes that carry
@@ -260,7 +260,7 @@ int launch_fused(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, c
     auto kern = fused_kernel<T, TI, n, CPLXV, NL>;                                                  \
     cudaError_t e = allow_full_smem(kern);                                                      \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(fused)");                   \
-    kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \
+    kern<<<nblocks, s.threads, s.smem, st>>>(a); note_launch();                                                \
     e = cudaGetLastError();                                                                     \
     if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");                           \
     return PWK_OK;                                                                              \

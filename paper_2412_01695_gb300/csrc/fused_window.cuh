@@ -1,8 +1,8 @@
 // Window-specialised fused H|psi> kernel.
 //
 // Same operator (kinetic and local terms) and the same one-HBM-round-trip structure as
-// fused_kernel (paper Sec. 2.2 and Sec. 5; see fused_kernel.cuh), for spheres whose Miller indices all satisfy |m_i| <= W with
-// W = N/4: a grid chosen to hold the differences G - G' of the basis (Sec. 5: "N_i large
+// fused_kernel (paper Sec. 2.2 and Sec. 4; see fused_kernel.cuh), for spheres whose Miller indices all satisfy |m_i| <= W with
+// W = N/4: a grid chosen to hold the differences G - G' of the basis (Sec. 4: "N_i large
 // enough"), N >= 4 max|m|, always satisfies it.  With the window known at compile time:
 //   * the z-sticks live in a dense (2W+1) x (2W+1) square of rows [m1][m2] (rows without a
 //     stick of this k stay zero), so the y pass reads and writes them without a stick table;
@@ -334,7 +334,7 @@ int launch_window_multi(int N, const FusedArgs& a, int nblocks, const LaunchShap
                             : fused_window_multi_kernel<T, TI, n, window_of(n), 0>;             \
     cudaError_t e = allow_full_smem(kern);                                                      \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(window multi)");            \
-    kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \
+    kern<<<nblocks, s.threads, s.smem, st>>>(a); note_launch();                                                \
     e = cudaGetLastError();                                                                     \
     if (e != cudaSuccess) return cuda_fail(e, "window multi kernel launch");                    \
     return PWK_OK;                                                                              \
@@ -357,7 +357,7 @@ int launch_window(int N, const FusedArgs& a, int nblocks, const LaunchShape& s, 
                             : fused_window_kernel<T, TI, n, window_of(n), 0, NL>;               \
     cudaError_t e = allow_full_smem(kern);                                                      \
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(window)");                  \
-    kern<<<nblocks, s.threads, s.smem, st>>>(a);                                                \
+    kern<<<nblocks, s.threads, s.smem, st>>>(a); note_launch();                                                \
     e = cudaGetLastError();                                                                     \
     if (e != cudaSuccess) return cuda_fail(e, "window kernel launch");                          \
     return PWK_OK;                                                                              \

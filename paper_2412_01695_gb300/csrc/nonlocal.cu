@@ -343,13 +343,13 @@ int launch_nl_pc(const NlArgs& a, int nblocks, cudaStream_t st) {
   if (a.phase == 0) {
     if (cudaError_t e = allow_full_smem(nl_project_kernel<T, TI, PC>); e != cudaSuccess)
       return cuda_fail(e, "cudaFuncSetAttribute(nl_project)");
-    nl_project_kernel<T, TI, PC><<<nblocks, kNlThreads, s1, st>>>(a);
+    nl_project_kernel<T, TI, PC><<<nblocks, kNlThreads, s1, st>>>(a); note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "nl_project_kernel");
   } else {
     if (cudaError_t e = allow_full_smem(nl_addback_kernel<T, TI, PC>); e != cudaSuccess)
       return cuda_fail(e, "cudaFuncSetAttribute(nl_addback)");
-    nl_addback_kernel<T, TI, PC><<<nblocks, kNlThreads, s3, st>>>(a);
+    nl_addback_kernel<T, TI, PC><<<nblocks, kNlThreads, s3, st>>>(a); note_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "nl_addback_kernel");
   }

@@ -41,9 +41,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kProducers = 224;          // warps 0..6 copy and split; warp 7 issues the MMAs
-constexpr int kRing = 4;                 // raw blocks in the asynchronous-copy ring
 constexpr int kStages = 3;               // hi/lo tile stages
 constexpr int kTileA = 128 * 128;        // bytes of a 128-row tile
+// dynamic shared memory a CTA may use (227 KB less the kernels' static shared memory)
+constexpr size_t kSmemCap = 226 * 1024;
 // polls of the final wait for MMAs already issued when a kernel gives up (so that tensor
 // memory is never freed under a running MMA), independent of the plan's wait bound
 constexpr long long kDrainPolls = 1LL << 22;
@@ -149,7 +150,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ int round16(int n) { return (n + 15) & ~15; }
 
 // ----------------------------------------------------------------------------- projection
-template <typename TI>
+template <typename TI, int RING>
 __global__ void __launch_bounds__(kThreads, 1) nl_project_tcw_kernel(NlArgs a) {
   using VI = c2_t<TI>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -207,11 +208,11 @@ __global__ void __launch_bounds__(kThreads, 1) nl_project_tcw_kernel(NlArgs a) {
 
   const VI* cin = static_cast<const VI*>(a.in) + (size_t)k * a.nvec_in * a.npw_max;
   const float2* bin = static_cast<const float2*>(a.beta) + (size_t)k * nkb * a.npw_max;
-  // block b into ring slot b % kRing: nb rows of 16 coefficients, nkb rows of 16 projector
+  // block b into ring slot b % RING: nb rows of 16 coefficients, nkb rows of 16 projector
   // values (one complex element per copy; zero-filled past npw(k))
   auto fetch = [&](int b) {
     if (b < nblk) {
-      unsigned char* slot = ring + (b % kRing) * raw_slot;
+      unsigned char* slot = ring + (b % RING) * raw_slot;
       for (int t = tid; t < 16 * (nb + nkb); t += kProducers) {
         const int r = t >> 4, j = t & 15, g = 16 * b + j;
         const bool in = g < np;
@@ -229,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1) nl_project_tcw_kernel(NlArgs a) {
   // split tasks: four plane waves of a band row (B) or of a projector (two A rows)
   const int ntask = 4 * (nb + nkb);
   auto split = [&](int b, int s) {
-    const unsigned char* slot = ring + (b % kRing) * raw_slot;
+    const unsigned char* slot = ring + (b % RING) * raw_slot;
     for (int t = tid; t < ntask; t += kProducers) {
       const bool is_c = t < 4 * nb;
       const int row = is_c ? (t >> 2) : ((t - 4 * nb) >> 2);
@@ -282,16 +283,16 @@ __global__ void __launch_bounds__(kThreads, 1) nl_project_tcw_kernel(NlArgs a) {
 
   if (warp < kProducers / 32) {
 #pragma unroll 1
-    for (int j = 0; j < kRing - 1; ++j) fetch(j);
+    for (int j = 0; j < RING - 1; ++j) fetch(j);
 #pragma unroll 1
     for (int b = 0; b < nblk; ++b) {
       const int s = b % kStages;
       if (b >= kStages && !wait_parity(&empty[s], (uint32_t)(((b - kStages) / kStages) & 1), a.wait_polls))
         pfail[b & 1] = 1;
-      asm volatile("cp.async.wait_group %0;\n" ::"n"(kRing - 2) : "memory");
+      asm volatile("cp.async.wait_group %0;\n" ::"n"(RING - 2) : "memory");
       asm volatile("bar.sync 1, %0;\n" ::"n"(kProducers) : "memory");
       if (pfail[b & 1]) break;
-      fetch(b + kRing - 1);
+      fetch(b + RING - 1);
       split(b, s);
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(saddr(&full[s]))
@@ -373,21 +374,42 @@ __global__ void __launch_bounds__(kThreads, 1) nl_project_tcw_kernel(NlArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncol));
 }
 
-size_t project_tcw_smem(int nb, int nkb, int io_bytes) {
+// copy-ring depth of the projection: 8 raw blocks in flight where shared memory allows, else 4
+int project_tcw_ring(int nb, int nkb, int io_bytes);
+size_t project_tcw_smem_ring(int nb, int nkb, int io_bytes, int ring) {
   const int NB = (nb + 15) & ~15;
   const size_t stages = (size_t)kStages * (2 * kTileA + 2 * NB * 128);
-  const size_t ring = (size_t)kRing * (nb * 16 * io_bytes + nkb * 16 * 8);
+  const size_t rbytes = (size_t)ring * (nb * 16 * io_bytes + nkb * 16 * 8);
   const size_t lam = (size_t)2 * nkb * nb * 4;   // reuses the stages
-  return (stages > lam ? stages : lam) + ring + 1024;
+  return (stages > lam ? stages : lam) + rbytes + 1024;
+}
+int project_tcw_ring(int nb, int nkb, int io_bytes) {
+  return project_tcw_smem_ring(nb, nkb, io_bytes, 8) <= kSmemCap ? 8 : 4;
+}
+size_t project_tcw_smem(int nb, int nkb, int io_bytes) {
+  return project_tcw_smem_ring(nb, nkb, io_bytes, project_tcw_ring(nb, nkb, io_bytes));
 }
 
 // ----------------------------------------------------------------------------- add-back
-// One CTA per k-point.  Per tile of 128 plane waves and per block of 16 projectors: all
-// threads copy the block of beta(k) (16 rows of 128 values) into shared memory, split and
-// transpose it into the A tile (plane-wave rows), and one lane issues the tile's 12 MMAs
-// (4 K steps x 3 products) against the block's B tile; after the last block the accumulator
-// (128 plane waves x N) is added to H C.  Two A buffers alternate, so the copy and split of
-// a block overlap the MMAs of the previous one.
+// Shared-memory layout of the add-back: the B hi/lo tiles of every projector block, two A
+// buffers (hi/lo), two raw beta blocks ([16 projectors][128 plane waves] float2) and, when it
+// fits, the tile of H C being updated ([nb][128] elements of the I/O type).
+constexpr int kRawBlock = 16 * 128 * 8;
+__host__ __device__ constexpr size_t addback_base_bytes(int nb, int nkb) {
+  return (size_t)((nkb + 15) / 16) * 2 * ((2 * nb + 15) & ~15) * 128 + 2 * 2 * kTileA + 2 * kRawBlock + 1024;
+}
+__host__ __device__ constexpr size_t addback_hbuf_bytes(int nb, int io_bytes) { return (size_t)128 * nb * io_bytes; }
+__host__ __device__ constexpr bool addback_uses_hbuf(int nb, int nkb, int io_bytes) {
+  return addback_base_bytes(nb, nkb) + addback_hbuf_bytes(nb, io_bytes) <= kSmemCap;
+}
+
+// One CTA per k-point.  Per tile of 128 plane waves and per block of 16 projectors: the block
+// of beta(k) (16 rows of 128 values, copied one step ahead into the other raw buffer) is split
+// and transposed into an A tile (plane-wave rows), and one lane issues the tile's 12 MMAs
+// (4 K steps x 3 products) against the block's B tile.  The tile of H C is copied into shared
+// memory while the MMAs run; after the last block all eight warps add the accumulator (128
+// plane waves x N) to it and store the sum.  Two A buffers alternate, so the split of a block
+// overlaps the MMAs of the previous one.
 template <typename TI>
 __global__ void __launch_bounds__(kThreads, 1) nl_addback_tcw_kernel(NlArgs a) {
   using VI = c2_t<TI>;
@@ -401,11 +423,12 @@ __global__ void __launch_bounds__(kThreads, 1) nl_addback_tcw_kernel(NlArgs a) {
   const int N2 = round16(2 * nb);
   const int nkblk = (nkb + 15) / 16;
   const int b_tile = N2 * 128;
+  const bool use_hbuf = addback_uses_hbuf(nb, nkb, (int)sizeof(VI));
   unsigned char* base = smem_raw + ((1024u - (saddr(smem_raw) & 1023u)) & 1023u);
-  // layout: B hi/lo tiles of every projector block, two A buffers (hi/lo), the raw block
   unsigned char* btiles = base;
   unsigned char* abuf = base + (size_t)nkblk * 2 * b_tile;
-  unsigned char* raw = abuf + 2 * 2 * kTileA;   // [16 projectors][128 plane waves] float2
+  unsigned char* raw = abuf + 2 * 2 * kTileA;
+  VI* hbuf = reinterpret_cast<VI*>(raw + 2 * kRawBlock);
   auto bh = [&](int j) { return btiles + (size_t)j * 2 * b_tile; };
   auto bl = [&](int j) { return btiles + (size_t)j * 2 * b_tile + b_tile; };
   auto ah = [&](int u) { return abuf + u * 2 * kTileA; };
@@ -455,7 +478,38 @@ __global__ void __launch_bounds__(kThreads, 1) nl_addback_tcw_kernel(NlArgs a) {
   const float2* bk = static_cast<const float2*>(a.beta) + (size_t)k * nkb * a.npw_max;
   VI* hout = static_cast<VI*>(a.out) + (size_t)k * a.nvec_out * a.npw_max;
   const int ntile = (np + 127) / 128;
-  // per buffer: a commit not yet waited for, and the parity of its completion (every thread
+  const int nstep = ntile * nkblk;
+  // beta block of step s (tile s / nkblk, projector block s % nkblk) into raw buffer s & 1
+  // (zero outside the k-point's plane waves and projectors); one commit group per call
+  auto fetch_block = [&](int s) {
+    if (s < nstep) {
+      const int t = s / nkblk, j = s - t * nkblk;
+      unsigned char* dst = raw + (s & 1) * kRawBlock;
+      for (int e = tid; e < 16 * 128; e += kThreads) {
+        const int m = 16 * j + (e >> 7), g = 128 * t + (e & 127);
+        const bool in = m < nkb && g < np;
+        cp_async<8>(dst + e * 8, bk + (in ? (size_t)m * a.npw_max + g : 0), in ? 8 : 0);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  // the tile of H C (bands x 128 plane waves) into hbuf; one commit group per call
+  auto fetch_h = [&](int t) {
+    if (use_hbuf && t < ntile) {
+      for (int e = tid; e < nb * 128; e += kThreads) {
+        const int n = e >> 7, g = 128 * t + (e & 127);
+        const bool in = g < np;
+        cp_async<sizeof(VI)>(hbuf + e, hout + (size_t)n * a.npw_max + (in ? g : 0), in ? (int)sizeof(VI) : 0);
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+  };
+  auto wait_groups = [&](int pending) {   // all but the `pending` most recent groups complete
+    if (pending <= 0) asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    else if (pending == 1) asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    else asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+  };
+  // per A buffer: a commit not yet waited for, and the parity of its completion (every thread
   // keeps the same copy: the control flow is uniform)
   bool pend[2] = {false, false};
   uint32_t ph[2] = {0u, 0u};
@@ -466,6 +520,9 @@ __global__ void __launch_bounds__(kThreads, 1) nl_addback_tcw_kernel(NlArgs a) {
     pend[u] = false;
     return true;
   };
+  // groups in order: block 0, H tile 0, block 1, [H tile 1 after the epilogue of tile 0], ...
+  fetch_block(0);
+  fetch_h(0);
   int step = 0;
   // `failed` is read only right after a barrier that follows every write to it, and the
   // decision is kept in `stop`, so every thread leaves the loops at the same barrier
@@ -478,25 +535,19 @@ __global__ void __launch_bounds__(kThreads, 1) nl_addback_tcw_kernel(NlArgs a) {
       const int u = step & 1;
       // A buffer u is free once its previous MMA group has completed
       if (!wait_buf(u, a.wait_polls)) failed = 1;
+      fetch_block(step + 1);
+      // groups issued after this step's block: the next block, and H tile t at j == 0
+      wait_groups(j == 0 ? 2 : 1);
       __syncthreads();
       if (failed) {
         stop = true;
         break;
       }
-      // raw block: projectors 16 j .. 16 j + 15, plane waves g0 .. g0 + 127 (zero outside)
-      for (int e = tid; e < 16 * 128; e += kThreads) {
-        const int m = 16 * j + (e >> 7), g = g0 + (e & 127);
-        const bool in = m < nkb && g < np;
-        cp_async<8>(raw + e * 8, bk + (in ? (size_t)m * a.npw_max + g : 0), in ? 8 : 0);
-      }
-      asm volatile("cp.async.commit_group;\n" ::: "memory");
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      __syncthreads();
       // A rows = plane waves: row r, chunks 2 grp, 2 grp + 1 = projectors 4 grp .. 4 grp + 3
       // of the block as [re, im, re, im]
+      const float2* x = reinterpret_cast<const float2*>(raw + (step & 1) * kRawBlock);
       for (int e = tid; e < 128 * 4; e += kThreads) {
         const int r = e >> 2, grp = e & 3;
-        const float2* x = reinterpret_cast<const float2*>(raw);
         const float2 v0 = x[(4 * grp) * 128 + r], v1 = x[(4 * grp + 1) * 128 + r];
         const float2 v2 = x[(4 * grp + 2) * 128 + r], v3 = x[(4 * grp + 3) * 128 + r];
         float4 h0, l0, h1, l1;
@@ -524,35 +575,43 @@ __global__ void __launch_bounds__(kThreads, 1) nl_addback_tcw_kernel(NlArgs a) {
       pend[u] = true;
     }
     if (stop) break;
-    // the tile's accumulator is complete when both buffers' last groups have completed
+    // the tile's accumulator is complete when both buffers' last groups have completed; the
+    // H tile when every group but the next block's has
     if (!wait_buf(0, a.wait_polls) || !wait_buf(1, a.wait_polls)) failed = 1;
+    wait_groups(1);
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     __syncthreads();
     if (failed) {
       stop = true;
       break;
     }
-    // H C_n(G) += D[G][2n] + i D[G][2n+1] for the tile's plane waves (warps 0..3: lanes = rows)
-    if (warp < 4) {
-      const int g = g0 + 32 * warp + lane;
-      for (int c0 = 0; c0 < N2; c0 += 16) {
+    // H C_n(G) += D[G][2n] + i D[G][2n+1]: warp w reads tensor-memory lanes 32 (w % 4) ..
+    // (its plane waves) and every other 16-column chunk from w / 4
+    {
+      const int row = 32 * (warp & 3) + lane, g = g0 + row;
+      for (int c0 = 16 * (warp >> 2); c0 < N2; c0 += 32) {
         float v[16];
-        tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+        tmem_ld16(tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)c0, v);
         if (g < np) {
+          VI h[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const int n = c0 / 2 + i;
-            if (n < nb) {
-              VI& h = hout[(size_t)n * a.npw_max + g];
-              h = VI{h.x + TI(v[2 * i]), h.y + TI(v[2 * i + 1])};
-            }
+            if (n < nb) h[i] = use_hbuf ? hbuf[n * 128 + row] : hout[(size_t)n * a.npw_max + g];
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int n = c0 / 2 + i;
+            if (n < nb) hout[(size_t)n * a.npw_max + g] = VI{h[i].x + TI(v[2 * i]), h[i].y + TI(v[2 * i + 1])};
           }
         }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
+    fetch_h(t + 1);   // hbuf is free again
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   // after a failure: drain the MMA groups already issued before tensor memory is released
   wait_buf(0, kDrainPolls);
   wait_buf(1, kDrainPolls);
@@ -562,10 +621,8 @@ __global__ void __launch_bounds__(kThreads, 1) nl_addback_tcw_kernel(NlArgs a) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncol));
 }
 
-size_t addback_tcw_smem(int nb, int nkb) {
-  const int N2 = (2 * nb + 15) & ~15;
-  const int nkblk = (nkb + 15) / 16;
-  return (size_t)nkblk * 2 * N2 * 128 + 2 * 2 * kTileA + 16 * 128 * 8 + 1024;
+size_t addback_tcw_smem(int nb, int nkb, int io_bytes) {
+  return addback_base_bytes(nb, nkb) + (addback_uses_hbuf(nb, nkb, io_bytes) ? addback_hbuf_bytes(nb, io_bytes) : 0);
 }
 
 }  // namespace
@@ -579,8 +636,8 @@ int nl_tcw_applies(int precision, const NlArgs& a) {
   if (a.nitems % a.nvec_in != 0) return 0;
   if (a.phase == 1 && a.sout != nullptr) return 0;   // S C: the CUDA-core add-back
   const int io = precision == PWK_FP32 ? 8 : 16;
-  if (project_tcw_smem(a.nvec_in, a.nkb, io) > 227 * 1024) return 0;
-  if (addback_tcw_smem(a.nvec_in, a.nkb) > 227 * 1024) return 0;
+  if (project_tcw_smem(a.nvec_in, a.nkb, io) > kSmemCap) return 0;
+  if (addback_tcw_smem(a.nvec_in, a.nkb, io) > kSmemCap) return 0;
   return 1;
 }
 
@@ -590,22 +647,26 @@ int launch_nl_tcw(int precision, const NlArgs& a, cudaStream_t st) {
   cudaError_t e;
   const bool f32 = precision == PWK_FP32;
   if (a.phase == 0) {
-    const size_t smem = project_tcw_smem(a.nvec_in, a.nkb, f32 ? 8 : 16);
-    if (f32) {
-      if ((e = allow_full_smem(nl_project_tcw_kernel<float>)) != cudaSuccess) return cuda_fail(e, "attr(tcw)");
-      nl_project_tcw_kernel<float><<<nkl, kThreads, smem, st>>>(a);
-    } else {
-      if ((e = allow_full_smem(nl_project_tcw_kernel<double>)) != cudaSuccess) return cuda_fail(e, "attr(tcw)");
-      nl_project_tcw_kernel<double><<<nkl, kThreads, smem, st>>>(a);
-    }
+    const int io = f32 ? 8 : 16;
+    const size_t smem = project_tcw_smem(a.nvec_in, a.nkb, io);
+    const bool deep = project_tcw_ring(a.nvec_in, a.nkb, io) == 8;
+    auto go = [&](auto kern) -> cudaError_t {
+      cudaError_t e2 = allow_full_smem(kern);
+      if (e2 != cudaSuccess) return e2;
+      kern<<<nkl, kThreads, smem, st>>>(a); note_launch();
+      return cudaSuccess;
+    };
+    if (f32) e = deep ? go(nl_project_tcw_kernel<float, 8>) : go(nl_project_tcw_kernel<float, 4>);
+    else e = deep ? go(nl_project_tcw_kernel<double, 8>) : go(nl_project_tcw_kernel<double, 4>);
+    if (e != cudaSuccess) return cuda_fail(e, "attr(tcw)");
   } else {
-    const size_t smem = addback_tcw_smem(a.nvec_in, a.nkb);
+    const size_t smem = addback_tcw_smem(a.nvec_in, a.nkb, f32 ? 8 : 16);
     if (f32) {
       if ((e = allow_full_smem(nl_addback_tcw_kernel<float>)) != cudaSuccess) return cuda_fail(e, "attr(tcw)");
-      nl_addback_tcw_kernel<float><<<nkl, kThreads, smem, st>>>(a);
+      nl_addback_tcw_kernel<float><<<nkl, kThreads, smem, st>>>(a); note_launch();
     } else {
       if ((e = allow_full_smem(nl_addback_tcw_kernel<double>)) != cudaSuccess) return cuda_fail(e, "attr(tcw)");
-      nl_addback_tcw_kernel<double><<<nkl, kThreads, smem, st>>>(a);
+      nl_addback_tcw_kernel<double><<<nkl, kThreads, smem, st>>>(a); note_launch();
     }
   }
   e = cudaGetLastError();

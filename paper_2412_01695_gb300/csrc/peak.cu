@@ -51,7 +51,7 @@ int measure(int iters, double* flops_per_s, int* sm_count, cudaStream_t st) {
   } else {
     for (int rep = 0; rep < 4 && rc == PWK_OK; ++rep) {   // the first launch is a warm-up
       cudaEventRecord(e0, st);
-      fma_peak_kernel<T><<<blocks, kPeakThreads, 0, st>>>(static_cast<T*>(out), T(0.9999), T(1e-4), iters);
+      fma_peak_kernel<T><<<blocks, kPeakThreads, 0, st>>>(static_cast<T*>(out), T(0.9999), T(1e-4), iters); note_launch();
       cudaEventRecord(e1, st);
       if ((e = cudaEventSynchronize(e1)) != cudaSuccess) {
         rc = cuda_fail(e, "fma_peak_kernel");

@@ -1,8 +1,9 @@
-// Plans: the per-k tables of a block of k-points kept resident on the device (paper Sec. 4:
+// Plans: the per-k tables of a block of k-points kept resident on the device (paper Sec. 3:
 // projectors and wave-function layout loaded for all N_k points before the solvers run),
-// the sphere -> stick maps of the pruned transforms (Sec. 5), and the H|psi> entry points.
+// the sphere -> stick maps of the pruned transforms (Sec. 4), and the H|psi> entry points.
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -34,6 +35,9 @@ void mark_smem_limit_raised(const void* kern, int dev) {
   std::lock_guard<std::mutex> lock(g_smem_mu);
   g_smem_raised[{kern, dev}] = true;
 }
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int cuda_fail(cudaError_t e, const char* what) {
   char buf[256];
@@ -495,42 +499,51 @@ int autotune_shape(pwk_plan* p, int precision) {
   cudaFree(out);
   in = out = nullptr;
   // The projector terms inside the best fused shape against the separate kernels around the
-  // best plain shape (projections, local kernel, add-back), timed as whole H applications on
-  // a larger sample (at least about 16 waves of CTAs), where launch overheads and partial last
-  // waves no longer decide.
-  bool fused = false;
+  // best plain shape (projections, local kernel, add-back; on the CUDA cores and, for the FP32
+  // arithmetic where they apply, on the tensor cores), timed as whole H applications of 32
+  // bands (a whole-k-point call of a band set) on a larger sample (a few waves of the
+  // one-CTA-per-k-point projector kernels), where launch overheads and partial last waves no
+  // longer decide.
+  bool fused = false, tc = false;
   if (p->nkb > 0 && tfused[bf] < 1e29f && tplain[bp] < 1e29f) {
-    const int nk2 = std::min(p->nk, precision == PWK_FP64 ? 256 : 1536);
-    const size_t bytes2 = (size_t)nk2 * nv * p->npw_max * io_elem;
+    const int nv2 = 32, nk2 = std::min(p->nk, precision == PWK_FP64 ? 64 : 384);
+    const size_t bytes2 = (size_t)nk2 * nv2 * p->npw_max * io_elem;
     void* coef = nullptr;
     if (cudaMalloc(&in, bytes2) == cudaSuccess && cudaMalloc(&out, bytes2) == cudaSuccess &&
-        cudaMalloc(&coef, (size_t)nk2 * nv * 2 * p->nkb * elem) == cudaSuccess) {
+        cudaMalloc(&coef, (size_t)nk2 * nv2 * 2 * p->nkb * elem) == cudaSuccess) {
       cudaMemset(in, 0, bytes2);
       FusedArgs b = hpsi_args(p, precision, in, out);
-      b.nvec_in = b.nvec_out = nv;
-      NlArgs n = nl_args(p, precision, in, out, nullptr, nullptr, nullptr, nk2 * nv, nv, nv, 0);
-      n.tensor_cores = false;
+      b.nvec_in = b.nvec_out = nv2;
+      NlArgs n = nl_args(p, precision, in, out, nullptr, nullptr, nullptr, nk2 * nv2, nv2, nv2, 0);
       n.coef = coef;
-      float tf = 1e30f, ts = 1e30f;
+      n.tensor_cores = true;
+      const bool try_tc = precision != PWK_FP64 && nl_tcw_applies(precision, n);
+      float tf = 1e30f, ts = 1e30f, tt = 1e30f;
+      auto split = [&](bool on_tc) {
+        const LaunchShape& cp = cands[bp];
+        b.L = cp.L;
+        use_kind(p, b, cp.kind);
+        b.beta = nullptr;
+        n.tensor_cores = on_tc;
+        return time_it([&] {
+          n.phase = 0;
+          int r = launch_nl(precision, n, 0);
+          if (r == PWK_OK) r = launch_variant(precision, N, b, nk2 * nv2, cp, 0);
+          n.phase = 1;
+          return r ? r : launch_nl(precision, n, 0);
+        });
+      };
       for (int round = 0; round < 2; ++round) {
         const LaunchShape& cf = cands[bf];
         b.L = cf.L;
         use_kind(p, b, cf.kind);
         set_fused_nl(p, precision, b, nullptr, cf);
-        tf = std::min(tf, time_it([&] { return launch_variant(precision, N, b, nk2 * nv, cf, 0); }));
-        const LaunchShape& cp = cands[bp];
-        b.L = cp.L;
-        use_kind(p, b, cp.kind);
-        b.beta = nullptr;
-        ts = std::min(ts, time_it([&] {
-          n.phase = 0;
-          int r = launch_nl(precision, n, 0);
-          if (r == PWK_OK) r = launch_variant(precision, N, b, nk2 * nv, cp, 0);
-          n.phase = 1;
-          return r ? r : launch_nl(precision, n, 0);
-        }));
+        tf = std::min(tf, time_it([&] { return launch_variant(precision, N, b, nk2 * nv2, cf, 0); }));
+        ts = std::min(ts, split(false));
+        if (try_tc) tt = std::min(tt, split(true));
       }
-      fused = tf <= ts;
+      fused = tf <= ts && tf <= tt;
+      tc = !fused && tt < ts;
     } else {
       cudaGetLastError();
     }
@@ -543,6 +556,7 @@ int autotune_shape(pwk_plan* p, int precision) {
   if (tplain[bp] < 1e29f || fused) {
     p->shape[precision] = fused ? cands[bf] : cands[bp];
     p->nl_fused[precision] = fused;
+    p->nl_tc[precision] = tc;
   }
   return PWK_OK;
 }
@@ -617,7 +631,7 @@ static NlArgs nl_args(const pwk_plan* p, int precision, const void* in, void* ou
   n.d_count = d_count;
   n.k0 = k0;
   n.err = p->d_err;
-  n.tensor_cores = p->projector_path == 1;
+  n.tensor_cores = p->projector_path == 1 || (p->projector_path == 0 && p->nl_tc[precision]);
   n.wait_polls = p->wait_polls;
   n.nitems = nblocks;
   n.nvec_in = nvec_in;
@@ -747,6 +761,8 @@ int pwk_plan_errors(pwk_plan* p, int* flags, int clear) {
   return PWK_OK;
 }
 
+long long pwk_launch_count(void) { return pwk::g_launches.load(std::memory_order_relaxed); }
+
 int pwk_plan_set_projector_path(pwk_plan* p, int path) {
   if (p == nullptr || path < 0 || path > 3) {
     set_error("null plan or path not 0..3");
@@ -759,6 +775,14 @@ int pwk_plan_set_projector_path(pwk_plan* p, int path) {
 int pwk_plan_projector_fused(const pwk_plan* p, int precision) {
   if (p == nullptr || precision < 0 || precision > 2) return -1;
   return nl_fused_for(p, precision, p->shape[precision]) ? 1 : 0;
+}
+
+int pwk_plan_projector_choice(const pwk_plan* p, int precision) {
+  if (p == nullptr || precision < 0 || precision > 2) return -1;
+  if (p->nkb == 0) return 0;
+  if (nl_fused_for(p, precision, p->shape[precision])) return 3;
+  const bool tc = p->projector_path == 1 || (p->projector_path == 0 && p->nl_tc[precision]);
+  return tc && precision != PWK_FP64 ? 1 : 2;
 }
 
 int pwk_plan_set_launch_shape(pwk_plan* p, int precision, int kind, int threads, int l3_chunk) {
@@ -907,12 +931,12 @@ int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int
        "cudaMemcpy(miller)");
   TRYC(cudaMemcpy(d_B, p->B, sizeof(double) * 9, cudaMemcpyHostToDevice), "cudaMemcpy(B)");
   kinetic_table_kernel<<<blocks_for((size_t)nk * npw_max), 256>>>(nk, npw_max, p->d_npw, p->d_kcart,
-                                                                  d_miller, d_B, p->d_g2);
+                                                                  d_miller, d_B, p->d_g2); note_launch();
   TRYC(cudaGetLastError(), "kinetic_table_kernel");
   if (nkb > 0) {
     const size_t nb2 = (size_t)nk * nkb * npw_max * 2;
     TRY(plan_alloc(p, (void**)&p->d_beta32, sizeof(float) * nb2));
-    to_f32_kernel<<<blocks_for(nb2), 256>>>(nb2, static_cast<const double*>(beta), (float*)p->d_beta32);
+    to_f32_kernel<<<blocks_for(nb2), 256>>>(nb2, static_cast<const double*>(beta), (float*)p->d_beta32); note_launch();
     TRYC(cudaGetLastError(), "beta to f32");
     std::vector<float> D32(p->h_D.begin(), p->h_D.end());
     TRY(plan_alloc(p, (void**)&p->d_D, sizeof(double) * nkb * nkb));
@@ -922,12 +946,12 @@ int pwk_plan_create(pwk_plan** out, const double* A, int N1, int N2, int N3, int
   }
   TRY(plan_alloc(p, (void**)&p->d_V32, sizeof(float) * (size_t)p->Nr));
   TRY(plan_alloc(p, (void**)&p->d_Vt64, sizeof(double) * (size_t)p->Nr));
-  transpose_v_kernel<float><<<blocks_for(p->Nr), 256>>>(p->N, vloc_r, p->d_V32);
-  transpose_v_kernel<double><<<blocks_for(p->Nr), 256>>>(p->N, vloc_r, p->d_Vt64);
+  transpose_v_kernel<float><<<blocks_for(p->Nr), 256>>>(p->N, vloc_r, p->d_V32); note_launch();
+  transpose_v_kernel<double><<<blocks_for(p->Nr), 256>>>(p->N, vloc_r, p->d_Vt64); note_launch();
   TRYC(cudaGetLastError(), "V transpose");
   TRYC(cudaMalloc(&d_vsum, sizeof(double)), "cudaMalloc(tmp)");
   TRYC(cudaMemset(d_vsum, 0, sizeof(double)), "cudaMemset");
-  sum_kernel<<<1, 256>>>((size_t)p->Nr, vloc_r, d_vsum);
+  sum_kernel<<<1, 256>>>((size_t)p->Nr, vloc_r, d_vsum); note_launch();
   TRYC(cudaGetLastError(), "sum_kernel");
   TRYC(cudaMemcpy(&p->v_mean, d_vsum, sizeof(double), cudaMemcpyDeviceToHost), "cudaMemcpy(vsum)");
   p->v_mean /= (double)p->Nr;

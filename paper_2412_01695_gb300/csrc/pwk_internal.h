@@ -16,6 +16,8 @@ namespace pwk {
 
 void set_error(const std::string& msg);  // thread-local detail for pwk_last_error_detail()
 int cuda_fail(cudaError_t e, const char* what);
+// Counts one kernel launch of the library (process-wide, read by pwk_launch_count).
+void note_launch();
 
 // Whether a kernel's shared-memory limit was already raised on a device (plan.cu; a
 // process-wide table guarded by a mutex).
@@ -107,6 +109,7 @@ struct pwk_plan {
   pwk::LaunchShape xshape;       // transfer kernel (complex dv, FP64)
   int projector_path = 0;        // 0 automatic, 1 tensor cores, 2 separate kernels, 3 fused
   bool nl_fused[3] = {false, false, false};   // automatic choice per precision (autotuner)
+  bool nl_tc[3] = {false, false, false};      // separate kernels: tensor cores (autotuner)
   long long wait_polls = 1LL << 24;   // bound on the polls of each device-side wait
   int* d_err = nullptr;          // device error word (bad work items)
   // solver phase timing (pwk_plan_set_solver_timing): figures of the last solver call

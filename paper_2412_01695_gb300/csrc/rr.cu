@@ -1,4 +1,4 @@
-// Batched generalized Hermitian eigensolver for the Davidson reduced problem (paper Sec. 6):
+// Batched generalized Hermitian eigensolver for the Davidson reduced problem (paper Sec. 5):
 //   H~ v = eps S~ v,   n = N_base <= 160,   lowest nb eigenpairs, one CTA per k-point, FP64.
 //
 // The paper runs LAPACK ZHEGV(X) converted to device routines, one thread per k, with a
@@ -9,11 +9,13 @@
 //   3. Householder reduction of C to a real symmetric tridiagonal T = Q^H C Q
 //      (reflectors H = I - tau v v^H, beta real, two-sided rank-2 updates of the lower
 //      triangle);
-//   4. the nb lowest eigenvalues of T by bisection on Sturm counts and their eigenvectors by
-//      inverse iteration on T (one thread per cluster of close eigenvalues, clusters in
-//      parallel; the members of a cluster reorthogonalised inside the iteration);
-//   5. back-transform x = L^-H Q z (reflectors applied in reverse order, then back
-//      substitution).
+//   4. the nb lowest eigenvalues of T from Sturm counts (a bracket narrowed by bisection in
+//      FP32, confirmed by two FP64 counts, then safeguarded Newton steps on det(T - x) in
+//      FP64 down to two ulp of |T|) and their eigenvectors by inverse iteration on T (one
+//      thread per cluster of close eigenvalues, clusters in parallel; the members of a
+//      cluster reorthogonalised inside the iteration);
+//   5. back-transform x = L^-H Q z (reflectors applied in reverse order, then the triangular
+//      solve column by column; a few lanes of one warp per vector).
 // All matrices live in a per-k global workspace (L2-resident while the CTA works on it).
 // The kernel is bound by the FP64 pipe (1/64 of the FP32 rate on this GPU) when the batch
 // is full, so the loops count FP64 instructions: fused multiply-add chains (4 per complex
@@ -311,7 +313,7 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   //      lockstep, so every FP64 instruction serves up to 32 eigenvalues), then inverse
   //      iteration for the eigenvectors.
   double* e2 = rs;
-  __shared__ double glo, ghi, pivmin, tiny, werr;
+  __shared__ double glo, ghi, pivmin, tiny, werr, atol;
   __shared__ float d32[kMaxBasis], e232[kMaxBasis];
   __shared__ float pivmin32;
   __shared__ int use32;
@@ -332,11 +334,16 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     ghi = hi + 1e-14 * span + 1e-300;
     pivmin = 1e-290 * fmax(1.0, emax);
     tiny = 2.2e-16 * fmax(1.0, fmax(dmax, sqrt(emax)));
-    // FP32 Sturm counts are exact for a T perturbed by at most u32 (2 dmax + |x| + 3 max|e|)
-    // (u32 = 2^-24: rounding of d, e^2 to FP32 and of each step of the recurrence), so an
-    // FP32 bracket widened by werr (8 times that bound, |x| <= dmax + 2 max|e|) holds the
-    // eigenvalue; the FP64 counts confirm it before it is used.
-    werr = 4.8e-7 * (3.0 * dmax + 5.0 * sqrt(emax));
+    // absolute accuracy of the eigenvalues: two units in the last place of the Gershgorin
+    // bound of |T| (a Sturm count is backward stable, so no bracket narrower than a few
+    // ulp(|T|) is meaningful; a bound relative to |lambda| alone never ends for lambda ~ 0)
+    atol = 4.4e-16 * span;
+    // FP32 Sturm counts are exact for a T perturbed by at most u32 (2 dmax + |x| + 9 max|e|)
+    // (u32 = 2^-24: rounding of d, e^2 to FP32 and of each step of the recurrence, whose
+    // division is the fast one, within 2 ulp), so an FP32 bracket widened by werr (8 times
+    // that bound, |x| <= dmax + 2 max|e|) holds the eigenvalue; the FP64 counts confirm it
+    // before it is used.
+    werr = 4.8e-7 * (3.0 * dmax + 11.0 * sqrt(emax));
     use32 = dmax < 1e15 && emax < 1e28;
     pivmin32 = (float)(1e-30 * fmax(1.0, emax));
   }
@@ -352,7 +359,7 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
   // kernel when the batch is full, so the Sturm counts are not multiplied across threads.
   // count(x) = number of eigenvalues below x (Sturm sequence of the LDL^T factorisation of
   // T - x).  The bracket is first narrowed in FP32 (64 times the FP64 rate) down to werr;
-  // the FP64 bisection then starts from that bracket widened by werr on both sides.
+  // the FP64 stage then starts from that bracket widened by werr on both sides.
   auto count64 = [&](double x) {
     double q = d[0] - x;
     int cnt = q < 0.0;
@@ -363,8 +370,29 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     }
     return cnt;
   };
+  // The same recurrence with its derivative: the count at x, and in s the logarithmic
+  // derivative of det(T - x) = prod_i q_i, s = sum_i q_i' / q_i with
+  // q_i' = -1 + e_{i-1}^2 q_{i-1}' / q_{i-1}^2, so that x - 1/s is the Newton step for det.
+  auto count_newton = [&](double x, double& s) {
+    double q = d[0] - x, dq = -1.0;
+    int cnt = q < 0.0;
+    if (fabs(q) < pivmin) q = -pivmin;
+    double r = 1.0 / q;
+    s = dq * r;
+    for (int i = 1; i < n; ++i) {
+      const double t = e2[i - 1] * r;   // e_{i-1}^2 / q_{i-1}
+      dq = fma(t * r, dq, -1.0);
+      q = (d[i] - x) - t;
+      cnt += q < 0.0;
+      if (fabs(q) < pivmin) q = -pivmin;
+      r = 1.0 / q;
+      s = fma(dq, r, s);
+    }
+    return cnt;
+  };
   for (int j = tid; j < nb; j += nth) {
     double a = glo, b = ghi;
+    int ca = 0, cb = n;   // counts at a and b
     if (use32) {
       float a32 = __double2float_rd(glo), b32 = __double2float_ru(ghi);
       const float w32 = (float)werr;
@@ -375,25 +403,70 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
         int cnt = q < 0.0f;
         for (int i = 1; i < n; ++i) {
           if (fabsf(q) < pivmin32) q = -pivmin32;
-          q = d32[i] - mid - e232[i - 1] / q;
+          q = d32[i] - mid - __fdividef(e232[i - 1], q);
           cnt += q < 0.0f;
         }
         if (cnt > j) b32 = mid;
         else a32 = mid;
       }
       const double a1 = fmax(glo, (double)a32 - werr), b1 = fmin(ghi, (double)b32 + werr);
-      if (count64(a1) <= j && count64(b1) > j) {
+      const int c1 = count64(a1), c2 = count64(b1);
+      if (c1 <= j && c2 > j) {
         a = a1;
         b = b1;
+        ca = c1;
+        cb = c2;
       }
     }
+    // FP64: safeguarded Newton on det(T - x).  Every pass counts at x and shrinks the bracket
+    // to the side that keeps eigenvalue j; while the bracket holds eigenvalue j alone
+    // (count(a) = j, count(b) = j + 1) the Newton step is taken if it lands inside it, else
+    // (and for eigenvalues not yet separated from a neighbour) the bracket is bisected.  The
+    // Newton iterates approach the eigenvalue from one side, so the far end of the bracket
+    // stays where it was: once a step of rounding size (at most atol) points out of the
+    // bracket (the last iterate, now one end of it, is within rounding of the eigenvalue) the
+    // next count is taken atol inside that end, which closes the bracket to atol instead of
+    // halving it from the far end; a larger step out of the bracket is replaced by a
+    // bisection.  A separated eigenvalue takes two to five passes instead of the ~30 halvings
+    // from werr down.
+    double x = 0.5 * (a + b), lj = x;
     for (int it = 0; it < 200; ++it) {
-      const double mid = 0.5 * (a + b);
-      if (mid <= a || mid >= b || b - a <= 4.4e-16 * fmax(fabs(a), fabs(b)) + 2.0 * pivmin) break;
-      if (count64(mid) > j) b = mid;
-      else a = mid;
+      const double tol = atol + 2.0 * pivmin;
+      if (b - a <= tol) {
+        lj = 0.5 * (a + b);
+        break;
+      }
+      double sd;
+      const int c = count_newton(x, sd);
+      if (c > j) {
+        b = x;
+        cb = c;
+      } else {
+        a = x;
+        ca = c;
+      }
+      if (ca == j && cb == j + 1) {
+        const double xn = x - 1.0 / sd;
+        if (xn > a && xn < b) {
+          lj = xn;
+          if (fabs(xn - x) <= tol) break;
+          x = xn;
+          continue;
+        }
+        if (fabs(xn - x) <= tol) {   // a rounding-size step out of the bracket
+          const double xi = x == a ? x + tol : x - tol;
+          if (xi > a && xi < b) {
+            x = xi;
+            lj = x;
+            continue;
+          }
+        }
+      }
+      x = 0.5 * (a + b);
+      lj = x;
+      if (x <= a || x >= b) break;
     }
-    lam[j] = 0.5 * (a + b);
+    lam[j] = lj;
   }
   __syncthreads();
   double* XS = reinterpret_cast<double*>(X);   // x_j at XS + j n, pivots of T - lam_j at XS + (nb + j) n
@@ -477,54 +550,74 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
     if (tid == 0 && status != nullptr) status[k] = PWK_ERR_NUMERIC;
     return;
   }
-  // ---- 5. back-transform x = L^-H Q z of the selected vectors
+  // ---- 5. back-transform x = L^-H Q z of the selected vectors.  G lanes of one warp per
+  //      vector (G = 8 for nb <= 32, fewer for more vectors); lane c of a group holds the rows
+  //      r = c, c + G, c + 2G, ... of its vector, so a reflector on rows h+1..n-1 costs each
+  //      lane about (n-h-1)/G row updates and a G-lane reduction, the triangular solve
+  //      (column by column: x_r, then its share subtracted from the rows above) a broadcast
+  //      and about r/G updates per row, and the vectors of a warp need no block barrier.
   for (int j = tid; j < nb; j += nth) eps[k * nb + j] = lam[j];
   double2* E = ev + (size_t)k * ld * nb;
-  // one warp per selected vector
-  const int warp = tid >> 5, lane = tid & 31, nw = nth >> 5;
-  for (int j = warp; j < nb; j += nw) {
-    // y = z (real) in E[:, j]
-    for (int r = lane; r < n; r += 32) E[r * nb + j] = make_double2(XS[(size_t)j * n + r], 0.0);
-    __syncwarp();
-    // y = H_0 H_1 ... H_{n-2} y : apply H_{n-2} first
-    for (int h = n - 2; h >= 0; --h) {
-      const double2 th = tau[h];
-      if (th.x == 0.0 && th.y == 0.0) continue;
-      double2 s = make_double2(0.0, 0.0);   // v^H y over rows h+1..n-1
-      for (int r = h + 1 + lane; r < n; r += 32) {
-        const double2 p = cmulc(C[r * ld + h], E[r * nb + j]);
-        s.x += p.x;
-        s.y += p.y;
+  {
+    const int G = nb <= nth / 8 ? 8 : nb <= nth / 4 ? 4 : nb <= nth / 2 ? 2 : 1;
+    const int c = tid % G, lane = tid & 31, ngroups = nth / G;
+    const int gbase = lane & ~(G - 1);   // lane of c = 0 in this group (G divides 32)
+    auto first_row = [&](int lo) { return lo <= c ? c : c + G * ((lo - c + G - 1) / G); };
+    for (int j0 = 0; j0 < nb; j0 += ngroups) {   // uniform trip counts: shuffles see every lane
+      const int j = j0 + tid / G;
+      const bool valid = j < nb;
+      if (valid)
+        for (int r = c; r < n; r += G) E[r * nb + j] = make_double2(XS[(size_t)j * n + r], 0.0);
+      // y = H_0 H_1 ... H_{n-2} y : apply H_{n-2} first; H_h = I - tau_h v_h v_h^H
+      for (int h = n - 2; h >= 0; --h) {
+        const double2 th = tau[h];
+        if (th.x == 0.0 && th.y == 0.0) continue;   // uniform across the block
+        double2 sv = make_double2(0.0, 0.0);      // v^H y over rows h+1..n-1
+        const int r0 = first_row(h + 1);
+        if (valid)
+          for (int r = r0; r < n; r += G) {
+            const double2 v = C[r * ld + h], y = E[r * nb + j];
+            sv.x = fma(v.x, y.x, fma(v.y, y.y, sv.x));
+            sv.y = fma(v.x, y.y, fma(-v.y, y.x, sv.y));
+          }
+        for (int o = G >> 1; o > 0; o >>= 1) {
+          sv.x += __shfl_xor_sync(0xffffffffu, sv.x, o);
+          sv.y += __shfl_xor_sync(0xffffffffu, sv.y, o);
+        }
+        const double2 ts = cmul(th, sv);
+        if (valid)
+          for (int r = r0; r < n; r += G) {
+            const double2 v = C[r * ld + h];
+            double2 y = E[r * nb + j];
+            y.x = fma(-v.x, ts.x, fma(v.y, ts.y, y.x));
+            y.y = fma(-v.x, ts.y, fma(-v.y, ts.x, y.y));
+            E[r * nb + j] = y;
+          }
       }
-      for (int o = 16; o > 0; o >>= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+      // x = L^-H y: x_r = y_r / L[r][r] from the last row up, then y_q -= conj(L[r][q]) x_r
+      // for the rows q < r (L^H has conj(L[r][q]) in row q, column r)
+      for (int r = n - 1; r >= 0; --r) {
+        const int owner = r % G;
+        double2 xr = make_double2(0.0, 0.0);
+        if (valid && c == owner) {
+          const double il = rc[r];
+          const double2 y = E[r * nb + j];
+          xr = make_double2(y.x * il, y.y * il);
+          E[r * nb + j] = xr;
+        }
+        xr.x = __shfl_sync(0xffffffffu, xr.x, gbase + owner);
+        xr.y = __shfl_sync(0xffffffffu, xr.y, gbase + owner);
+        if (valid) {
+          const double2* lr = Lm + (size_t)r * ld;
+          for (int q = c; q < r; q += G) {
+            const double2 l = lr[q];
+            double2 y = E[q * nb + j];
+            y.x = fma(-l.x, xr.x, fma(-l.y, xr.y, y.x));
+            y.y = fma(-l.x, xr.y, fma(l.y, xr.x, y.y));
+            E[q * nb + j] = y;
+          }
+        }
       }
-      const double2 ts = cmul(th, s);
-      for (int r = h + 1 + lane; r < n; r += 32) {
-        const double2 t = cmul(C[r * ld + h], ts);
-        E[r * nb + j].x -= t.x;
-        E[r * nb + j].y -= t.y;
-      }
-      __syncwarp();
-    }
-    // x = L^-H y: back substitution, x_r = (y_r - sum_{q>r} conj(L[q][r]) x_q) / L[r][r]
-    for (int r = n - 1; r >= 0; --r) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int q = r + 1 + lane; q < n; q += 32) {
-        const double2 p = cmulc(Lm[q * ld + r], E[q * nb + j]);
-        s.x += p.x;
-        s.y += p.y;
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-        s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-      }
-      if (lane == 0) {
-        const double il = rc[r];
-        E[r * nb + j] = make_double2((E[r * nb + j].x - s.x) * il, (E[r * nb + j].y - s.y) * il);
-      }
-      __syncwarp();
     }
   }
   if (tid == 0 && status != nullptr) status[k] = PWK_OK;
@@ -533,7 +626,7 @@ __global__ void __launch_bounds__(256) rr_kernel(int nk, int ld, int nb, const i
 int launch_rr(int nk, int ld, int nb, const int* nbase, const int* active, const double2* Hr,
               const double2* Sr, double2* W, double2* ev, double* eps, int* status,
               cudaStream_t st, unsigned char* drop_out, double* flops) {
-  rr_kernel<<<nk, 256, 0, st>>>(nk, ld, nb, nbase, active, Hr, Sr, W, ev, eps, status, drop_out, flops);
+  rr_kernel<<<nk, 256, 0, st>>>(nk, ld, nb, nbase, active, Hr, Sr, W, ev, eps, status, drop_out, flops); note_launch();
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? PWK_OK : cuda_fail(e, "rr_kernel");
 }

@@ -456,7 +456,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
   const double2* su = psi_kq;
   const bool with_s = pq->d_q != nullptr;   // this call applies S (the workspace may hold more)
   if (with_s) {
-    cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
+    cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items); note_launch();
     if ((rc = run_hpsi(pq, PWK_FP64, psi_kq, w->r, w->items, nullptr, npairs, nocc, nocc, st, w->su)))
       return rc;
     su = w->su;
@@ -465,8 +465,8 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
   // one warp per valence vector for the projections mu_v (8 to 16 warps)
   const int pc_threads = 32 * std::min(std::max(nocc, 8), 16);
   proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, nullptr, psi_kq, su, nullptr, w->t,
-                                              nullptr, 0, nullptr, 0, nullptr, w->b, w->bnorm);
-  tkin_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, psi_kq, w->tkin);
+                                              nullptr, 0, nullptr, 0, nullptr, w->b, w->bnorm); note_launch();
+  tkin_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, psi_kq, w->tkin); note_launch();
   cudaMemsetAsync(w->iters, 0, sizeof(int) * npairs, st);
   cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)npairs * np, st);
   KCK("sternheimer setup");
@@ -483,17 +483,17 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
     if (x_zero) {
       residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, w->b, w->bnorm, tol_in, eta,
-                                              w->r, w->rnorm, w->thr, w->active, w->first, w->counters);
+                                              w->r, w->rnorm, w->thr, w->active, w->first, w->counters); note_launch();
     } else {
       // t = H x (FP64) on every pair, then t = t - eps x + alpha P_v x, r = t - b
-      cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
+      cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items); note_launch();
       cudaEvent_t th = T.mark();
       if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
       T.close(0, th);
       proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1,
-                                                  eps_k, 1, alpha, w->t, nullptr);
+                                                  eps_k, 1, alpha, w->t, nullptr); note_launch();
       residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol_in, eta,
-                                              w->r, w->rnorm, w->thr, w->active, w->first, w->counters);
+                                              w->r, w->rnorm, w->thr, w->active, w->first, w->counters); note_launch();
     }
     KCK("sternheimer residual");
     if ((rc = read_counters())) return rc;
@@ -503,38 +503,38 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     for (int it = 0; it < max_iter; ++it) {
       cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
       cg_dir_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, w->tkin, w->r, w->d, w->dold,
-                                            w->rho, w->rho_old, w->thr, w->active, w->first, w->counters);
+                                            w->rho, w->rho_old, w->thr, w->active, w->first, w->counters); note_launch();
       KCK("cg_dir_kernel");
       if ((rc = read_counters())) return rc;
       T.harvest();
       if (hc[0] == 0) break;
-      cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->items);
+      cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->items); note_launch();
       cudaEvent_t th = T.mark();
       if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx)))
         return rc;
       T.close(0, th);
       if (inner_prec == PWK_FP64)
-        proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
-                                                            w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr);
+        { proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
+                                                            w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr); note_launch(); }
       else
-        proj_combine_kernel<float><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
-                                                           w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr);
+        { proj_combine_kernel<float><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
+                                                           w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr); note_launch(); }
       cg_step_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, w->d, w->t, x, w->r, w->dold,
-                                             w->rho, w->rho_old, w->iters, w->counters);
+                                             w->rho, w->rho_old, w->iters, w->counters); note_launch();
       KCK("cg_step_kernel");
     }
   }
   // final true residual with the FP64 operator
   cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
   {
-    cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items);
+    cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items); note_launch();
     cudaEvent_t th = T.mark();
     if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
     T.close(0, th);
     proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1, eps_k,
-                                                1, alpha, w->t, nullptr);
+                                                1, alpha, w->t, nullptr); note_launch();
     residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, 0.0, w->r,
-                                            w->rnorm, w->thr, w->active, w->first, w->counters);
+                                            w->rnorm, w->thr, w->active, w->first, w->counters); note_launch();
     KCK("sternheimer final residual");
     std::vector<double> h_rn(npairs);
     std::vector<int> h_it(npairs);

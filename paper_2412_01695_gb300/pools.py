@@ -1,4 +1,4 @@
-"""k-point pools across ranks (paper Sec. 4: k-points are split into pools, one MPI process per
+"""k-point pools across ranks (paper Sec. 3: k-points are split into pools, one MPI process per
 GPU, no GPU-GPU communication).
 
 H|psi>, the Davidson and the Sternheimer CG have no collective: every rank owns a contiguous

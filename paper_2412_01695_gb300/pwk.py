@@ -23,13 +23,14 @@ PWK_FLAG_ITEM_SKIPPED, PWK_FLAG_WAIT_TIMEOUT = 1, 2
 EXPORTS = ("pwk_plan_create", "pwk_plan_destroy", "pwk_plan_device_bytes",
            "pwk_plan_launch_shape", "pwk_plan_set_launch_shape", "pwk_plan_set_projector_path",
            "pwk_plan_errors", "pwk_plan_set_wait_limit", "pwk_plan_projector_fused",
+           "pwk_plan_projector_choice",
            "pwk_supported_grid",
            "pwk_hpsi_batched", "pwk_hpsi_batched_host", "pwk_hpsi_items", "pwk_hpsi_multi",
            "pwk_plan_set_overlap",
            "pwk_plan_has_overlap",
            "pwk_hspsi_batched", "pwk_hspsi_items", "pwk_drho_batched", "pwk_davidson_batched",
            "pwk_sternheimer_cg_batched", "pwk_eigh_batched", "pwk_eigh_batched_noalloc",
-           "pwk_measure_fma_peak", "pwk_plan_set_solver_timing", "pwk_plan_solver_stats",
+           "pwk_measure_fma_peak", "pwk_launch_count", "pwk_plan_set_solver_timing", "pwk_plan_solver_stats",
            "pwk_strerror", "pwk_last_error_detail", "pwk_version")
 
 _lib = None
@@ -57,6 +58,7 @@ def load(path: str = LIB_PATH):
         "pwk_plan_set_launch_shape": (_I, [_P, _I, _I, _I, _I]),
         "pwk_plan_set_projector_path": (_I, [_P, _I]),
         "pwk_plan_projector_fused": (_I, [_P, _I]),
+        "pwk_plan_projector_choice": (_I, [_P, _I]),
         "pwk_plan_errors": (_I, [_P, ctypes.POINTER(_I), _I]),
         "pwk_plan_set_wait_limit": (_I, [_P, ctypes.c_longlong]),
         "pwk_supported_grid": (_I, [_I]),
@@ -75,6 +77,7 @@ def load(path: str = LIB_PATH):
         "pwk_eigh_batched": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
         "pwk_eigh_batched_noalloc": (_I, [_I, _I, _I, _P, _P, _P, _P, _P, _P]),
         "pwk_measure_fma_peak": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
+        "pwk_launch_count": (ctypes.c_longlong, []),
         "pwk_plan_set_solver_timing": (_I, [_P, _I]),
         "pwk_plan_solver_stats": (_I, [_P, ctypes.POINTER(_D)]),
         "pwk_strerror": (ctypes.c_char_p, [_I]),
@@ -156,6 +159,11 @@ class Plan:
         """pwk_plan_projector_fused: whether H|psi> of this precision runs the projector terms
         inside the local kernel."""
         return load().pwk_plan_projector_fused(self.handle, precision) == 1
+
+    def projector_choice(self, precision: int) -> int:
+        """pwk_plan_projector_choice: the projector path whole-k-point H|psi> calls of this
+        precision take (3 fused, 1 tensor cores, 2 CUDA cores, 0 no projectors)."""
+        return int(load().pwk_plan_projector_choice(self.handle, precision))
 
     def errors(self, clear: bool = True) -> int:
         """pwk_plan_errors: the device-side flags (PWK_FLAG_*) recorded since the last clear."""
@@ -456,6 +464,11 @@ def measure_fma_peak(precision: int, stream=None):
     _check(load().pwk_measure_fma_peak(precision, ctypes.byref(f), ctypes.byref(n), _stream(stream)),
            "pwk_measure_fma_peak")
     return f.value, n.value
+
+
+def launch_count() -> int:
+    """pwk_launch_count: kernels the library has launched in this process so far."""
+    return int(load().pwk_launch_count())
 
 
 def supported_grid(N: int) -> bool:

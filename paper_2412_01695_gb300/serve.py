@@ -4,7 +4,7 @@ A job names a synthetic cell (lattice, atoms, cut-off, grid), a set of k-points 
 operation.  The server
   * admits a queued job when a slot is free and its estimated device footprint fits in the
     HBM budget next to the jobs already running (the analogue of the paper's memgpu: a block
-    of k-points is loaded only when the GPU memory allows it, Sec. 4 / Sec. 7.1);
+    of k-points is loaded only when the GPU memory allows it, Sec. 3 / Sec. 6.1);
   * runs every admitted job on its own worker thread and CUDA stream, so the work of different
     jobs overlaps on the device (a job that arrives while others run starts as soon as a slot
     and memory are free: continuous admission, not a queue in front of one job at a time);

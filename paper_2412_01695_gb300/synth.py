@@ -10,10 +10,10 @@ are fed from here; neither is imported by this module.
 
 Conventions (Rydberg atomic units, lengths in bohr, energies in Ry):
   * lattice vectors a_i are the rows of A; reciprocal vectors b_i are the rows
-    of B with a_i . b_j = 2 pi delta_ij (paper Sec. 5, Miller mesh G_{m1,m2,m3});
+    of B with a_i . b_j = 2 pi delta_ij (paper Sec. 4, Miller mesh G_{m1,m2,m3});
   * the basis of k is every G = m1 b1 + m2 b2 + m3 b3 with |k+G|^2 < ecut (Ry),
     the Rydberg form of the paper's cut-off (Sec. 2.2.1, 1/2|k+G|^2 < E_cut in Ha);
-  * the real-space grid is r_l = sum_i (l_i/N_i) a_i (Sec. 5), arrays indexed
+  * the real-space grid is r_l = sum_i (l_i/N_i) a_i (Sec. 4), arrays indexed
     [l1][l2][l3] with l3 fastest;
   * V(r) = sum_G V(G) e^{iG.r} is real; projectors follow
       beta_{I,lm}(q) = Omega^{-1/2} (-i)^l P_lm(q) exp(-|q|^2/4) exp(-i q.tau_I),

@@ -201,12 +201,15 @@ def test_every_launch_shape_gives_identical_results(precision):
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp32_c128"])
-@pytest.mark.parametrize("cfg,nks,nb", [(2, 6, 20), (1, 8, 8), (4, 5, 12), (2, 3, 44), (3, 2, 40), (3, 2, 7)])
+@pytest.mark.parametrize("cfg,nks,nb", [(2, 6, 20), (1, 8, 8), (4, 5, 12), (2, 3, 44), (3, 2, 40), (3, 2, 7),
+                                       (3, 3, 64)])
 def test_tensor_core_projections_match_cuda_cores_and_oracle(precision, cfg, nks, nb):
     """The FP32 projector contractions on the tensor cores (projection and add-back, three TF32
     products of a hi/lo split each) and on the CUDA cores both meet the FP32 bound against the
     oracle, and agree with each other to FP32 rounding: 4, 9 and 36 projectors (cell 3: four
-    atoms), 7 to 44 bands, one and several tiles of 128 plane waves, ragged last tiles."""
+    atoms), 7 to 64 bands, one and several tiles of 128 plane waves, ragged last tiles, the
+    H C tile of the add-back staged in shared memory or (where it does not fit: complex128
+    I/O with 40 bands, 64 bands) read in place, both depths of the projection's copy ring."""
     torch = torch_cuda()
     from paper_2412_01695_gb300 import pwk
     nkfull = int(np.prod(synth.CONFIGS[cfg]["mp"]))
@@ -218,7 +221,7 @@ def test_tensor_core_projections_match_cuda_cores_and_oracle(precision, cfg, nks
     dt = torch.complex64 if precision == "fp32" else torch.complex128
     x = torch.from_numpy(np.ascontiguousarray(psi)).to("cuda", dt)
     outs = []
-    for path in (0, 1):
+    for path in (2, 1):
         plan.set_projector_path(path)
         y = torch.full_like(x, complex(np.nan, np.nan))
         pwk.hpsi_batched(plan, prec, x, y, prob.nb)
@@ -316,6 +319,7 @@ def test_projector_paths_match_the_oracle(precision, cfg, nks, nb):
         # there, and the general kernel (kind 0) reads it through L1/L2 instead
         if path == 2 or cfg != 3:
             assert plan.projector_fused(prec) == (path == 3)
+            assert plan.projector_choice(prec) == path
         y = torch.full_like(x, complex(np.nan, np.nan))
         pwk.hpsi_batched(plan, prec, x, y, prob.nb)
         torch.cuda.synchronize()
