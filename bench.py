@@ -736,6 +736,7 @@ def run_case(args):
         blk = sternheimer_block(nk, torch.device("cuda"), stream)
         mode = pwk.PWK_FP64 if args.precision == "fp64" else pwk.PWK_FP32_C128
         nocc = blk["nocc"]
+        blk["plan_q"].set_solver_timing(True)
         times = []
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_push("case")
@@ -752,7 +753,8 @@ def run_case(args):
         torch.cuda.nvtx.range_pop()
         print(json.dumps({"case": "sternheimer", "cfg": 4, "nk": nk, "nocc": nocc, "precision": args.precision,
                           "ms": times, "pairs_above_tol": int(rc), "iters_max": int(iters.max()),
-                          "max_true_residual": float(resid.max())}))
+                          "iters_mean": float(iters.mean()), "max_true_residual": float(resid.max()),
+                          "stats": blk["plan_q"].solver_stats()}))
         blk["plan_k"].close()
         blk["plan_q"].close()
         return

@@ -25,6 +25,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "solvers.h"
@@ -36,9 +37,12 @@ struct CgWork {
   bool with_s = false;    // overlap S (plan with q): S u_v and S d kept
   double2 *b = nullptr, *r = nullptr, *d = nullptr, *dold = nullptr, *t = nullptr;
   double2 *su = nullptr, *sx = nullptr;
+  float2* v32 = nullptr;   // the valence set of the operator (S psi or psi) in FP32
   double *rho = nullptr, *rho_old = nullptr, *bnorm = nullptr, *thr = nullptr, *tkin = nullptr;
   double *rnorm = nullptr;
   int *active = nullptr, *first = nullptr, *iters = nullptr, *items = nullptr, *counters = nullptr;
+  int* list = nullptr;   // pairs still iterating, compacted (cg_compact_kernel)
+  int* seen = nullptr;   // iters[i] at pair i's last true residual
   std::vector<void*> ptrs;
 };
 
@@ -87,7 +91,9 @@ static int ensure_cg_work(pwk_plan* p, int nocc) {
       (rc = calloc_(p, w, &w->thr, nv)) || (rc = calloc_(p, w, &w->tkin, nv)) ||
       (rc = calloc_(p, w, &w->rnorm, nv)) || (rc = calloc_(p, w, &w->active, nv)) ||
       (rc = calloc_(p, w, &w->first, nv)) || (rc = calloc_(p, w, &w->iters, nv)) ||
-      (rc = calloc_(p, w, &w->items, nv * 3)) || (rc = calloc_(p, w, &w->counters, 4))) {
+      (rc = calloc_(p, w, &w->items, nv * 3)) || (rc = calloc_(p, w, &w->list, nv)) ||
+      (rc = calloc_(p, w, &w->seen, nv)) || (rc = calloc_(p, w, &w->v32, nv2)) ||
+      (rc = calloc_(p, w, &w->counters, 4))) {
     destroy_cg_work(p);
     return rc;
   }
@@ -111,6 +117,37 @@ __device__ double bsum2(double v, double* red) {
   for (int i = 0; i < nw; ++i) s += red[i];
   __syncthreads();
   return s;
+}
+
+// Block sums of two doubles per thread, reduced by warp 0 alone from per-thread partials in
+// shared memory (part: blockDim.x entries): the FP64 pipe runs at 1/64 of the FP32 rate on
+// this GPU and an FP64 instruction costs the whole warp, so a shuffle tree in every warp
+// (or every thread re-adding the warp partials) costs several times the arithmetic it
+// reduces.  All threads get both sums.
+__device__ double2 bsum_pair(double a, double b, double2* part, double2* out) {
+  part[threadIdx.x] = make_double2(a, b);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double sa = 0.0, sb = 0.0;
+    for (int j = threadIdx.x; j < (int)blockDim.x; j += 32) {
+      sa += part[j].x;
+      sb += part[j].y;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    if (threadIdx.x == 0) *out = make_double2(sa, sb);
+  }
+  __syncthreads();
+  return *out;
+}
+
+// The preconditioner of Sec. 2.4 for one plane wave, 1/M_G = 1 / max(1, |k+q+G|^2 / T_kin),
+// formed in FP32 (any fixed positive M keeps the CG exact; the same expression serves every
+// iteration of a solve).
+__device__ __forceinline__ double precond(double g2, float itk) {
+  return (double)(1.0f / fmaxf(1.0f, (float)g2 * itk));
 }
 
 // out = u + a_w ws + a_p sum_v py_v <pm_v|w>  for (k, n) with active (or all if null).
@@ -255,16 +292,16 @@ __global__ void __launch_bounds__(256) cg_dir_kernel(int nocc, int np, const int
   __shared__ double red[32];
   const int npk = npw[k];
   const double* G = g2 + (size_t)k * np;
-  const double itk = 1.0 / tkin[i];
+  const float itk = (float)(1.0 / tkin[i]);
   const double2* R = r + (size_t)i * np;
-  // 1/M_G = 1 / max(1, |k+q+G|^2 / T_kin) (Eq. row2): one division per plane wave, kept in
-  // shared memory for the update pass when the sphere fits (np is uniform over the launch)
+  // 1/M_G (Eq. row2, precond()): kept in shared memory for the update pass when the sphere
+  // fits (np is uniform over the launch)
   __shared__ double im[kCgMaxPw];
   const bool keep = np <= kCgMaxPw;
   double rr = 0.0, rh = 0.0;
   for (int g = threadIdx.x; g < npk; g += blockDim.x) {
     const double2 x = R[g];
-    const double mi = 1.0 / fmax(1.0, G[g] * itk);
+    const double mi = precond(G[g], itk);
     if (keep) im[g] = mi;
     rr += x.x * x.x + x.y * x.y;
     rh += (x.x * x.x + x.y * x.y) * mi;   // Re<M^-1 r | r>
@@ -284,7 +321,7 @@ __global__ void __launch_bounds__(256) cg_dir_kernel(int nocc, int np, const int
       D[g] = make_double2(0.0, 0.0);
       continue;
     }
-    const double mi = keep ? im[g] : 1.0 / fmax(1.0, G[g] * itk);   // im[g]: this thread's, pass 1
+    const double mi = keep ? im[g] : precond(G[g], itk);   // im[g]: this thread's, pass 1
     double2 v = make_double2(R[g].x * mi, R[g].y * mi);
     if (!f) {
       v.x += gam * DO[g].x;
@@ -352,6 +389,280 @@ __global__ void __launch_bounds__(256) cg_step_kernel(int nocc, int np, const in
     iters[i] += 1;
   }
 }
+
+// The pairs still iterating as a compact list, with their H|psi> work items (k, n, n) in the
+// same order; counters[2] = their number.  Warp-aggregated: pairs keep their order within a
+// warp (the bands of a k-point stay together for the projector kernels), warps in any order.
+__global__ void cg_compact_kernel(int n_pairs, int nocc, const int* active, int* list, int* items,
+                                  int* counters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = i < n_pairs && active[i] != 0;
+  const unsigned m = __ballot_sync(0xffffffffu, on);
+  if (m == 0) return;   // uniform over the warp
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(&counters[2], __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (on) {
+    const int c = base + __popc(m & ((1u << lane) - 1u));
+    list[c] = i;
+    items[3 * c] = i / nocc;
+    items[3 * c + 1] = i % nocc;
+    items[3 * c + 2] = i % nocc;
+  }
+}
+
+// The pairs whose x changed since their last true residual (iters[i] != seen[i]) as a
+// compact list with their work items, like cg_compact_kernel; seen[i] is brought up to date.
+__global__ void stale_compact_kernel(int n_pairs, int nocc, const int* iters, int* seen, int* list,
+                                     int* items, int* counters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool on = i < n_pairs && iters[i] != seen[i];
+  const unsigned m = __ballot_sync(0xffffffffu, on);
+  if (m == 0) return;   // uniform over the warp
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(&counters[2], __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (on) {
+    const int c = base + __popc(m & ((1u << lane) - 1u));
+    list[c] = i;
+    items[3 * c] = i / nocc;
+    items[3 * c + 1] = i % nocc;
+    items[3 * c + 2] = i % nocc;
+    seen[i] = iters[i];
+  }
+}
+
+// The true residual r = A x - b with the FP64 operator for the listed pairs (the first
+// *count entries of list; H x and S x already applied): t = H x - eps S x + alpha sum_v py_v
+// <pm_v|x> (the arithmetic of proj_combine_kernel<double>), r = t - b, ||r|| / ||b|| into
+// rnorm, and the thresholds and activity of the next inner solve (as residual_kernel).
+__global__ void __launch_bounds__(512) true_residual_kernel(int nocc, int np, const int* npw, const int* list,
+                                                           const int* count, const double2* pm,
+                                                           const double2* py, const double2* hx,
+                                                           const double2* x, const double2* sx,
+                                                           const double* eps, const double* alpha,
+                                                           const double2* b, const double* bnorm,
+                                                           double tol, double eta, double2* r,
+                                                           double* rnorm, double* thr, int* active,
+                                                           int* first, int* counters) {
+  if ((int)blockIdx.x >= *count) return;
+  const int i = list[blockIdx.x], k = i / nocc;
+  const int npk = npw[k];
+  __shared__ double mur[64], mui[64];
+  __shared__ double red[32];
+  const double2* X = x + (size_t)i * np;
+  const double2* SX = sx != nullptr ? sx + (size_t)i * np : X;
+  const double2* HX = hx + (size_t)i * np;
+  const double2* B = b + (size_t)i * np;
+  const double2* Pk = pm + (size_t)k * nocc * np;
+  const double2* Yk = py + (size_t)k * nocc * np;
+  double2* R = r + (size_t)i * np;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int v = warp; v < nocc; v += nw) {
+    double sx_ = 0, sy_ = 0;
+    const double2* pv = Pk + (size_t)v * np;
+    for (int g = lane; g < npk; g += 32) {
+      const double2 a = pv[g], bb = X[g];   // conj(a) x
+      sx_ += a.x * bb.x + a.y * bb.y;
+      sy_ += a.x * bb.y - a.y * bb.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx_ += __shfl_xor_sync(0xffffffffu, sx_, o);
+      sy_ += __shfl_xor_sync(0xffffffffu, sy_, o);
+    }
+    if (lane == 0) {
+      mur[v] = sx_;
+      mui[v] = sy_;
+    }
+  }
+  __syncthreads();
+  const double aw = -eps[i], ap = alpha[k];
+  double nn = 0.0;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) {
+    double2 v = make_double2(-B[g].x, -B[g].y);
+    if (g < npk) {
+      double yx = 0, yy = 0;
+      for (int u = 0; u < nocc; ++u) {
+        const double2 p = Yk[(size_t)u * np + g];
+        yx += p.x * mur[u] - p.y * mui[u];
+        yy += p.x * mui[u] + p.y * mur[u];
+      }
+      const double2 wg = SX[g], h = HX[g];
+      v.x += (aw * wg.x + ap * yx) + h.x;
+      v.y += (aw * wg.y + ap * yy) + h.y;
+    }
+    R[g] = v;
+    nn += v.x * v.x + v.y * v.y;
+  }
+  nn = bsum2(nn, red);
+  if (threadIdx.x == 0) {
+    const double rn = sqrt(nn), bn = bnorm[i];
+    rnorm[i] = bn > 0.0 ? rn / bn : 0.0;
+    const bool on = bn > 0.0 && rn > tol * bn;
+    active[i] = on ? 1 : 0;
+    first[i] = 1;
+    const double th = fmax(tol * bn, eta * rn);
+    thr[i] = th * th;
+    if (on) atomicAdd(&counters[0], 1);
+  }
+}
+
+// FP32 copy of n complex128 values (the valence set the mixed-mode operator reads every
+// iteration, converted once per solve).
+__global__ void to_c64_kernel(size_t n, const double2* in, float2* out) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = make_float2((float)in[i].x, (float)in[i].y);
+}
+
+// One CG iteration of a pair after H d (and S d) have been applied, in one pass over the
+// pair's vectors (one CTA per listed pair, a warp per valence vector for the projections):
+//   mu_v = <pm_v|d>, t = H d - eps (S) d + alpha sum_v pm_v mu_v          (Eqs. compute_mu,
+//          use_mu: the operator A d, in the arithmetic T like proj_combine_kernel)
+//   lambda = -Re<d|r> / Re<d|t>, x += lambda d, r += lambda t               (Eqs. lambda,
+//          updatex, updater)
+//   stop if ||r||^2 <= thr; else rho' = Re<M^-1 r|r>, d = M^-1 r + (rho'/rho) d, rho = rho'
+//          (Eqs. row2 - updated of the next iteration; d_old is the d just used, so no
+//          separate copy is kept)
+// The valence set pm (S psi_v, or psi_v without S) is read in T: for FP32 from its FP32 copy
+// (pm32), so the vectors the projections read every iteration are converted once per solve,
+// and d is staged in T in shared memory once per CTA (an FP64 <-> FP32 conversion runs on the
+// FP64 pipe).  t and the new r stay in shared memory (2 np complex128) between the passes.
+// Scalars are FP64.  counters[0] counts the pairs with a new direction, counters[1] flags a
+// breakdown (Re<d|t> <= 0: the pair stops, as in cg_step_kernel).
+template <typename T>
+__global__ void __launch_bounds__(512) cg_update_kernel(int nocc, int np, const int* npw, const int* list,
+                                                       const double* g2, const double* tkin,
+                                                       const double2* pm, const float2* pm32,
+                                                       const double2* hd, double2* d,
+                                                       const double2* sd, const double* eps,
+                                                       const double* alpha, double2* x, double2* r,
+                                                       double* rho, const double* thr, int* active,
+                                                       int* iters, int* counters) {
+  using T2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
+  const int i = list[blockIdx.x], k = i / nocc;
+  const int npk = npw[k];
+  extern __shared__ double2 cg_sm[];
+  double2* ts = cg_sm;                                // t = A d
+  double2* rs = cg_sm + np;                           // the updated r
+  T2* dT = reinterpret_cast<T2*>(cg_sm + 2 * np);     // d in T
+  __shared__ T mur[64], mui[64];
+  __shared__ double2 part[512], tot;
+  double2* D = d + (size_t)i * np;
+  const double2* HD = hd + (size_t)i * np;
+  const T2* Pk;
+  if constexpr (std::is_same<T, float>::value) Pk = pm32 + (size_t)k * nocc * np;
+  else Pk = pm + (size_t)k * nocc * np;
+  double2* X = x + (size_t)i * np;
+  double2* R = r + (size_t)i * np;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    const double2 v = D[g];
+    dT[g] = T2{T(v.x), T(v.y)};
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int v = warp; v < nocc; v += nw) {
+    T sx = 0, sy = 0;
+    const T2* pv = Pk + (size_t)v * np;
+    for (int g = lane; g < npk; g += 32) {
+      const T2 a = pv[g], b = dT[g];   // conj(a) b
+      sx += a.x * b.x + a.y * b.y;
+      sy += a.x * b.y - a.y * b.x;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) {
+      mur[v] = sx;
+      mui[v] = sy;
+    }
+  }
+  __syncthreads();
+  const T aw = T(-eps[i]), ap = T(alpha[k]);
+  double dr = 0.0, dt = 0.0;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    T yx = 0, yy = 0;
+    for (int v = 0; v < nocc; ++v) {
+      const T2 pv = Pk[(size_t)v * np + g];
+      const T mx = mur[v], my = mui[v];
+      yx += pv.x * mx - pv.y * my;
+      yy += pv.x * my + pv.y * mx;
+    }
+    T wx, wy;
+    if (sd != nullptr) {
+      const double2 sv = sd[(size_t)i * np + g];
+      wx = T(sv.x);
+      wy = T(sv.y);
+    } else {
+      wx = dT[g].x;
+      wy = dT[g].y;
+    }
+    const T ox = aw * wx + ap * yx, oy = aw * wy + ap * yy;
+    const double2 h = HD[g];
+    const double2 t = make_double2(double(ox) + h.x, double(oy) + h.y);
+    ts[g] = t;
+    const double2 dg = D[g], rg = R[g];
+    dr += dg.x * rg.x + dg.y * rg.y;
+    dt += dg.x * t.x + dg.y * t.y;
+  }
+  {
+    const double2 s2 = bsum_pair(dr, dt, part, &tot);
+    dr = s2.x;
+    dt = s2.y;
+  }
+  if (!(dt > 0.0) || !isfinite(dr)) {   // indefinite direction or breakdown: stop this pair
+    if (threadIdx.x == 0) {
+      active[i] = 0;
+      atomicOr(&counters[1], 1);
+    }
+    return;
+  }
+  const double lam = -dr / dt;
+  const float itk = (float)(1.0 / tkin[i]);
+  const double* G = g2 + (size_t)k * np;
+  double rr = 0.0, rh = 0.0;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    const double2 dg = D[g], t = ts[g];
+    double2 xg = X[g], rg = R[g];
+    xg.x += lam * dg.x;
+    xg.y += lam * dg.y;
+    rg.x += lam * t.x;
+    rg.y += lam * t.y;
+    X[g] = xg;
+    R[g] = rg;
+    rs[g] = rg;
+    const double mi = precond(G[g], itk);
+    rr += rg.x * rg.x + rg.y * rg.y;
+    rh += (rg.x * rg.x + rg.y * rg.y) * mi;
+  }
+  {
+    const double2 s2 = bsum_pair(rr, rh, part, &tot);
+    rr = s2.x;
+    rh = s2.y;
+  }
+  if (threadIdx.x == 0) iters[i] += 1;
+  if (rr <= thr[i]) {
+    if (threadIdx.x == 0) active[i] = 0;
+    return;
+  }
+  const double gam = rh / rho[i];
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    const double mi = precond(G[g], itk);
+    const double2 rg = rs[g], dg = D[g];
+    D[g] = make_double2(rg.x * mi + gam * dg.x, rg.y * mi + gam * dg.y);
+  }
+  if (threadIdx.x == 0) {
+    rho[i] = rh;
+    atomicAdd(&counters[0], 1);
+  }
+}
+
+// Shared memory of cg_update_kernel for spheres of np plane waves; the fused step is used
+// while it fits, else the separate proj_combine, cg_step and cg_dir kernels.
+static size_t cg_update_smem(int np) { return (size_t)3 * np * sizeof(double2); }
+constexpr size_t kCgUpdateMaxSmem = 200 * 1024;
 
 // The stick maps of the pair (k sphere of plan_k -> k+q sphere of plan_kq, the union of their
 // z-sticks), built once per pair of plans and kept in plan_kq.
@@ -468,16 +779,43 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
                                               nullptr, 0, nullptr, 0, nullptr, w->b, w->bnorm); note_launch();
   tkin_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, psi_kq, w->tkin); note_launch();
   cudaMemsetAsync(w->iters, 0, sizeof(int) * npairs, st);
+  cudaMemsetAsync(w->seen, 0, sizeof(int) * npairs, st);
   cudaMemsetAsync(x, 0, sizeof(double2) * (size_t)npairs * np, st);
   KCK("sternheimer setup");
 
   PhaseTimer T(pq, st);   // pwk_plan_set_solver_timing (H applications inside the CG)
+  const size_t upd_smem = cg_update_smem(np);
+  const bool fused_step = upd_smem <= kCgUpdateMaxSmem;
+  if (fused_step && upd_smem > 48 * 1024) {
+    cudaError_t e = allow_full_smem(cg_update_kernel<double>);
+    if (e == cudaSuccess) e = allow_full_smem(cg_update_kernel<float>);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cg_update)");
+  }
   const int inner_prec = (mode == PWK_FP64) ? PWK_FP64 : PWK_FP32_C128;
   const double eta = (mode == PWK_FP64) ? 0.0 : 1e-4;
   // The iteration aims at half the requested residual: an FP64 operator that rounds
   // differently (another library, a dense matrix) then still finds ||A x - b|| <= tol ||b||;
   // the count returned and resid_out are measured against tol itself.
   const double tol_in = 0.5 * tol;
+  // FP64 H x, S x and the true residual for the pairs whose x changed since their last one
+  // (a compact list; the launches cover every pair and read the list's length on the device)
+  auto true_residual = [&](double tol_r, double eta_r) -> int {
+    stale_compact_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->iters, w->seen, w->list, w->items,
+                                                       w->counters); note_launch();
+    cudaEvent_t th = T.mark();
+    int r2 = run_hpsi(pq, PWK_FP64, x, w->t, w->items, w->counters + 2, npairs, nocc, nocc, st, sx);
+    if (r2) return r2;
+    T.close(0, th);
+    true_residual_kernel<<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->list, w->counters + 2, su, su,
+                                                        w->t, x, sx, eps_k, alpha, w->b, w->bnorm, tol_r,
+                                                        eta_r, w->r, w->rnorm, w->thr, w->active, w->first,
+                                                        w->counters); note_launch();
+    return PWK_OK;
+  };
+  if (fused_step && inner_prec != PWK_FP64) {
+    const size_t nvv = (size_t)nk * nocc * np;
+    to_c64_kernel<<<std::min<size_t>(nblk(nvv), 4 * 1024), 256, 0, st>>>(nvv, su, w->v32); note_launch();
+  }
   bool x_zero = true;
   for (int outer = 0; outer < 8; ++outer) {
     cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
@@ -485,56 +823,71 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
       residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, nullptr, w->b, w->bnorm, tol_in, eta,
                                               w->r, w->rnorm, w->thr, w->active, w->first, w->counters); note_launch();
     } else {
-      // t = H x (FP64) on every pair, then t = t - eps x + alpha P_v x, r = t - b
-      cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items); note_launch();
-      cudaEvent_t th = T.mark();
-      if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
-      T.close(0, th);
-      proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1,
-                                                  eps_k, 1, alpha, w->t, nullptr); note_launch();
-      residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol_in, eta,
-                                              w->r, w->rnorm, w->thr, w->active, w->first, w->counters); note_launch();
+      // the true residual of the pairs whose x changed in the last inner solve (the others
+      // keep theirs: converged, or stopped by a breakdown at their first step)
+      if ((rc = true_residual(tol_in, eta))) return rc;
     }
     KCK("sternheimer residual");
     if ((rc = read_counters())) return rc;
     T.harvest();
     if (hc[0] == 0) break;
     x_zero = false;
-    for (int it = 0; it < max_iter; ++it) {
+    // the first direction of this inner solve: d = M^-1 r (cg_dir_kernel)
+    cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
+    cg_dir_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, w->tkin, w->r, w->d, w->dold,
+                                          w->rho, w->rho_old, w->thr, w->active, w->first, w->counters); note_launch();
+    KCK("cg_dir_kernel");
+    if ((rc = read_counters())) return rc;
+    T.harvest();
+    for (int it = 0; it < max_iter && hc[0] > 0; ++it) {
+      const int nact = hc[0];   // pairs with a direction (all active ones)
       cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
-      cg_dir_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, w->tkin, w->r, w->d, w->dold,
-                                            w->rho, w->rho_old, w->thr, w->active, w->first, w->counters); note_launch();
-      KCK("cg_dir_kernel");
+      if (fused_step) {
+        // one pass per pair: the active pairs compacted, H (and S) applied to their
+        // directions, then the fused CG step that also forms the next direction
+        cg_compact_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->list, w->items,
+                                                        w->counters); note_launch();
+        cudaEvent_t th = T.mark();
+        if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, nact, nocc, nocc, st, sx))) return rc;
+        T.close(0, th);
+        if (inner_prec == PWK_FP64)
+          { cg_update_kernel<double><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
+                w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
+                w->counters); note_launch(); }
+        else
+          { cg_update_kernel<float><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
+                w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
+                w->counters); note_launch(); }
+        KCK("cg_update_kernel");
+      } else {
+        // spheres too large for the fused step: A d, the step and the next direction apart
+        cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->items); note_launch();
+        cudaEvent_t th = T.mark();
+        if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx)))
+          return rc;
+        T.close(0, th);
+        if (inner_prec == PWK_FP64)
+          { proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
+                                                              w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr); note_launch(); }
+        else
+          { proj_combine_kernel<float><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
+                                                             w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr); note_launch(); }
+        cg_step_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, w->d, w->t, x, w->r, w->dold,
+                                               w->rho, w->rho_old, w->iters, w->counters); note_launch();
+        cudaMemsetAsync(w->counters, 0, sizeof(int), st);
+        cg_dir_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, w->tkin, w->r, w->d, w->dold,
+                                              w->rho, w->rho_old, w->thr, w->active, w->first, w->counters); note_launch();
+        KCK("cg_step_kernel");
+      }
       if ((rc = read_counters())) return rc;
       T.harvest();
-      if (hc[0] == 0) break;
-      cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->items); note_launch();
-      cudaEvent_t th = T.mark();
-      if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx)))
-        return rc;
-      T.close(0, th);
-      if (inner_prec == PWK_FP64)
-        { proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
-                                                            w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr); note_launch(); }
-      else
-        { proj_combine_kernel<float><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, w->active, su, su, w->t,
-                                                           w->d, sx, 1, eps_k, 1, alpha, w->t, nullptr); note_launch(); }
-      cg_step_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->active, w->d, w->t, x, w->r, w->dold,
-                                             w->rho, w->rho_old, w->iters, w->counters); note_launch();
-      KCK("cg_step_kernel");
     }
   }
-  // final true residual with the FP64 operator
+  // final true residual with the FP64 operator, for the pairs whose x changed since their
+  // last one (the others' rnorm is that of their current x already)
   cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
   {
-    cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, nullptr, w->items); note_launch();
-    cudaEvent_t th = T.mark();
-    if ((rc = run_hpsi(pq, PWK_FP64, x, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx))) return rc;
-    T.close(0, th);
-    proj_combine_kernel<double><<<npairs, pc_threads, 0, st>>>(nocc, np, pq->d_npw, nullptr, su, su, w->t, x, sx, 1, eps_k,
-                                                1, alpha, w->t, nullptr); note_launch();
-    residual_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->t, w->b, w->bnorm, tol, 0.0, w->r,
-                                            w->rnorm, w->thr, w->active, w->first, w->counters); note_launch();
+    if ((rc = true_residual(tol, 0.0))) return rc;
     KCK("sternheimer final residual");
     std::vector<double> h_rn(npairs);
     std::vector<int> h_it(npairs);
