@@ -78,7 +78,12 @@ PATH_NAMES = {1: "separate tensor-core kernels", 2: "separate CUDA-core kernels"
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of a kernel, from ncu captures
 # summarised under profiles/, with the digest of the sources they were captured at.
-TRAFFIC = {}
+# rr_kernel: a full-batch launch of the 64-k solve (11.04 MB) scaled by k-points to the
+# 512-k batch of the headline step.
+TRAFFIC = {
+    "rr_kernel": {"bytes": 8 * 11042560, "profile": "profiles/rr_kernel_davidson_fcc64k_20b.md",
+                  "sources": ["rr.cu", "solvers.h"], "digest": "88ebedd93321"},
+}
 
 
 def traffic_for(kernel: str):
