@@ -80,9 +80,23 @@ PATH_NAMES = {1: "separate tensor-core kernels", 2: "separate CUDA-core kernels"
 # summarised under profiles/, with the digest of the sources they were captured at.
 # rr_kernel: a full-batch launch of the 64-k solve (11.04 MB) scaled by k-points to the
 # 512-k batch of the headline step.
+# The H|psi> kernels of the 512-k cell in FP32: mean of three launches.
 TRAFFIC = {
     "rr_kernel": {"bytes": 8 * 11042560, "profile": "profiles/rr_kernel_davidson_fcc64k_20b.md",
                   "sources": ["rr.cu", "solvers.h"], "digest": "88ebedd93321"},
+    "fused_window_kernel<float,float,24,6>": {
+        "bytes": 48430848 + 4129195, "profile": "profiles/hpsi_step_kernels_fcc512k_20b_fp32.md",
+        "sources": ["fused_window.cuh", "fft_line.cuh", "hpsi_f32.cu"], "digest": "e8fae88693ee"},
+    "nl_project_kernel<float,float,9>": {
+        "bytes": 65060011 + 12288, "profile": "profiles/hpsi_step_kernels_fcc512k_20b_fp32.md",
+        "sources": ["nonlocal.cu"], "digest": "67c9475f7eb9"},
+    "nl_addback_kernel<float,float,9>": {
+        "bytes": 66527147 + 159061, "profile": "profiles/hpsi_step_kernels_fcc512k_20b_fp32.md",
+        "sources": ["nonlocal.cu"], "digest": "67c9475f7eb9"},
+    "fused_window_kernel_nl<float,float,24,6>": {
+        "bytes": 68650069 + 11811669, "profile": "profiles/fused_window_kernel_nl_hpsi_fcc512k_20b_fp32.md",
+        "sources": ["fused_window.cuh", "fft_line.cuh", "nl_fused.cuh", "hpsi_f32_nl.cu"],
+        "digest": "d9d6563f277a"},
 }
 
 
@@ -440,10 +454,24 @@ def run_hpsi_kernels(args, torch, dev, stream, peaks):
     ns, npl = hit_planes(prob)
     kname = f"fused_window_kernel<float,float,{prob.N},{prob.N // 4}>"
     tb, tprof = traffic_for(kname)
+    # DRAM bytes of one FP32 step in the automatic projector path (ncu captures summarised
+    # under profiles/), against the step's algorithmic bytes
+    choice = plan.projector_choice(pwk.PWK_FP32)
+    step_kernels = {2: [f"nl_project_kernel<float,float,{prob.nkb}>", kname,
+                        f"nl_addback_kernel<float,float,{prob.nkb}>"],
+                    3: [f"fused_window_kernel_nl<float,float,{prob.N},{prob.N // 4}>"]}.get(choice, [])
+    step_t = [traffic_for(k) for k in step_kernels]
+    step_dram = sum(t[0] for t in step_t) if step_t and all(t[0] for t in step_t) else None
+    step_alg = algorithmic_bytes_per_band(prob, 8) * nbk
     out = {
         "fp32_batched": {"band_k_applies_per_s": nbk / kern_s, "ms": kern_s * 1e3,
                          "tflops_algorithmic": step_tf,
-                         "hbm_gbs_algorithmic": algorithmic_bytes_per_band(prob, 8) * nbk / kern_s / 1e9},
+                         "hbm_gbs_algorithmic": algorithmic_bytes_per_band(prob, 8) * nbk / kern_s / 1e9,
+                         "algorithmic_bytes_per_step": step_alg,
+                         "dram_bytes_per_step": step_dram,
+                         "dram_over_algorithmic": step_dram / step_alg if step_dram else None,
+                         "dram_kernels": step_kernels,
+                         "dram_profiles": sorted({t[1] for t in step_t if t[1]})},
         "fp64_batched": {"band_k_applies_per_s": nbk / float(np.mean(t64)), "ms": float(np.mean(t64)) * 1e3},
         "fp64_per_k": {"band_k_applies_per_s": nbk / float(np.mean(tpk)),
                        "call": "pwk_hpsi_items, one launch set per k-point"},
@@ -801,7 +829,8 @@ def run_case(args):
     torch.cuda.nvtx.range_pop()
     print(json.dumps({"case": args.case, "cfg": args.cfg, "nk": prob.nk, "nb": prob.nb,
                       "precision": args.precision, "ms": times,
-                      "launch_shape": plan.launch_shape(pwk.PRECISIONS[args.precision]), **extra}))
+                      "launch_shape": plan.launch_shape(pwk.PRECISIONS[args.precision]),
+                      "projector_path": plan.projector_choice(pwk.PRECISIONS[args.precision]), **extra}))
     plan.close()
 
 
