@@ -101,9 +101,10 @@ int pwk_plan_set_launch_shape(pwk_plan* plan, int precision, int kind, int threa
 
 /* How the nonlocal projector terms (Eqs. lambdah, gamma, finalnl; with q also delta_eq,
  * finals) are applied:
- *   0 (default)  automatic: path 3, path 2 or (FP32 arithmetic) path 1, whichever
- *                pwk_plan_create measured fastest for each precision as whole H applications of
- *                32 bands on the plan's own k-points (pwk_plan_projector_choice tells);
+ *   0 (default)  automatic: path 2, unless path 3 or (FP32 arithmetic) path 1 ran more than
+ *                3 % faster when pwk_plan_create timed them for each precision as whole H
+ *                applications of 32 bands on the plan's own k-points (then the faster of
+ *                the two; pwk_plan_projector_choice tells);
  *   1            separate kernels, both contractions of FP32 batched calls on whole k-points
  *                on the 5th-generation tensor cores where they apply (2 nkb <= 128, nb <= 128,
  *                tiles within shared memory; the S add-back stays on the CUDA cores): three
