@@ -540,8 +540,9 @@ __global__ void __launch_bounds__(512) cg_update_kernel(int nocc, int np, const 
                                                        const double2* sd, const double* eps,
                                                        const double* alpha, double2* x, double2* r,
                                                        double* rho, const double* thr, int* active,
-                                                       int* iters, int* counters) {
+                                                       int* iters, int* counters, const int* count) {
   using T2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
+  if ((int)blockIdx.x >= *count) return;   // the launch covers an upper bound of the list
   const int i = list[blockIdx.x], k = i / nocc;
   const int npk = npw[k];
   extern __shared__ double2 cg_sm[];
@@ -664,6 +665,8 @@ __global__ void __launch_bounds__(512) cg_update_kernel(int nocc, int np, const 
 // while it fits, else the separate proj_combine, cg_step and cg_dir kernels.
 static size_t cg_update_smem(int np) { return (size_t)3 * np * sizeof(double2); }
 constexpr size_t kCgUpdateMaxSmem = 200 * 1024;
+// CG iterations between two reads of the solver's counters by the host
+constexpr int kCgBurst = 4;
 
 // The stick maps of the pair (k sphere of plan_k -> k+q sphere of plan_kq, the union of their
 // z-sticks), built once per pair of plans and kept in plan_kq.
@@ -840,28 +843,36 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     KCK("cg_dir_kernel");
     if ((rc = read_counters())) return rc;
     T.harvest();
-    for (int it = 0; it < max_iter && hc[0] > 0; ++it) {
-      const int nact = hc[0];   // pairs with a direction (all active ones)
-      cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
+    for (int it = 0; it < max_iter && hc[0] > 0;) {
+      const int nact = hc[0];   // pairs with a direction at the last read: an upper bound after it
       if (fused_step) {
-        // one pass per pair: the active pairs compacted, H (and S) applied to their
-        // directions, then the fused CG step that also forms the next direction
-        cg_compact_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->list, w->items,
-                                                        w->counters); note_launch();
-        cudaEvent_t th = T.mark();
-        if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, nact, nocc, nocc, st, sx))) return rc;
-        T.close(0, th);
-        if (inner_prec == PWK_FP64)
-          { cg_update_kernel<double><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
-                w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
-                w->counters); note_launch(); }
-        else
-          { cg_update_kernel<float><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
-                w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
-                w->counters); note_launch(); }
-        KCK("cg_update_kernel");
+        // one pass per pair and iteration: the active pairs compacted, H (and S) applied to
+        // their directions, then the fused CG step that also forms the next direction.  Up to
+        // kCgBurst iterations run between two reads of the counters (pairs only leave the
+        // active set, so nact bounds every list of the burst; the launches read its current
+        // length on the device)
+        for (int b = 0; b < kCgBurst && it < max_iter; ++b, ++it) {
+          cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
+          cg_compact_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->list, w->items,
+                                                          w->counters); note_launch();
+          cudaEvent_t th = T.mark();
+          if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, w->counters + 2, nact, nocc, nocc, st, sx)))
+            return rc;
+          T.close(0, th);
+          if (inner_prec == PWK_FP64)
+            { cg_update_kernel<double><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
+                  w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
+                  w->counters, w->counters + 2); note_launch(); }
+          else
+            { cg_update_kernel<float><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
+                  w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
+                  w->counters, w->counters + 2); note_launch(); }
+          KCK("cg_update_kernel");
+        }
       } else {
         // spheres too large for the fused step: A d, the step and the next direction apart
+        ++it;
+        cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
         cg_items_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->items); note_launch();
         cudaEvent_t th = T.mark();
         if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, nullptr, npairs, nocc, nocc, st, sx)))
