@@ -351,9 +351,11 @@ int pwk_eigh_batched_noalloc(int nprob, int n, int nev, const void* H, const voi
  * preconditioner M_GG = max(1, |k+q+G|^2 / <psi_{k+q,n}|T|psi_{k+q,n}>).
  *   plan_kq   plan of the k+q points (the operator); plan_k  plan of the k points; both
  *             have the same nk, cell and grid, point i of plan_kq being k_i + q
- *   mode      PWK_FP64: FP64 operator.  PWK_FP32_C128: FP32 H inside an FP64 iterative
- *             refinement (true residual with the FP64 operator, FP32-operator PCG on the
- *             correction); CG vectors, dot products and scalars are FP64 in both modes.
+ *   mode      PWK_FP64: FP64 operator and CG vectors.  PWK_FP32_C128: FP64 iterative
+ *             refinement (true residual with the FP64 operator, x in FP64) around an inner
+ *             PCG on the correction with the FP32 operator and FP32 vectors; dot products
+ *             are FP64 sums (of per-thread FP32 partials in the inner PCG) and the CG
+ *             scalars are FP64 in both modes.
  *   psi_k     device [nk][nocc][npw_max(k)] complex128    occupied states at k
  *   eps_k     device [nk][nocc] float64                   their eigenvalues (Ry)
  *   psi_kq    device [nk][nocc][npw_max(k+q)] complex128  occupied states at k+q

@@ -17,12 +17,13 @@
 //             d_old (Eq. updated); ||r|| for the stopping test
 //   cg_step : lambda = -Re<d|r>/Re<d|t> (Eq. lambda), x += lambda d, r += lambda t,
 //             d_old = d, rho_old = rho (Eqs. updatex, updater, updatedold)
-// All vectors, dot products and scalars are FP64 and stay on the device; the host reads one
-// counter (pairs still iterating) per iteration.  Mixed mode: the operator inside the CG (H d
-// and the valence projection alpha Q d) uses FP32 arithmetic, and the solve is wrapped in
-// FP64 iterative refinement (the CG restarts from the true FP64 residual of the current x,
-// each inner solve reducing it by 1e-6: the FP32 operator's rounding allows that before the
-// inner iteration stalls; 1e-4 took one refinement round more, 1e-7 more iterations).
+// Dot products and scalars are FP64 and stay on the device; the host reads the counters
+// (pairs still iterating) every few iterations.  FP64 mode: FP64 vectors and operator.  Mixed
+// mode: FP64 iterative refinement around FP32 inner solves: each round takes the true FP64
+// residual r = A x - b, solves A e = -r for a correction with FP32 vectors and the FP32
+// operator (H d and the valence projection alpha Q d), reducing it by 1e-6 (the FP32
+// rounding allows that before the inner iteration stalls; 1e-4 took one refinement round
+// more, 1e-7 more iterations), and adds e to x in FP64.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -39,6 +40,10 @@ struct CgWork {
   double2 *b = nullptr, *r = nullptr, *d = nullptr, *dold = nullptr, *t = nullptr;
   double2 *su = nullptr, *sx = nullptr;
   float2* v32 = nullptr;   // the valence set of the operator (S psi or psi) in FP32
+  // mixed mode: the inner solve's vectors in FP32 (correction e, its residual r, direction
+  // d, t = H d and S d)
+  bool has32 = false;
+  float2 *e32 = nullptr, *r32 = nullptr, *d32 = nullptr, *t32 = nullptr, *sd32 = nullptr;
   double *rho = nullptr, *rho_old = nullptr, *bnorm = nullptr, *thr = nullptr, *tkin = nullptr;
   double *rnorm = nullptr;
   int *active = nullptr, *first = nullptr, *iters = nullptr, *items = nullptr, *counters = nullptr;
@@ -64,13 +69,14 @@ static int calloc_(pwk_plan* p, CgWork* w, T** ptr, size_t n) {
 // Grows only, like the Davidson workspace: a call with at most the allocated number of
 // occupied bands (and an overlap the arrays cover) reuses it; arrays are indexed with the
 // call's nocc.
-static int ensure_cg_work(pwk_plan* p, int nocc) {
+static int ensure_cg_work(pwk_plan* p, int nocc, bool mixed) {
   const bool want_s = p->d_q != nullptr;
-  if (p->cg && p->cg->nocc >= nocc && (p->cg->with_s || !want_s)) return PWK_OK;
-  bool with_s = want_s;
+  if (p->cg && p->cg->nocc >= nocc && (p->cg->with_s || !want_s) && (p->cg->has32 || !mixed)) return PWK_OK;
+  bool with_s = want_s, has32 = mixed;
   if (p->cg) {
     nocc = std::max(nocc, p->cg->nocc);
     with_s = with_s || p->cg->with_s;
+    has32 = has32 || p->cg->has32;
   }
   destroy_cg_work(p);
   CgWork* w = new CgWork();
@@ -82,6 +88,13 @@ static int ensure_cg_work(pwk_plan* p, int nocc) {
   const size_t nv = (size_t)p->nk * nocc, nv2 = nv * p->npw_max;
   int rc;
   if (with_s && ((rc = calloc_(p, w, &w->su, nv2)) || (rc = calloc_(p, w, &w->sx, nv2)))) {
+    destroy_cg_work(p);
+    return rc;
+  }
+  w->has32 = has32;
+  if (has32 && ((rc = calloc_(p, w, &w->e32, nv2)) || (rc = calloc_(p, w, &w->r32, nv2)) ||
+                (rc = calloc_(p, w, &w->d32, nv2)) || (rc = calloc_(p, w, &w->t32, nv2)) ||
+                (with_s && (rc = calloc_(p, w, &w->sd32, nv2))))) {
     destroy_cg_work(p);
     return rc;
   }
@@ -529,7 +542,8 @@ __global__ void to_c64_kernel(size_t n, const double2* in, float2* out) {
 // The valence set pm (S psi_v, or psi_v without S) is read in T: for FP32 from its FP32 copy
 // (pm32), so the vectors the projections read every iteration are converted once per solve,
 // and d is staged in T in shared memory once per CTA (an FP64 <-> FP32 conversion runs on the
-// FP64 pipe).  t and the new r stay in shared memory (2 np complex128) between the passes.
+// FP64 pipe).  t and M^-1 r stay in shared memory (2 np complex128) between the passes; sums
+// and updates are FMA chains (every FP64 instruction counts on this GPU).
 // Scalars are FP64.  counters[0] counts the pairs with a new direction, counters[1] flags a
 // breakdown (Re<d|t> <= 0: the pair stops, as in cg_step_kernel).
 template <typename T>
@@ -547,7 +561,7 @@ __global__ void __launch_bounds__(512) cg_update_kernel(int nocc, int np, const 
   const int npk = npw[k];
   extern __shared__ double2 cg_sm[];
   double2* ts = cg_sm;                                // t = A d
-  double2* rs = cg_sm + np;                           // the updated r
+  double2* rs = cg_sm + np;                           // M^-1 r of the updated r
   T2* dT = reinterpret_cast<T2*>(cg_sm + 2 * np);     // d in T
   __shared__ T mur[64], mui[64];
   __shared__ double2 part[512], tot;
@@ -606,8 +620,8 @@ __global__ void __launch_bounds__(512) cg_update_kernel(int nocc, int np, const 
     const double2 t = make_double2(double(ox) + h.x, double(oy) + h.y);
     ts[g] = t;
     const double2 dg = D[g], rg = R[g];
-    dr += dg.x * rg.x + dg.y * rg.y;
-    dt += dg.x * t.x + dg.y * t.y;
+    dr = fma(dg.x, rg.x, fma(dg.y, rg.y, dr));
+    dt = fma(dg.x, t.x, fma(dg.y, t.y, dt));
   }
   {
     const double2 s2 = bsum_pair(dr, dt, part, &tot);
@@ -628,16 +642,17 @@ __global__ void __launch_bounds__(512) cg_update_kernel(int nocc, int np, const 
   for (int g = threadIdx.x; g < npk; g += blockDim.x) {
     const double2 dg = D[g], t = ts[g];
     double2 xg = X[g], rg = R[g];
-    xg.x += lam * dg.x;
-    xg.y += lam * dg.y;
-    rg.x += lam * t.x;
-    rg.y += lam * t.y;
+    xg.x = fma(lam, dg.x, xg.x);
+    xg.y = fma(lam, dg.y, xg.y);
+    rg.x = fma(lam, t.x, rg.x);
+    rg.y = fma(lam, t.y, rg.y);
     X[g] = xg;
     R[g] = rg;
-    rs[g] = rg;
     const double mi = precond(G[g], itk);
-    rr += rg.x * rg.x + rg.y * rg.y;
-    rh += (rg.x * rg.x + rg.y * rg.y) * mi;
+    rs[g] = make_double2(rg.x * mi, rg.y * mi);   // M^-1 r for the next direction
+    const double q = fma(rg.x, rg.x, rg.y * rg.y);
+    rr += q;
+    rh = fma(q, mi, rh);
   }
   {
     const double2 s2 = bsum_pair(rr, rh, part, &tot);
@@ -651,13 +666,193 @@ __global__ void __launch_bounds__(512) cg_update_kernel(int nocc, int np, const 
   }
   const double gam = rh / rho[i];
   for (int g = threadIdx.x; g < npk; g += blockDim.x) {
-    const double mi = precond(G[g], itk);
-    const double2 rg = rs[g], dg = D[g];
-    D[g] = make_double2(rg.x * mi + gam * dg.x, rg.y * mi + gam * dg.y);
+    const double2 zg = rs[g], dg = D[g];   // zg = M^-1 r
+    D[g] = make_double2(fma(gam, dg.x, zg.x), fma(gam, dg.y, zg.y));
   }
   if (threadIdx.x == 0) {
     rho[i] = rh;
     atomicAdd(&counters[0], 1);
+  }
+}
+
+// ------------------------------------------------------------------ mixed-mode inner solve
+// The inner solve of a refinement round works on the correction e of the current x: it
+// solves A e = -r (r = A x - b, the FP64 true residual) with FP32 vectors and the FP32
+// operator, and the round ends with x += e in FP64.  Only the dot products are reduced in
+// FP64 (each thread's FP32 partial, then an FP64 sum over the block), and the CG scalars are
+// FP64; the element-wise work stays off the FP64 pipe.
+
+// Start of an inner solve for every pair: e = 0; for the active pairs r32 = r, the first
+// direction d = M^-1 r, rho = Re<M^-1 r|r>, and the stopping test (||r||^2 <= thr: the pair
+// is inactive; counters[0] counts the pairs with a direction).
+__global__ void __launch_bounds__(256) cg_init32_kernel(int nocc, int np, const int* npw, const double* g2,
+                                                       const double* tkin, const double2* r, float2* e32,
+                                                       float2* r32, float2* d32, double* rho,
+                                                       const double* thr, int* active, int* counters) {
+  const int i = blockIdx.x, k = i / nocc;
+  __shared__ double2 part[256], tot;
+  float2* E = e32 + (size_t)i * np;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) E[g] = make_float2(0.f, 0.f);
+  if (!active[i]) return;
+  const int npk = npw[k];
+  const float itk = (float)(1.0 / tkin[i]);
+  const double* G = g2 + (size_t)k * np;
+  const double2* R = r + (size_t)i * np;
+  float2* R32 = r32 + (size_t)i * np;
+  float2* D32 = d32 + (size_t)i * np;
+  float rr = 0.f, rh = 0.f;
+  for (int g = threadIdx.x; g < np; g += blockDim.x) {
+    if (g >= npk) {
+      R32[g] = make_float2(0.f, 0.f);
+      D32[g] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const float2 v = make_float2((float)R[g].x, (float)R[g].y);
+    const float mi = 1.0f / fmaxf(1.0f, (float)G[g] * itk);
+    R32[g] = v;
+    D32[g] = make_float2(v.x * mi, v.y * mi);
+    const float q = fmaf(v.x, v.x, v.y * v.y);
+    rr += q;
+    rh = fmaf(q, mi, rh);
+  }
+  const double2 s2 = bsum_pair((double)rr, (double)rh, part, &tot);
+  if (threadIdx.x == 0) {
+    if (s2.x <= thr[i]) {
+      active[i] = 0;
+    } else {
+      rho[i] = s2.y;
+      atomicAdd(&counters[0], 1);
+    }
+  }
+}
+
+// One FP32 CG iteration of a listed pair (the first *count entries of list): t = H d - eps S d +
+// alpha sum_v pm_v <pm_v|d> from the FP32 H (and S) output, lambda = -Re<d|r>/Re<d|t>,
+// e += lambda d, r += lambda t, the stopping test, the next direction d = M^-1 r + gamma d.
+// Vectors and element-wise arithmetic FP32; each thread's partial dot products are summed in
+// FP64 over the block; lambda, gamma, rho FP64.  Counters as in cg_update_kernel.
+__global__ void __launch_bounds__(512) cg_update32_kernel(int nocc, int np, const int* npw, const int* list,
+                                                         const int* count, const double* g2,
+                                                         const double* tkin, const float2* pm32,
+                                                         const float2* t32, float2* d32,
+                                                         const float2* sd32, const double* eps,
+                                                         const double* alpha, float2* e32, float2* r32,
+                                                         double* rho, const double* thr, int* active,
+                                                         int* iters, int* counters) {
+  if ((int)blockIdx.x >= *count) return;   // the launch covers an upper bound of the list
+  const int i = list[blockIdx.x], k = i / nocc;
+  const int npk = npw[k];
+  extern __shared__ float2 cg32_sm[];
+  float2* ds = cg32_sm;            // d
+  float2* ts = cg32_sm + np;       // t = A d
+  float2* zs = cg32_sm + 2 * np;   // M^-1 r of the updated r
+  __shared__ float mur[64], mui[64];
+  __shared__ double2 part[512], tot;
+  float2* D = d32 + (size_t)i * np;
+  const float2* HD = t32 + (size_t)i * np;
+  const float2* Pk = pm32 + (size_t)k * nocc * np;
+  float2* E = e32 + (size_t)i * np;
+  float2* R = r32 + (size_t)i * np;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) ds[g] = D[g];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int v = warp; v < nocc; v += nw) {
+    float sx = 0.f, sy = 0.f;
+    const float2* pv = Pk + (size_t)v * np;
+    for (int g = lane; g < npk; g += 32) {
+      const float2 a = pv[g], b = ds[g];   // conj(a) b
+      sx = fmaf(a.x, b.x, fmaf(a.y, b.y, sx));
+      sy = fmaf(a.x, b.y, fmaf(-a.y, b.x, sy));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) {
+      mur[v] = sx;
+      mui[v] = sy;
+    }
+  }
+  __syncthreads();
+  const float aw = (float)(-eps[i]), ap = (float)alpha[k];
+  float dr = 0.f, dt = 0.f;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    float yx = 0.f, yy = 0.f;
+    for (int v = 0; v < nocc; ++v) {
+      const float2 pv = Pk[(size_t)v * np + g];
+      yx = fmaf(pv.x, mur[v], fmaf(-pv.y, mui[v], yx));
+      yy = fmaf(pv.x, mui[v], fmaf(pv.y, mur[v], yy));
+    }
+    const float2 w = sd32 != nullptr ? sd32[(size_t)i * np + g] : ds[g];
+    const float2 h = HD[g];
+    const float2 t = make_float2(fmaf(aw, w.x, fmaf(ap, yx, h.x)), fmaf(aw, w.y, fmaf(ap, yy, h.y)));
+    ts[g] = t;
+    const float2 dg = ds[g], rg = R[g];
+    dr = fmaf(dg.x, rg.x, fmaf(dg.y, rg.y, dr));
+    dt = fmaf(dg.x, t.x, fmaf(dg.y, t.y, dt));
+  }
+  double drd, dtd;
+  {
+    const double2 s2 = bsum_pair((double)dr, (double)dt, part, &tot);
+    drd = s2.x;
+    dtd = s2.y;
+  }
+  if (!(dtd > 0.0) || !isfinite(drd)) {   // indefinite direction or breakdown: stop this pair
+    if (threadIdx.x == 0) {
+      active[i] = 0;
+      atomicOr(&counters[1], 1);
+    }
+    return;
+  }
+  const float lam = (float)(-drd / dtd);
+  const float itk = (float)(1.0 / tkin[i]);
+  const double* G = g2 + (size_t)k * np;
+  float rr = 0.f, rh = 0.f;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    const float2 dg = ds[g], t = ts[g];
+    float2 eg = E[g], rg = R[g];
+    eg.x = fmaf(lam, dg.x, eg.x);
+    eg.y = fmaf(lam, dg.y, eg.y);
+    rg.x = fmaf(lam, t.x, rg.x);
+    rg.y = fmaf(lam, t.y, rg.y);
+    E[g] = eg;
+    R[g] = rg;
+    const float mi = 1.0f / fmaxf(1.0f, (float)G[g] * itk);
+    zs[g] = make_float2(rg.x * mi, rg.y * mi);
+    const float q = fmaf(rg.x, rg.x, rg.y * rg.y);
+    rr += q;
+    rh = fmaf(q, mi, rh);
+  }
+  double rrd, rhd;
+  {
+    const double2 s2 = bsum_pair((double)rr, (double)rh, part, &tot);
+    rrd = s2.x;
+    rhd = s2.y;
+  }
+  if (threadIdx.x == 0) iters[i] += 1;
+  if (rrd <= thr[i]) {
+    if (threadIdx.x == 0) active[i] = 0;
+    return;
+  }
+  const float gam = (float)(rhd / rho[i]);
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    const float2 zg = zs[g], dg = ds[g];
+    D[g] = make_float2(fmaf(gam, dg.x, zg.x), fmaf(gam, dg.y, zg.y));
+  }
+  if (threadIdx.x == 0) {
+    rho[i] = rhd;
+    atomicAdd(&counters[0], 1);
+  }
+}
+
+// x += e for every pair (e is zero where the pair did not iterate)
+__global__ void add_correction_kernel(int nocc, int np, const int* npw, const float2* e32, double2* x) {
+  const int i = blockIdx.x, k = i / nocc, npk = npw[k];
+  const float2* E = e32 + (size_t)i * np;
+  double2* X = x + (size_t)i * np;
+  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
+    const float2 e = E[g];
+    X[g] = make_double2(X[g].x + (double)e.x, X[g].y + (double)e.y);
   }
 }
 
@@ -730,7 +925,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int rc;
   if ((rc = ensure_xfer(pq, pk))) return rc;
-  if ((rc = ensure_cg_work(pq, nocc))) return rc;
+  if ((rc = ensure_cg_work(pq, nocc, mode == PWK_FP32_C128))) return rc;
   CgWork* w = pq->cg;
   const int nk = pq->nk, np = pq->npw_max, npairs = nk * nocc;
   const double2* psi_kq = static_cast<const double2*>(psi_kq_v);
@@ -790,9 +985,15 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
   PhaseTimer T(pq, st);   // pwk_plan_set_solver_timing (H applications inside the CG)
   const size_t upd_smem = cg_update_smem(np);
   const bool fused_step = upd_smem <= kCgUpdateMaxSmem;
+  // mixed mode: the inner solves on FP32 vectors (fused step only)
+  const size_t upd32_smem = (size_t)3 * np * sizeof(float2);
+  const bool inner32 = fused_step && mode == PWK_FP32_C128;
+  if (inner32 && upd32_smem > 48 * 1024) {
+    cudaError_t e = allow_full_smem(cg_update32_kernel);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cg_update32)");
+  }
   if (fused_step && upd_smem > 48 * 1024) {
     cudaError_t e = allow_full_smem(cg_update_kernel<double>);
-    if (e == cudaSuccess) e = allow_full_smem(cg_update_kernel<float>);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cg_update)");
   }
   const int inner_prec = (mode == PWK_FP64) ? PWK_FP64 : PWK_FP32_C128;
@@ -836,6 +1037,39 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     T.harvest();
     if (hc[0] == 0) break;
     x_zero = false;
+    if (inner32) {
+      // mixed mode: the inner solve on the FP32 correction e (A e = -r), then x += e
+      cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
+      cg_init32_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, w->tkin, w->r, w->e32, w->r32,
+                                              w->d32, w->rho, w->thr, w->active, w->counters); note_launch();
+      KCK("cg_init32_kernel");
+      if ((rc = read_counters())) return rc;
+      T.harvest();
+      for (int it = 0; it < max_iter && hc[0] > 0;) {
+        const int nact = hc[0];   // pairs with a direction at the last read: an upper bound after it
+        for (int b = 0; b < kCgBurst && it < max_iter; ++b, ++it) {
+          cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
+          cg_compact_kernel<<<nblk(npairs), 256, 0, st>>>(npairs, nocc, w->active, w->list, w->items,
+                                                          w->counters); note_launch();
+          cudaEvent_t th = T.mark();
+          if ((rc = run_hpsi(pq, PWK_FP32, w->d32, w->t32, w->items, w->counters + 2, nact, nocc, nocc, st,
+                             with_s ? w->sd32 : nullptr)))
+            return rc;
+          T.close(0, th);
+          cg_update32_kernel<<<nact, pc_threads, upd32_smem, st>>>(nocc, np, pq->d_npw, w->list, w->counters + 2,
+                                                                   pq->d_g2, w->tkin, w->v32, w->t32, w->d32,
+                                                                   with_s ? w->sd32 : nullptr, eps_k, alpha, w->e32,
+                                                                   w->r32, w->rho, w->thr, w->active, w->iters,
+                                                                   w->counters); note_launch();
+          KCK("cg_update32_kernel");
+        }
+        if ((rc = read_counters())) return rc;
+        T.harvest();
+      }
+      add_correction_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, w->e32, x); note_launch();
+      KCK("add_correction_kernel");
+      continue;
+    }
     // the first direction of this inner solve: d = M^-1 r (cg_dir_kernel)
     cudaMemsetAsync(w->counters, 0, 4 * sizeof(int), st);
     cg_dir_kernel<<<npairs, 256, 0, st>>>(nocc, np, pq->d_npw, pq->d_g2, w->tkin, w->r, w->d, w->dold,
@@ -859,14 +1093,10 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
           if ((rc = run_hpsi(pq, inner_prec, w->d, w->t, w->items, w->counters + 2, nact, nocc, nocc, st, sx)))
             return rc;
           T.close(0, th);
-          if (inner_prec == PWK_FP64)
-            { cg_update_kernel<double><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
-                  w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
-                  w->counters, w->counters + 2); note_launch(); }
-          else
-            { cg_update_kernel<float><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
-                  w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
-                  w->counters, w->counters + 2); note_launch(); }
+          // FP64 mode (the mixed mode's inner solves take the FP32 path above)
+          cg_update_kernel<double><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
+                w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
+                w->counters, w->counters + 2); note_launch();
           KCK("cg_update_kernel");
         }
       } else {

@@ -379,3 +379,27 @@ def test_fused_projectors_every_launch_shape_identical(precision):
                     assert np.array_equal(out, first), (kind, T, L)
     assert first is not None
     plan.close()
+
+
+def test_launch_count_follows_the_projector_path():
+    """pwk_launch_count counts the kernels the library queues: one H|psi> call is one launch
+    with the projector terms inside the local kernel (path 3), three with the separate
+    CUDA-core kernels (path 2), and none for an empty work list."""
+    torch = torch_cuda()
+    from paper_2412_01695_gb300 import pwk
+    prob = synth.make_config(2, k_subset=[0, 3, 300], nb=4)
+    plan = pwk.plan_from_problem(prob)
+    x = torch.from_numpy(prob.psi).cuda().to(torch.complex64)
+    y = torch.empty_like(x)
+    for path, launches in ((3, 1), (2, 3)):
+        plan.set_projector_path(path)
+        pwk.hpsi_batched(plan, pwk.PWK_FP32, x, y, prob.nb)   # first call: any one-time set-up
+        torch.cuda.synchronize()
+        c0 = pwk.launch_count()
+        pwk.hpsi_batched(plan, pwk.PWK_FP32, x, y, prob.nb)
+        torch.cuda.synchronize()
+        assert pwk.launch_count() - c0 == launches, (path, pwk.launch_count() - c0)
+    c0 = pwk.launch_count()
+    pwk.hpsi_items(plan, pwk.PWK_FP32, x, y, None, prob.nb)
+    assert pwk.launch_count() == c0
+    plan.close()
