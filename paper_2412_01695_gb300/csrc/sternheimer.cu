@@ -27,7 +27,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <type_traits>
 #include <vector>
 
 #include "solvers.h"
@@ -531,60 +530,47 @@ __global__ void to_c64_kernel(size_t n, const double2* in, float2* out) {
 }
 
 // One CG iteration of a pair after H d (and S d) have been applied, in one pass over the
-// pair's vectors (one CTA per listed pair, a warp per valence vector for the projections):
+// pair's vectors (one CTA per listed pair, a warp per valence vector for the projections), FP64
+// (the mixed mode's inner solves use cg_update32_kernel):
 //   mu_v = <pm_v|d>, t = H d - eps (S) d + alpha sum_v pm_v mu_v          (Eqs. compute_mu,
-//          use_mu: the operator A d, in the arithmetic T like proj_combine_kernel)
+//          use_mu: the operator A d)
 //   lambda = -Re<d|r> / Re<d|t>, x += lambda d, r += lambda t               (Eqs. lambda,
 //          updatex, updater)
 //   stop if ||r||^2 <= thr; else rho' = Re<M^-1 r|r>, d = M^-1 r + (rho'/rho) d, rho = rho'
 //          (Eqs. row2 - updated of the next iteration; d_old is the d just used, so no
 //          separate copy is kept)
-// The valence set pm (S psi_v, or psi_v without S) is read in T: for FP32 from its FP32 copy
-// (pm32), so the vectors the projections read every iteration are converted once per solve,
-// and d is staged in T in shared memory once per CTA (an FP64 <-> FP32 conversion runs on the
-// FP64 pipe).  t and M^-1 r stay in shared memory (2 np complex128) between the passes; sums
-// and updates are FMA chains (every FP64 instruction counts on this GPU).
-// Scalars are FP64.  counters[0] counts the pairs with a new direction, counters[1] flags a
+// pm is the valence set S psi_v (psi_v without S).  t and M^-1 r stay in shared memory (2 np
+// complex128) between the passes; sums and updates are FMA chains (every FP64 instruction
+// counts on this GPU).  counters[0] counts the pairs with a new direction, counters[1] flags a
 // breakdown (Re<d|t> <= 0: the pair stops, as in cg_step_kernel).
-template <typename T>
 __global__ void __launch_bounds__(512) cg_update_kernel(int nocc, int np, const int* npw, const int* list,
                                                        const double* g2, const double* tkin,
-                                                       const double2* pm, const float2* pm32,
-                                                       const double2* hd, double2* d,
+                                                       const double2* pm, const double2* hd, double2* d,
                                                        const double2* sd, const double* eps,
                                                        const double* alpha, double2* x, double2* r,
                                                        double* rho, const double* thr, int* active,
                                                        int* iters, int* counters, const int* count) {
-  using T2 = typename std::conditional<std::is_same<T, float>::value, float2, double2>::type;
   if ((int)blockIdx.x >= *count) return;   // the launch covers an upper bound of the list
   const int i = list[blockIdx.x], k = i / nocc;
   const int npk = npw[k];
   extern __shared__ double2 cg_sm[];
-  double2* ts = cg_sm;                                // t = A d
-  double2* rs = cg_sm + np;                           // M^-1 r of the updated r
-  T2* dT = reinterpret_cast<T2*>(cg_sm + 2 * np);     // d in T
-  __shared__ T mur[64], mui[64];
+  double2* ts = cg_sm;          // t = A d
+  double2* rs = cg_sm + np;     // M^-1 r of the updated r
+  __shared__ double mur[64], mui[64];
   __shared__ double2 part[512], tot;
   double2* D = d + (size_t)i * np;
   const double2* HD = hd + (size_t)i * np;
-  const T2* Pk;
-  if constexpr (std::is_same<T, float>::value) Pk = pm32 + (size_t)k * nocc * np;
-  else Pk = pm + (size_t)k * nocc * np;
+  const double2* Pk = pm + (size_t)k * nocc * np;
   double2* X = x + (size_t)i * np;
   double2* R = r + (size_t)i * np;
-  for (int g = threadIdx.x; g < npk; g += blockDim.x) {
-    const double2 v = D[g];
-    dT[g] = T2{T(v.x), T(v.y)};
-  }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int v = warp; v < nocc; v += nw) {
-    T sx = 0, sy = 0;
-    const T2* pv = Pk + (size_t)v * np;
+    double sx = 0, sy = 0;
+    const double2* pv = Pk + (size_t)v * np;
     for (int g = lane; g < npk; g += 32) {
-      const T2 a = pv[g], b = dT[g];   // conj(a) b
-      sx += a.x * b.x + a.y * b.y;
-      sy += a.x * b.y - a.y * b.x;
+      const double2 a = pv[g], b = D[g];   // conj(a) b
+      sx = fma(a.x, b.x, fma(a.y, b.y, sx));
+      sy = fma(a.x, b.y, fma(-a.y, b.x, sy));
     }
     for (int o = 16; o > 0; o >>= 1) {
       sx += __shfl_xor_sync(0xffffffffu, sx, o);
@@ -596,30 +582,20 @@ __global__ void __launch_bounds__(512) cg_update_kernel(int nocc, int np, const 
     }
   }
   __syncthreads();
-  const T aw = T(-eps[i]), ap = T(alpha[k]);
+  const double aw = -eps[i], ap = alpha[k];
   double dr = 0.0, dt = 0.0;
   for (int g = threadIdx.x; g < npk; g += blockDim.x) {
-    T yx = 0, yy = 0;
+    double yx = 0, yy = 0;
     for (int v = 0; v < nocc; ++v) {
-      const T2 pv = Pk[(size_t)v * np + g];
-      const T mx = mur[v], my = mui[v];
-      yx += pv.x * mx - pv.y * my;
-      yy += pv.x * my + pv.y * mx;
+      const double2 pv = Pk[(size_t)v * np + g];
+      yx = fma(pv.x, mur[v], fma(-pv.y, mui[v], yx));
+      yy = fma(pv.x, mui[v], fma(pv.y, mur[v], yy));
     }
-    T wx, wy;
-    if (sd != nullptr) {
-      const double2 sv = sd[(size_t)i * np + g];
-      wx = T(sv.x);
-      wy = T(sv.y);
-    } else {
-      wx = dT[g].x;
-      wy = dT[g].y;
-    }
-    const T ox = aw * wx + ap * yx, oy = aw * wy + ap * yy;
-    const double2 h = HD[g];
-    const double2 t = make_double2(double(ox) + h.x, double(oy) + h.y);
-    ts[g] = t;
     const double2 dg = D[g], rg = R[g];
+    const double2 w = sd != nullptr ? sd[(size_t)i * np + g] : dg;
+    const double2 h = HD[g];
+    const double2 t = make_double2(fma(aw, w.x, fma(ap, yx, h.x)), fma(aw, w.y, fma(ap, yy, h.y)));
+    ts[g] = t;
     dr = fma(dg.x, rg.x, fma(dg.y, rg.y, dr));
     dt = fma(dg.x, t.x, fma(dg.y, t.y, dt));
   }
@@ -858,7 +834,7 @@ __global__ void add_correction_kernel(int nocc, int np, const int* npw, const fl
 
 // Shared memory of cg_update_kernel for spheres of np plane waves; the fused step is used
 // while it fits, else the separate proj_combine, cg_step and cg_dir kernels.
-static size_t cg_update_smem(int np) { return (size_t)3 * np * sizeof(double2); }
+static size_t cg_update_smem(int np) { return (size_t)2 * np * sizeof(double2); }
 constexpr size_t kCgUpdateMaxSmem = 200 * 1024;
 // CG iterations between two reads of the solver's counters by the host
 constexpr int kCgBurst = 4;
@@ -993,7 +969,7 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cg_update32)");
   }
   if (fused_step && upd_smem > 48 * 1024) {
-    cudaError_t e = allow_full_smem(cg_update_kernel<double>);
+    cudaError_t e = allow_full_smem(cg_update_kernel);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(cg_update)");
   }
   const int inner_prec = (mode == PWK_FP64) ? PWK_FP64 : PWK_FP32_C128;
@@ -1094,8 +1070,8 @@ extern "C" int pwk_sternheimer_cg_batched(pwk_plan* pq, pwk_plan* pk, int mode, 
             return rc;
           T.close(0, th);
           // FP64 mode (the mixed mode's inner solves take the FP32 path above)
-          cg_update_kernel<double><<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
-                w->tkin, su, w->v32, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
+          cg_update_kernel<<<nact, pc_threads, upd_smem, st>>>(nocc, np, pq->d_npw, w->list, pq->d_g2,
+                w->tkin, su, w->t, w->d, sx, eps_k, alpha, x, w->r, w->rho, w->thr, w->active, w->iters,
                 w->counters, w->counters + 2); note_launch();
           KCK("cg_update_kernel");
         }
