@@ -210,18 +210,44 @@ __global__ void __launch_bounds__(kThreads, 1) nl_project_tcw_kernel(NlArgs a) {
   const float2* bin = static_cast<const float2*>(a.beta) + (size_t)k * nkb * a.npw_max;
   // block b into ring slot b % RING: nb rows of 16 coefficients, nkb rows of 16 projector
   // values (one complex element per copy; zero-filled past npw(k))
+  // 8-byte elements (FP32 coefficients, beta) go two plane waves per 16-byte copy when every
+  // row starts on a 16-byte boundary (even npw_max, aligned bases); the part of a pair past
+  // npw(k) is zero-filled
+  const bool pairs = (a.npw_max % 2 == 0) && ((reinterpret_cast<uintptr_t>(a.in) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(a.beta) & 15) == 0);
   auto fetch = [&](int b) {
     if (b < nblk) {
       unsigned char* slot = ring + (b % RING) * raw_slot;
-      for (int t = tid; t < 16 * (nb + nkb); t += kProducers) {
-        const int r = t >> 4, j = t & 15, g = 16 * b + j;
-        const bool in = g < np;
-        if (r < nb) {
-          cp_async<sizeof(VI)>(slot + (r * 16 + j) * sizeof(VI), cin + (size_t)r * a.npw_max + (in ? g : 0),
-                               in ? (int)sizeof(VI) : 0);
-        } else {
-          const int m = r - nb;
-          cp_async<8>(slot + raw_c + (m * 16 + j) * 8, bin + (size_t)m * a.npw_max + (in ? g : 0), in ? 8 : 0);
+      if (pairs) {
+        constexpr int per = sizeof(VI) == 8 ? 8 : 16;   // copies per band row
+        for (int t = tid; t < per * nb + 8 * nkb; t += kProducers) {
+          if (t < per * nb) {
+            const int r = t / per, j = t - r * per;
+            if constexpr (sizeof(VI) == 8) {
+              const int g = 16 * b + 2 * j, nin = g + 1 < np ? 2 : (g < np ? 1 : 0);
+              cp_async<16>(slot + (r * 16 + 2 * j) * 8, cin + (size_t)r * a.npw_max + (nin ? g : 0), 8 * nin);
+            } else {
+              const int g = 16 * b + j;
+              const bool in = g < np;
+              cp_async<16>(slot + (r * 16 + j) * 16, cin + (size_t)r * a.npw_max + (in ? g : 0), in ? 16 : 0);
+            }
+          } else {
+            const int u = t - per * nb, m = u >> 3, j = u & 7;
+            const int g = 16 * b + 2 * j, nin = g + 1 < np ? 2 : (g < np ? 1 : 0);
+            cp_async<16>(slot + raw_c + (m * 16 + 2 * j) * 8, bin + (size_t)m * a.npw_max + (nin ? g : 0), 8 * nin);
+          }
+        }
+      } else {
+        for (int t = tid; t < 16 * (nb + nkb); t += kProducers) {
+          const int r = t >> 4, j = t & 15, g = 16 * b + j;
+          const bool in = g < np;
+          if (r < nb) {
+            cp_async<sizeof(VI)>(slot + (r * 16 + j) * sizeof(VI), cin + (size_t)r * a.npw_max + (in ? g : 0),
+                                 in ? (int)sizeof(VI) : 0);
+          } else {
+            const int m = r - nb;
+            cp_async<8>(slot + raw_c + (m * 16 + j) * 8, bin + (size_t)m * a.npw_max + (in ? g : 0), in ? 8 : 0);
+          }
         }
       }
     }
