@@ -54,3 +54,22 @@ def test_cpu_baseline_leg_measures_busy_cores():
     for ik, e in eigs.items():
         w = np.linalg.eigvalsh(ham.problem_h(prob, ik))[:prob.nb]
         assert np.max(np.abs(e - w)) <= bench.EIG_TOL
+
+
+def test_traffic_figures_name_their_profile_and_sources():
+    """Every DRAM-traffic figure bench.py reports comes from a profile summary under
+    profiles/ and names the kernel sources whose digest gates it (a figure whose sources
+    changed since the capture is reported as null)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    assert b.TRAFFIC
+    for name, t in b.TRAFFIC.items():
+        assert t["bytes"] > 0, name
+        assert os.path.isfile(os.path.join(ROOT, t["profile"])), (name, t["profile"])
+        for src in t["sources"]:
+            assert os.path.isfile(os.path.join(ROOT, "paper_2412_01695_gb300", "csrc", src)), (name, src)
+        assert len(t["digest"]) == 12
+        got = b.traffic_for(name)
+        assert got == (None, None) or got == (t["bytes"], t["profile"])
